@@ -1,0 +1,212 @@
+/*
+ * sdf.h -- C ABI of the GB300 (sm_103a) implementation of the convolution-based
+ * signed distance method of Gurumoorthy & Rangarajan, "Fast convolution based
+ * method for computing the signed distance function and its derivatives".
+ *
+ * What one execute computes (all on the GPU, on the plan's CUDA stream):
+ *   1. Snap each point Y_k to its nearest grid node (Sec. 6, Examples 3-4) and
+ *      scatter it onto a zero-padded M^D grid: g(X) = sum_k delta(X - Y_k)
+ *      (eq. function_g, Table 1 step 2), and the tangent- or normal-weighted
+ *      fields g_j = sum_k Z_k^j delta(X - Y_k) (Sec. 4.1) / P_k^j (Sec. 4.2).
+ *   2. Convolve g by FFT with f(X) = exp(-||X||/tau) (eq. function_f, Table 1
+ *      steps 1, 3-5), with f*X_j/||X|| (eq. SxSyconv) and with the Hessian
+ *      kernels (eqs. Sxx, Syy, Sxy; the same differentiation in 3D), and the
+ *      g_j with the winding-number kernels X_j/||X||^2 (eq.
+ *      kappadiscretefinal, 2D) or degree kernels X_j/||X||^3 (eq. mudef, 3D).
+ *   3. S = -tau log(phi) (eq. STilde, Table 1 step 6), grad S = (f_j f * g)/phi
+ *      (eq. SxSyconv), the Hessian (eqs. Sxx, Syy, Sxy), and the sign: +1
+ *      (inside) where |mu| >= 1/2, -1 outside (Sec. 4; positive inside, Sec. 1).
+ *
+ * Grids.  dims[a] = N_a nodes on axis a (x first); node i sits at i*h (origin
+ * 0).  Every grid array is C-order with x fastest: element (x, y[, z]) at
+ * x + N_0*(y + N_1*z).  The padded FFT size per axis is the smallest power of
+ * two M_a >= max(2*N_a - 1, 16), so the circular convolution equals the linear
+ * one on the N^D output nodes.
+ *
+ * Precision.  SDF_FP64: every FFT pass, product and epilogue in double; grid
+ * outputs are double.  SDF_FP32 (the mixed path): FFT passes and products in
+ * float, outputs float; nodes where phi falls below the FP32 transform's noise
+ * bound but inside the FP64 trust region are recomputed by a shifted direct
+ * sum (flag SDF_FLAG_FIXUP), so S matches the FP64 path there.
+ *
+ * Trust region.  The FFT returns phi with an absolute error near u*|f|_1*|g|_2
+ * (u the unit roundoff), so -tau log(phi) is noise where phi is tiny (the
+ * paper's Sec. 3.3).  Both paths use the same FP64 trust threshold theta_64;
+ * at nodes with phi < theta_64 they return S_cap = -tau log(theta_64) (a lower
+ * bound on S), zero derivatives, and set SDF_FLAG_CAPPED.  The sign is valid
+ * everywhere.
+ *
+ * Ownership and errors.  The caller owns every points/weights/output buffer;
+ * the plan owns its workspace and kernel spectra.  All calls are asynchronous
+ * on the plan's stream unless stated.  Errors detected on the device (a point
+ * outside the grid, a bounded wait that expired) are recorded in the plan and
+ * returned by sdf_sync().  No exception or longjmp crosses this ABI.  A plan is
+ * not thread-safe: one host thread at a time per plan.
+ */
+#ifndef SDF_GB300_H
+#define SDF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdf_plan_s *sdf_plan;
+
+typedef enum {
+    SDF_OK = 0,
+    SDF_ERR_INVALID_ARG = 1,       /* bad argument; nothing was enqueued        */
+    SDF_ERR_UNSUPPORTED = 2,       /* D not 2 or 3, or a grid too large         */
+    SDF_ERR_POINT_OUT_OF_GRID = 3, /* some point snapped outside [0, N_a)       */
+    SDF_ERR_OOM = 4,               /* device allocation failed                  */
+    SDF_ERR_CUDA = 5,              /* a CUDA runtime call failed                */
+    SDF_ERR_TIMEOUT = 6,           /* a bounded device-side wait expired        */
+    SDF_ERR_CAPACITY = 7           /* input larger than a fixed-size buffer     */
+} sdf_status;
+
+typedef enum { SDF_FP64 = 0, SDF_FP32 = 1 } sdf_precision;
+
+/* Output fields a plan prepares kernel spectra for (bit mask). */
+enum {
+    SDF_OUT_S = 1,    /* S (always computed)                               */
+    SDF_OUT_DS = 2,   /* grad S, D planes                                  */
+    SDF_OUT_D2S = 4,  /* Hessian, D(D+1)/2 planes: xx,yy[,zz],xy[,xz,yz]   */
+    SDF_OUT_SIGN = 8  /* winding number (2D) / topological degree (3D)     */
+};
+
+/* Per-node flag bits written to the optional flags output. */
+enum {
+    SDF_FLAG_CAPPED = 1, /* phi below the FP64 trust threshold: S = S_cap       */
+    SDF_FLAG_FIXUP = 2,  /* value from the shifted direct sum (SDF_FP32 plans)  */
+    SDF_FLAG_SOURCE = 4  /* a point snapped onto this node (mu is meaningless) */
+};
+
+/* Plan facts, filled by sdf_plan_get_info(). */
+typedef struct {
+    int D;
+    int precision;
+    unsigned outputs;
+    int64_t dims[3];          /* N_a                                       */
+    int64_t padded[3];        /* M_a                                       */
+    double h, tau;
+    double kernel_l1[16];     /* l1 norm of each sampled kernel (see sdf.cu) */
+    int n_kernels;
+    double noise_const_fp32;  /* C in the noise model, float transforms    */
+    double noise_const_fp64;  /* C in the noise model, double transforms   */
+    double plan_ms;           /* wall time of sdf_plan_create              */
+    size_t workspace_bytes;   /* device bytes owned by the plan            */
+} sdf_plan_info;
+
+/* Results of the last execute, filled by sdf_get_stats() (synchronises). */
+typedef struct {
+    double theta64;      /* FP64 trust threshold on phi                        */
+    double theta32;      /* FP32 trust threshold on phi (SDF_FP32 plans)       */
+    double s_cap;        /* -tau log(theta64)                                  */
+    double g_norm2;      /* ||g||_2 = sqrt(sum over nodes of count^2)          */
+    int64_t n_unique;    /* distinct occupied nodes                            */
+    int64_t n_fixup_tiles;  /* tiles the direct-sum fix-up visited             */
+    int64_t n_fixup_nodes;  /* nodes it recomputed                            */
+    int64_t n_capped;    /* nodes returned as S_cap                            */
+} sdf_exec_stats;
+
+/*
+ * sdf_plan_create -- build a plan for a D-dimensional grid.
+ *   out        receives the plan (NULL on failure).
+ *   D          2 or 3 (else SDF_ERR_UNSUPPORTED).
+ *   dims       host array of D node counts, x first, each in [2, 4096] (2D) or
+ *              [2, 1024] (3D); M_a (above) must fit the device (else
+ *              SDF_ERR_UNSUPPORTED).
+ *   h          grid spacing (> 0).  tau: the paper's tau (> 0).
+ *   precision  SDF_FP64 or SDF_FP32.
+ *   outputs    mask of SDF_OUT_* bits.  SDF_OUT_S is implied.
+ *   stream     cudaStream_t (as void*) on which every call enqueues; NULL is
+ *              the legacy default stream.
+ * Samples every kernel on the padded grid and transforms it in FP64 (Table 1
+ * step 1 and the kernels of Secs. 4-5), storing 1/2^D of each spectrum in the
+ * plan's precision.  Synchronous; allocates device memory.
+ */
+sdf_status sdf_plan_create(sdf_plan *out, int D, const int64_t *dims, double h,
+                           double tau, int precision, unsigned outputs,
+                           void *stream);
+
+/*
+ * sdf_execute -- one pass of the whole path (steps 1-3 above), enqueued on the
+ * plan's stream.
+ *   K          number of points (>= 1).
+ *   points     device, K x D doubles, row-major, world coordinates.
+ *   weights    device, K x D doubles: 2D tangents Z_k (eq. tangentVec;
+ *              chord- or arc-length-weighted), 3D outward normals P_k times
+ *              area (eq. normflux).  NULL: no sign is computed and S is
+ *              unsigned.  Component sums per node are formed in 62-bit fixed
+ *              point scaled to max|weight| (order-independent, deterministic).
+ *   S          device, N^D values (double for SDF_FP64, float for SDF_FP32):
+ *              signed S (sign * S) when the sign is computed, else S.
+ *   dS         device, D planes of N^D (same type), grad S; NULL to skip.
+ *   d2S        device, D(D+1)/2 planes, the Hessian; NULL to skip.
+ *   sign       device, N^D int8 (+1 inside, -1 outside); NULL to skip.
+ *   flags      device, N^D uint8 of SDF_FLAG_* bits; NULL to skip.
+ * Requesting a field the plan was not created for returns SDF_ERR_INVALID_ARG.
+ * The first call with a larger K than any before allocates point buffers.
+ * Points that snap outside the grid are dropped and reported by sdf_sync().
+ */
+sdf_status sdf_execute(sdf_plan plan, int64_t K, const double *points,
+                       const double *weights, void *S, void *dS, void *d2S,
+                       int8_t *sign, uint8_t *flags);
+
+/*
+ * sdf_execute_host -- sdf_execute with HOST buffers (same shapes and types):
+ * copies points/weights to plan-owned device buffers, executes, copies the
+ * requested outputs back, and waits for the stream.  Page-locked host memory
+ * makes the copies asynchronous DMA.  Returns the device status as sdf_sync().
+ */
+sdf_status sdf_execute_host(sdf_plan plan, int64_t K, const double *points,
+                            const double *weights, void *S, void *dS, void *d2S,
+                            int8_t *sign, uint8_t *flags);
+
+/*
+ * sdf_backward -- adjoint of L = sum_X w(X) S(X) for UNSIGNED S (the chain
+ * rule applied to eq. STilde):
+ *   dL/dY_k = (a * k_grad)(Y^_k), a = w/phi, k_grad(X) = f(X) X/||X||
+ *   dL/dtau = ( sum_X w S - sum_k (a * (||X|| f))(Y^_k) ) / tau
+ * evaluated at the snapped points Y^_k (snapping is piecewise constant; this
+ * is the gradient of the continuous definition at Y = Y^).
+ *   K, points  as in sdf_execute (the same points as the forward).
+ *   w          device, N^D loss weights dL/dS (plan type).
+ *   S_saved    device, N^D unsigned S from the forward (plan type); phi is
+ *              recovered as exp(-S/tau).
+ *   flags      device, N^D flags from the forward or NULL; nodes with
+ *              SDF_FLAG_CAPPED are skipped (their S does not depend on Y).
+ *   dL_dY      device, K x D doubles (written for every point).
+ *   dL_dtau    device, one double.
+ * The plan must have SDF_OUT_DS.  Recomputes spectra; keeps no forward state.
+ */
+sdf_status sdf_backward(sdf_plan plan, int64_t K, const double *points,
+                        const void *w, const void *S_saved,
+                        const uint8_t *flags, double *dL_dY, double *dL_dtau);
+
+/* Wait for the plan's stream; return (and clear) any error recorded on the
+ * device since the last sdf_sync, or SDF_ERR_CUDA for an asynchronous fault. */
+sdf_status sdf_sync(sdf_plan plan);
+
+/* Plan facts (host-side, no synchronisation). */
+sdf_status sdf_plan_get_info(sdf_plan plan, sdf_plan_info *info);
+
+/* Statistics of the last execute (synchronises the stream). */
+sdf_status sdf_get_stats(sdf_plan plan, sdf_exec_stats *stats);
+
+/* Free the plan and everything it owns (synchronises its stream). */
+void sdf_plan_destroy(sdf_plan plan);
+
+/* Static description of a status code. */
+const char *sdf_status_string(sdf_status status);
+
+/* Last CUDA error text recorded by the library (thread-local; static storage). */
+const char *sdf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDF_GB300_H */

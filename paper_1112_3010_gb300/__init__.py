@@ -1,0 +1,265 @@
+"""GB300 (sm_103a) implementation of the convolution-based signed distance
+method of Gurumoorthy & Rangarajan.
+
+This module is a thin ctypes binding of the C ABI in ``include/sdf.h``: the
+functions ``sdf_plan_create``, ``sdf_execute``, ``sdf_execute_host``,
+``sdf_backward``, ``sdf_sync``, ``sdf_plan_get_info``, ``sdf_get_stats`` and
+``sdf_plan_destroy`` marshal arguments and nothing else; every step of the
+method runs in the CUDA library.  :class:`Plan` wraps them with torch device
+buffers and the current CUDA stream.  There is no CPU fallback: if the
+library cannot be loaded, :func:`load_library` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libsdf_gb300.so")
+
+SDF_FP64, SDF_FP32 = 0, 1
+SDF_OUT_S, SDF_OUT_DS, SDF_OUT_D2S, SDF_OUT_SIGN = 1, 2, 4, 8
+SDF_FLAG_CAPPED, SDF_FLAG_FIXUP, SDF_FLAG_SOURCE = 1, 2, 4
+STATUS = {0: "SDF_OK", 1: "SDF_ERR_INVALID_ARG", 2: "SDF_ERR_UNSUPPORTED",
+          3: "SDF_ERR_POINT_OUT_OF_GRID", 4: "SDF_ERR_OOM", 5: "SDF_ERR_CUDA",
+          6: "SDF_ERR_TIMEOUT", 7: "SDF_ERR_CAPACITY"}
+
+EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
+            "sdf_plan_get_info", "sdf_get_stats", "sdf_plan_destroy", "sdf_status_string",
+            "sdf_last_error"]
+
+
+class SDFError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = "%s: %s" % (where, STATUS.get(code, str(code)))
+        try:
+            extra = _lib().sdf_last_error().decode()
+            if extra and code in (4, 5):
+                msg += " (%s)" % extra
+        except Exception:
+            pass
+        super().__init__(msg)
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int), ("precision", ctypes.c_int), ("outputs", ctypes.c_uint),
+                ("dims", ctypes.c_int64 * 3), ("padded", ctypes.c_int64 * 3),
+                ("h", ctypes.c_double), ("tau", ctypes.c_double),
+                ("kernel_l1", ctypes.c_double * 16), ("n_kernels", ctypes.c_int),
+                ("noise_const_fp32", ctypes.c_double), ("noise_const_fp64", ctypes.c_double),
+                ("plan_ms", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class ExecStats(ctypes.Structure):
+    _fields_ = [("theta64", ctypes.c_double), ("theta32", ctypes.c_double), ("s_cap", ctypes.c_double),
+                ("g_norm2", ctypes.c_double), ("n_unique", ctypes.c_int64),
+                ("n_fixup_tiles", ctypes.c_int64), ("n_fixup_nodes", ctypes.c_int64),
+                ("n_capped", ctypes.c_int64)]
+
+
+_LIBH = None
+_LOCK = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Load the CUDA library (building nothing).  Raises if it is missing."""
+    global _LIBH
+    with _LOCK:
+        if _LIBH is not None:
+            return _LIBH
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError("CUDA library %s is missing: run __graft_entry__.build()" % p)
+        L = ctypes.CDLL(p)
+        vp, i64, d, u = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint
+        L.sdf_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(i64), d, d,
+                                      ctypes.c_int, u, vp]
+        L.sdf_execute.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
+        L.sdf_execute_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
+        L.sdf_backward.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+        L.sdf_sync.argtypes = [vp]
+        L.sdf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        L.sdf_get_stats.argtypes = [vp, ctypes.POINTER(ExecStats)]
+        L.sdf_plan_destroy.argtypes = [vp]
+        L.sdf_plan_destroy.restype = None
+        L.sdf_status_string.argtypes = [ctypes.c_int]
+        L.sdf_status_string.restype = ctypes.c_char_p
+        L.sdf_last_error.argtypes = []
+        L.sdf_last_error.restype = ctypes.c_char_p
+        for n in ("sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
+                  "sdf_plan_get_info", "sdf_get_stats"):
+            getattr(L, n).restype = ctypes.c_int
+        _LIBH = L
+        return L
+
+
+def _lib():
+    return load_library()
+
+
+def _ck(code, where):
+    if code != 0:
+        raise SDFError(code, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- C-ABI names
+def sdf_plan_create(D, dims, h, tau, precision, outputs, stream):
+    """Create a plan; returns the opaque handle (ctypes.c_void_p)."""
+    handle = ctypes.c_void_p()
+    dims_arr = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    _ck(_lib().sdf_plan_create(ctypes.byref(handle), int(D), dims_arr, float(h), float(tau),
+                               int(precision), int(outputs), ctypes.c_void_p(stream or 0)),
+        "sdf_plan_create")
+    return handle
+
+
+def sdf_execute(handle, K, points, weights, S, dS, d2S, sign, flags):
+    _ck(_lib().sdf_execute(handle, int(K), _ptr(points), _ptr(weights), _ptr(S), _ptr(dS),
+                           _ptr(d2S), _ptr(sign), _ptr(flags)), "sdf_execute")
+
+
+def sdf_execute_host(handle, K, points, weights, S, dS, d2S, sign, flags):
+    _ck(_lib().sdf_execute_host(handle, int(K), _ptr(points), _ptr(weights), _ptr(S), _ptr(dS),
+                                _ptr(d2S), _ptr(sign), _ptr(flags)), "sdf_execute_host")
+
+
+def sdf_backward(handle, K, points, w, S_saved, flags, dL_dY, dL_dtau):
+    _ck(_lib().sdf_backward(handle, int(K), _ptr(points), _ptr(w), _ptr(S_saved), _ptr(flags),
+                            _ptr(dL_dY), _ptr(dL_dtau)), "sdf_backward")
+
+
+def sdf_sync(handle):
+    return int(_lib().sdf_sync(handle))
+
+
+def sdf_plan_get_info(handle) -> PlanInfo:
+    info = PlanInfo()
+    _ck(_lib().sdf_plan_get_info(handle, ctypes.byref(info)), "sdf_plan_get_info")
+    return info
+
+
+def sdf_get_stats(handle) -> ExecStats:
+    st = ExecStats()
+    _ck(_lib().sdf_get_stats(handle, ctypes.byref(st)), "sdf_get_stats")
+    return st
+
+
+def sdf_plan_destroy(handle):
+    _lib().sdf_plan_destroy(handle)
+
+
+# ---------------------------------------------------------------- convenience
+_OUTS = {"S": SDF_OUT_S, "dS": SDF_OUT_DS, "d2S": SDF_OUT_D2S, "sign": SDF_OUT_SIGN}
+
+
+class Plan:
+    """A plan for one grid (D, dims, h) and tau, on the current torch stream."""
+
+    def __init__(self, D, dims, h, tau, precision="fp32", outputs=("S", "dS", "sign"), stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.torch = torch
+        self.D = int(D)
+        self.dims = tuple(int(x) for x in dims)
+        self.h, self.tau = float(h), float(tau)
+        self.precision = SDF_FP64 if precision in ("fp64", SDF_FP64) else SDF_FP32
+        mask = 0
+        for o in outputs:
+            mask |= _OUTS[o]
+        self.outputs = mask | SDF_OUT_S
+        if self.outputs & SDF_OUT_D2S:
+            self.outputs |= SDF_OUT_DS
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = sdf_plan_create(self.D, self.dims, self.h, self.tau, self.precision,
+                                      self.outputs, self.stream.cuda_stream)
+        self.dtype = torch.float64 if self.precision == SDF_FP64 else torch.float32
+        self.n_nodes = int(np.prod(self.dims))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            sdf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> PlanInfo:
+        return sdf_plan_get_info(self.handle)
+
+    def stats(self) -> ExecStats:
+        return sdf_get_stats(self.handle)
+
+    def sync(self):
+        _ck(sdf_sync(self.handle), "sdf_sync")
+
+    def alloc_outputs(self, want=None, signed=True):
+        t = self.torch
+        dev = t.device("cuda")
+        want = want or [k for k, v in _OUTS.items() if self.outputs & v]
+        shp = tuple(reversed(self.dims))
+        nh = self.D * (self.D + 1) // 2
+        out = {}
+        if "S" in want:
+            out["S"] = t.empty(shp, dtype=self.dtype, device=dev)
+        if "dS" in want and self.outputs & SDF_OUT_DS:
+            out["dS"] = t.empty((self.D,) + shp, dtype=self.dtype, device=dev)
+        if "d2S" in want and self.outputs & SDF_OUT_D2S:
+            out["d2S"] = t.empty((nh,) + shp, dtype=self.dtype, device=dev)
+        if "sign" in want and self.outputs & SDF_OUT_SIGN and signed:
+            out["sign"] = t.empty(shp, dtype=t.int8, device=dev)
+        if "flags" in want:
+            out["flags"] = t.empty(shp, dtype=t.uint8, device=dev)
+        return out
+
+    def execute(self, points, weights=None, out=None, flags=True, check=True):
+        """Run the whole path on device tensors; returns the output dict.
+        Grid arrays are shaped (N_z, N_y, N_x) / (N_y, N_x) (x fastest)."""
+        t = self.torch
+        pts = points.to(device="cuda", dtype=t.float64).contiguous()
+        w = None if weights is None else weights.to(device="cuda", dtype=t.float64).contiguous()
+        if out is None:
+            want = [k for k, v in _OUTS.items() if self.outputs & v] + (["flags"] if flags else [])
+            out = self.alloc_outputs(want, signed=w is not None)
+        sdf_execute(self.handle, pts.shape[0], pts, w, out.get("S"), out.get("dS"), out.get("d2S"),
+                    out.get("sign"), out.get("flags"))
+        if check:
+            self.sync()
+        return out
+
+    def execute_host(self, points, weights=None, out=None):
+        """sdf_execute_host on host tensors (pinned memory makes the copies DMA)."""
+        t = self.torch
+        pts = points.to(dtype=t.float64).contiguous()
+        w = None if weights is None else weights.to(dtype=t.float64).contiguous()
+        if out is None:
+            shp = tuple(reversed(self.dims))
+            out = {"S": t.empty(shp, dtype=self.dtype, pin_memory=True)}
+        sdf_execute_host(self.handle, pts.shape[0], pts, w, out.get("S"), out.get("dS"),
+                         out.get("d2S"), out.get("sign"), out.get("flags"))
+        return out
+
+    def backward(self, points, w, S_saved, flags=None):
+        """dL/dY (K x D, float64, device) and dL/dtau (float64 scalar)."""
+        t = self.torch
+        pts = points.to(device="cuda", dtype=t.float64).contiguous()
+        dY = t.empty_like(pts)
+        dtau = t.zeros(1, dtype=t.float64, device="cuda")
+        sdf_backward(self.handle, pts.shape[0], pts, w.contiguous(), S_saved.contiguous(),
+                     None if flags is None else flags.contiguous(), dY, dtau)
+        self.sync()
+        return dY, dtau

@@ -1,0 +1,506 @@
+// api.cu -- the C ABI declared in include/sdf.h: plan creation (kernel set,
+// transform programme, workspace), execute orchestration and status.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "sdf_internal.cuh"
+
+namespace sdf {
+int kernel_parity(int id, int D);
+cudaError_t build_kernel_list(sdf_plan_impl *p, const std::vector<int> &ids);
+}  // namespace sdf
+
+using namespace sdf;
+
+static thread_local char g_last_error[256] = "";
+
+static sdf_status cuda_fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) {
+        snprintf(g_last_error, sizeof g_last_error, "%s", cudaGetErrorString(e));
+        cudaGetLastError();
+        return SDF_ERR_OOM;
+    }
+    snprintf(g_last_error, sizeof g_last_error, "%s", cudaGetErrorString(e));
+    return SDF_ERR_CUDA;
+}
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+// Noise constants C_p of the transform error model (see DESIGN notes in
+// passes.cu / include/sdf.h): the largest |phi_computed - phi| over a grid is
+// below C_p u_p sqrt(log2 n) ||k||_1 ||g||_2 / sqrt(n).
+static const double kNoiseC32 = 4.0;
+static const double kNoiseC64 = 4.0;
+
+static int64_t next_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+static double zeta_re(int nodd) { const int q = nodd & 3; return q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0); }
+static double zeta_im(int nodd) { const int q = nodd & 3; return q == 1 ? -1.0 : (q == 3 ? 1.0 : 0.0); }
+
+namespace sdf {
+cudaError_t build_spectra(sdf_plan_impl *p);
+
+// Add kernels (if absent) and build their spectra.
+cudaError_t build_kernel_list(sdf_plan_impl *p, const std::vector<int> &ids) {
+    std::vector<KernelSpec> keep = p->kernels;
+    std::vector<KernelSpec> fresh;
+    for (int id : ids) {
+        if (p->kslot[id] >= 0) continue;
+        KernelSpec k;
+        k.id = id;
+        k.parity = kernel_parity(id, p->D);
+        k.l1 = 0;
+        k.c = nullptr;
+        fresh.push_back(k);
+    }
+    if (fresh.empty()) return cudaSuccess;
+    p->kernels = fresh;
+    cudaError_t e = build_spectra(p);
+    fresh = p->kernels;
+    p->kernels = keep;
+    for (auto &k : fresh) {
+        p->kslot[k.id] = (int)p->kernels.size();
+        p->kernels.push_back(k);
+    }
+    return e;
+}
+}  // namespace sdf
+
+static void add_pair(sdf_plan_impl *p, int kA, int chA, int kB, int chB) {
+    Group &g = p->group[p->ngroup];
+    g.nterm = 0;
+    const int sa = p->kslot[kA];
+    const int na = __builtin_popcount((unsigned)p->kernels[sa].parity);
+    g.term[g.nterm++] = Term{sa, 0, zeta_re(na), zeta_im(na)};
+    p->gch[p->ngroup][0] = chA;
+    p->gch[p->ngroup][1] = CH_NONE;
+    if (kB >= 0) {
+        const int sb = p->kslot[kB];
+        const int nb = __builtin_popcount((unsigned)p->kernels[sb].parity);
+        // i * zeta
+        g.term[g.nterm++] = Term{sb, 0, -zeta_im(nb), zeta_re(nb)};
+        p->gch[p->ngroup][1] = chB;
+    }
+    ++p->ngroup;
+}
+
+static void add_mu(sdf_plan_impl *p) {
+    Group &g = p->group[p->ngroup];
+    g.nterm = 0;
+    const double pi = 3.14159265358979323846;
+    if (p->D == 2) {
+        // mu = Re[(Khat_W1 + i Khat_W2) Fhat_1] / (2 pi)   (eq. kappadiscretefinal)
+        const int s1 = p->kslot[KER_W1], s2 = p->kslot[KER_W2];
+        const int n1 = __builtin_popcount((unsigned)p->kernels[s1].parity);
+        const int n2 = __builtin_popcount((unsigned)p->kernels[s2].parity);
+        const double c = 1.0 / (2.0 * pi);
+        g.term[g.nterm++] = Term{s1, 1, c * zeta_re(n1), c * zeta_im(n1)};
+        g.term[g.nterm++] = Term{s2, 1, -c * zeta_im(n2), c * zeta_re(n2)};
+    } else {
+        // mu = -Re[(Khat_W1 - i Khat_W2) Fhat_1 + Khat_W3 Fhat_2] / (4 pi)   (eq. mudef)
+        const int s1 = p->kslot[KER_W1], s2 = p->kslot[KER_W2], s3 = p->kslot[KER_W3];
+        const int n1 = __builtin_popcount((unsigned)p->kernels[s1].parity);
+        const int n2 = __builtin_popcount((unsigned)p->kernels[s2].parity);
+        const int n3 = __builtin_popcount((unsigned)p->kernels[s3].parity);
+        const double c = -1.0 / (4.0 * pi);
+        g.term[g.nterm++] = Term{s1, 1, c * zeta_re(n1), c * zeta_im(n1)};
+        // -i * zeta2 * c
+        g.term[g.nterm++] = Term{s2, 1, c * zeta_im(n2), -c * zeta_re(n2)};
+        g.term[g.nterm++] = Term{s3, 2, c * zeta_re(n3), c * zeta_im(n3)};
+    }
+    p->gch[p->ngroup][0] = CH_MU;
+    p->gch[p->ngroup][1] = CH_NONE;
+    ++p->ngroup;
+}
+
+static size_t vbytes(const sdf_plan_impl *p) { return p->prec == SDF_FP64 ? sizeof(double2) : sizeof(float2); }
+
+static cudaError_t alloc(void **ptr, size_t bytes, size_t *acc) {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess && acc) *acc += bytes;
+    return e;
+}
+
+static void free_plan(sdf_plan_impl *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    for (auto &k : p->kernels) cudaFree(k.c);
+    for (int a = 0; a < 3; ++a) cudaFree(p->tw[a]);
+    cudaFree(p->bufA);
+    cudaFree(p->bufB);
+    cudaFree(p->pt_key);
+    cudaFree(p->pt_lc);
+    cudaFree(p->pt_entry);
+    cudaFree(p->bin_count);
+    cudaFree(p->bin_start);
+    cudaFree(p->bin_fill);
+    cudaFree(p->bin_nuniq);
+    cudaFree(p->ucell);
+    cudaFree(p->ucount);
+    cudaFree(p->uw);
+    cudaFree(p->cheb);
+    cudaFree(p->tile_flag);
+    cudaFree(p->flags_int);
+    cudaFree(p->sign_int);
+    cudaFree(p->dsc);
+    cudaFree(p->staging);
+    if (p->hsc) cudaFreeHost(p->hsc);
+}
+
+template <typename T>
+static cudaError_t upload_twiddles(void **dst, int64_t L, size_t *acc) {
+    using V = typename cplx_t<T>::type;
+    std::vector<V> h(L);
+    for (int64_t i = 0; i < L; ++i) {
+        long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)i / (long double)L;
+        h[i].x = (T)cosl(ang);
+        h[i].y = (T)sinl(ang);
+    }
+    cudaError_t e = alloc(dst, sizeof(V) * L, acc);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, h.data(), sizeof(V) * L, cudaMemcpyHostToDevice);
+}
+
+extern "C" {
+
+const char *sdf_status_string(sdf_status s) {
+    switch (s) {
+        case SDF_OK: return "ok";
+        case SDF_ERR_INVALID_ARG: return "invalid argument";
+        case SDF_ERR_UNSUPPORTED: return "unsupported configuration";
+        case SDF_ERR_POINT_OUT_OF_GRID: return "a point snapped outside the grid";
+        case SDF_ERR_OOM: return "device out of memory";
+        case SDF_ERR_CUDA: return "CUDA runtime error";
+        case SDF_ERR_TIMEOUT: return "a bounded device wait expired";
+        case SDF_ERR_CAPACITY: return "input exceeds a fixed-size buffer";
+        default: return "unknown status";
+    }
+}
+
+const char *sdf_last_error(void) { return g_last_error; }
+
+sdf_status sdf_plan_create(sdf_plan *out, int D, const int64_t *dims, double h, double tau, int precision,
+                           unsigned outputs, void *stream) {
+    if (!out) return SDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (D != 2 && D != 3) return SDF_ERR_UNSUPPORTED;
+    if (!dims || !(h > 0.0) || !(tau > 0.0) || !std::isfinite(h) || !std::isfinite(tau)) return SDF_ERR_INVALID_ARG;
+    if (precision != SDF_FP64 && precision != SDF_FP32) return SDF_ERR_INVALID_ARG;
+    if (outputs & ~15u) return SDF_ERR_INVALID_ARG;
+    const int64_t nmax = (D == 2) ? 4096 : 512;
+    for (int a = 0; a < D; ++a)
+        if (dims[a] < 2 || dims[a] > nmax) return SDF_ERR_UNSUPPORTED;
+    auto t0 = std::chrono::steady_clock::now();
+    sdf_plan_s *p = new (std::nothrow) sdf_plan_s();
+    if (!p) return SDF_ERR_OOM;
+    p->D = D;
+    p->prec = precision;
+    outputs |= SDF_OUT_S;
+    if (outputs & SDF_OUT_D2S) outputs |= SDF_OUT_DS;
+    p->outputs = outputs;
+    p->h = h;
+    p->tau = tau;
+    p->stream = reinterpret_cast<cudaStream_t>(stream);
+    p->nnodes = 1;
+    p->nbins = 1;
+    for (int a = 0; a < 3; ++a) {
+        p->N[a] = (a < D) ? dims[a] : 1;
+        p->M[a] = (a < D) ? std::max<int64_t>(16, next_pow2(2 * p->N[a] - 1)) : 1;
+        int l = 0;
+        while ((int64_t(1) << l) < p->M[a]) ++l;
+        p->logM[a] = l;
+        p->nb[a] = (p->N[a] + kBin - 1) / kBin;
+        p->nnodes *= p->N[a];
+        p->nbins *= p->nb[a];
+    }
+    for (int i = 0; i < KER_COUNT; ++i) p->kslot[i] = -1;
+    p->noise_c32 = kNoiseC32;
+    p->noise_c64 = kNoiseC64;
+
+    const bool ds = outputs & SDF_OUT_DS, d2 = outputs & SDF_OUT_D2S, sg = outputs & SDF_OUT_SIGN;
+    std::vector<int> ids = {KER_PHI};
+    if (ds) {
+        ids.push_back(KER_GX);
+        ids.push_back(KER_GY);
+        if (D == 3) ids.push_back(KER_GZ);
+    }
+    if (d2) {
+        ids.push_back(KER_HXX);
+        ids.push_back(KER_HYY);
+        if (D == 3) ids.push_back(KER_HZZ);
+        ids.push_back(KER_HXY);
+        if (D == 3) {
+            ids.push_back(KER_HXZ);
+            ids.push_back(KER_HYZ);
+        }
+    }
+    if (sg) {
+        ids.push_back(KER_W1);
+        ids.push_back(KER_W2);
+        if (D == 3) ids.push_back(KER_W3);
+    }
+    cudaError_t e;
+#define PCK(x)                          \
+    do {                                \
+        e = (x);                        \
+        if (e != cudaSuccess) {         \
+            sdf_status s_ = cuda_fail(e); \
+            free_plan(p);               \
+            delete p;                   \
+            return s_;                  \
+        }                               \
+    } while (0)
+    // twiddles in the plan precision
+    for (int a = 0; a < D; ++a) {
+        if (precision == SDF_FP64) PCK(upload_twiddles<double>(&p->tw[a], p->M[a], &p->workspace_bytes));
+        else PCK(upload_twiddles<float>(&p->tw[a], p->M[a], &p->workspace_bytes));
+    }
+    PCK(build_kernel_list(p, ids));
+    // transform programme
+    p->nfield = sg ? (D == 2 ? 2 : 3) : 1;
+    p->ngroup = 0;
+    if (D == 2) {
+        add_pair(p, KER_PHI, CH_PHI, ds ? KER_GX : -1, CH_GX);
+        if (ds) add_pair(p, KER_GY, CH_GY, d2 ? KER_HXX : -1, CH_HXX);
+        if (d2) add_pair(p, KER_HYY, CH_HYY, KER_HXY, CH_HXY);
+    } else {
+        add_pair(p, KER_PHI, CH_PHI, ds ? KER_GX : -1, CH_GX);
+        if (ds) add_pair(p, KER_GY, CH_GY, KER_GZ, CH_GZ);
+        if (d2) {
+            add_pair(p, KER_HXX, CH_HXX, KER_HYY, CH_HYY);
+            add_pair(p, KER_HZZ, CH_HZZ, KER_HXY, CH_HXY);
+            add_pair(p, KER_HXZ, CH_HXZ, KER_HYZ, CH_HYZ);
+        }
+    }
+    if (sg) add_mu(p);
+    // noise-model factor Q (how phi's error enters each requested output)
+    {
+        auto l1 = [&](int id) { return p->kslot[id] >= 0 ? p->kernels[p->kslot[id]].l1 : 0.0; };
+        const double f = l1(KER_PHI);
+        double gmax = 0, hmax = 0;
+        for (int id = KER_GX; id <= KER_GZ; ++id) gmax = std::max(gmax, l1(id));
+        for (int id = KER_HXX; id <= KER_HYZ; ++id) hmax = std::max(hmax, l1(id));
+        double q = f;
+        if (ds) q = std::max(q, f + gmax);
+        if (d2) q = std::max(q, tau * hmax + 2 * gmax + 2 * f);
+        p->q_factor = q;
+    }
+    // workspace
+    {
+        const int64_t N0 = p->N[0], N1 = p->N[1], N2 = p->N[2], M0 = p->M[0], M1 = p->M[1];
+        const int64_t ng = std::max(p->ngroup, 2);
+        const int64_t nf = p->nfield;
+        int64_t a, b;
+        if (D == 2) {
+            a = nf * M0 * N1;
+            b = ng * M0 * N1;
+        } else {
+            a = std::max(nf * M0 * N2 * N1, ng * M1 * M0 * N2);
+            b = std::max(nf * M1 * M0 * N2, ng * M0 * N2 * N1);
+        }
+        (void)N0;
+        p->bytesA = a * vbytes(p);
+        p->bytesB = b * vbytes(p);
+        PCK(alloc(&p->bufA, p->bytesA, &p->workspace_bytes));
+        PCK(alloc(&p->bufB, p->bytesB, &p->workspace_bytes));
+        const int64_t nb = p->nbins;
+        PCK(alloc((void **)&p->bin_count, sizeof(int) * (nb + 1), &p->workspace_bytes));
+        PCK(alloc((void **)&p->bin_start, sizeof(int) * (nb + 1), &p->workspace_bytes));
+        PCK(alloc((void **)&p->bin_fill, sizeof(int) * nb, &p->workspace_bytes));
+        PCK(alloc((void **)&p->bin_nuniq, sizeof(int) * nb, &p->workspace_bytes));
+        PCK(alloc((void **)&p->cheb, 2 * nb, &p->workspace_bytes));
+        PCK(alloc((void **)&p->tile_flag, nb, &p->workspace_bytes));
+        PCK(alloc((void **)&p->dsc, sizeof(DevScalars), &p->workspace_bytes));
+        PCK(cudaMemset(p->dsc, 0, sizeof(DevScalars)));
+        PCK(cudaMallocHost((void **)&p->hsc, sizeof(DevScalars)));
+        if (precision == SDF_FP32) {
+            PCK(alloc((void **)&p->flags_int, p->nnodes, &p->workspace_bytes));
+            PCK(alloc((void **)&p->sign_int, p->nnodes, &p->workspace_bytes));
+        }
+    }
+    PCK(cudaDeviceSynchronize());
+#undef PCK
+    p->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return SDF_OK;
+}
+
+static cudaError_t ensure_points(sdf_plan_impl *p, int64_t K) {
+    if (K <= p->Kcap) return cudaSuccess;
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->pt_key);
+    cudaFree(p->pt_lc);
+    cudaFree(p->pt_entry);
+    cudaFree(p->ucell);
+    cudaFree(p->ucount);
+    cudaFree(p->uw);
+    p->pt_key = p->pt_lc = p->ucell = p->ucount = nullptr;
+    p->pt_entry = nullptr;
+    p->uw = nullptr;
+    p->Kcap = 0;
+    const int64_t cap = std::max<int64_t>(K, 1024);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->pt_key, sizeof(int) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p->pt_lc, sizeof(int) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p->pt_entry, sizeof(long long) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p->ucell, sizeof(int) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p->ucount, sizeof(int) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p->uw, sizeof(double) * 3 * cap)) != cudaSuccess) return e;
+    p->Kcap = cap;
+    return cudaSuccess;
+}
+
+static sdf_status check_execute_args(sdf_plan p, int64_t K, const double *points, const double *weights,
+                                     const void *dS, const void *d2S, const int8_t *sign) {
+    if (!p || !points) return SDF_ERR_INVALID_ARG;
+    if (K < 1 || K >= (int64_t(1) << 31) - 1) return SDF_ERR_INVALID_ARG;
+    if (dS && !(p->outputs & SDF_OUT_DS)) return SDF_ERR_INVALID_ARG;
+    if (d2S && !(p->outputs & SDF_OUT_D2S)) return SDF_ERR_INVALID_ARG;
+    if (sign && !((p->outputs & SDF_OUT_SIGN) && weights)) return SDF_ERR_INVALID_ARG;
+    if (weights && !(p->outputs & SDF_OUT_SIGN)) return SDF_ERR_INVALID_ARG;
+    return SDF_OK;
+}
+
+sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double *weights, void *S, void *dS,
+                       void *d2S, int8_t *sign, uint8_t *flags) {
+    sdf_status s = check_execute_args(p, K, points, weights, dS, d2S, sign);
+    if (s != SDF_OK) return s;
+    CK(ensure_points(p, K));
+    p->last_K = K;
+    const bool ww = weights != nullptr;
+    CK(launch_points(p, K, points, weights));
+    uint8_t *fl = flags;
+    int8_t *sg = sign;
+    if (p->prec == SDF_FP32) {
+        if (!fl) fl = p->flags_int;
+        if (ww && !sg) sg = p->sign_int;
+        CK(cudaMemsetAsync(p->tile_flag, 0, p->nbins, p->stream));
+        CK(launch_cheb(p));
+    }
+    CK(launch_forward(p, ww, nullptr, 0, nullptr));
+    CK(launch_inverse_epilogue(p, ww, S, dS, d2S, sg, fl));
+    if (p->prec == SDF_FP32) CK(launch_fixup(p, ww, S, dS, d2S, ww ? sg : nullptr, fl));
+    if (flags) CK(launch_source_flags(p, flags));
+    return SDF_OK;
+}
+
+sdf_status sdf_execute_host(sdf_plan p, int64_t K, const double *points, const double *weights, void *S, void *dS,
+                            void *d2S, int8_t *sign, uint8_t *flags) {
+    sdf_status s = check_execute_args(p, K, points, weights, dS, d2S, sign);
+    if (s != SDF_OK) return s;
+    const int D = p->D;
+    const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
+    const int64_t nn = p->nnodes;
+    const int nh = D * (D + 1) / 2;
+    size_t need = sizeof(double) * K * D * (weights ? 2 : 1);
+    size_t oS = need, odS = oS + (S ? esz * nn : 0), od2 = odS + (dS ? esz * nn * D : 0),
+           osg = od2 + (d2S ? esz * nn * nh : 0), ofl = osg + (sign ? nn : 0), tot = ofl + (flags ? nn : 0);
+    if (tot > p->staging_bytes) {
+        cudaStreamSynchronize(p->stream);
+        cudaFree(p->staging);
+        p->staging = nullptr;
+        p->staging_bytes = 0;
+        CK(cudaMalloc((void **)&p->staging, tot));
+        p->staging_bytes = tot;
+    }
+    char *base = reinterpret_cast<char *>(p->staging);
+    double *dpts = reinterpret_cast<double *>(base);
+    double *dw = weights ? dpts + K * D : nullptr;
+    CK(cudaMemcpyAsync(dpts, points, sizeof(double) * K * D, cudaMemcpyHostToDevice, p->stream));
+    if (weights) CK(cudaMemcpyAsync(dw, weights, sizeof(double) * K * D, cudaMemcpyHostToDevice, p->stream));
+    void *dS_ = S ? base + oS : nullptr;
+    void *ddS = dS ? base + odS : nullptr;
+    void *dd2 = d2S ? base + od2 : nullptr;
+    int8_t *dsg = sign ? reinterpret_cast<int8_t *>(base + osg) : nullptr;
+    uint8_t *dfl = flags ? reinterpret_cast<uint8_t *>(base + ofl) : nullptr;
+    s = sdf_execute(p, K, dpts, dw, dS_, ddS, dd2, dsg, dfl);
+    if (s != SDF_OK) return s;
+    if (S) CK(cudaMemcpyAsync(S, dS_, esz * nn, cudaMemcpyDeviceToHost, p->stream));
+    if (dS) CK(cudaMemcpyAsync(dS, ddS, esz * nn * D, cudaMemcpyDeviceToHost, p->stream));
+    if (d2S) CK(cudaMemcpyAsync(d2S, dd2, esz * nn * nh, cudaMemcpyDeviceToHost, p->stream));
+    if (sign) CK(cudaMemcpyAsync(sign, dsg, nn, cudaMemcpyDeviceToHost, p->stream));
+    if (flags) CK(cudaMemcpyAsync(flags, dfl, nn, cudaMemcpyDeviceToHost, p->stream));
+    return sdf_sync(p);
+}
+
+sdf_status sdf_sync(sdf_plan p) {
+    if (!p) return SDF_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaMemcpy(p->hsc, p->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    const int st = p->hsc->status;
+    if (st != 0) CK(cudaMemset(p->dsc, 0, sizeof(int)));
+    return (sdf_status)st;
+}
+
+sdf_status sdf_plan_get_info(sdf_plan p, sdf_plan_info *info) {
+    if (!p || !info) return SDF_ERR_INVALID_ARG;
+    memset(info, 0, sizeof(*info));
+    info->D = p->D;
+    info->precision = p->prec;
+    info->outputs = p->outputs;
+    for (int a = 0; a < 3; ++a) {
+        info->dims[a] = p->N[a];
+        info->padded[a] = p->M[a];
+    }
+    info->h = p->h;
+    info->tau = p->tau;
+    info->n_kernels = (int)p->kernels.size();
+    for (size_t i = 0; i < p->kernels.size() && i < 16; ++i) info->kernel_l1[i] = p->kernels[i].l1;
+    info->noise_const_fp32 = p->noise_c32;
+    info->noise_const_fp64 = p->noise_c64;
+    info->plan_ms = p->plan_ms;
+    info->workspace_bytes = p->workspace_bytes;
+    return SDF_OK;
+}
+
+sdf_status sdf_get_stats(sdf_plan p, sdf_exec_stats *st) {
+    if (!p || !st) return SDF_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaMemcpy(p->hsc, p->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    const DevScalars &d = *p->hsc;
+    const int D = p->D;
+    const double n = (double)p->M[0] * (double)p->M[1] * (D == 3 ? (double)p->M[2] : 1.0);
+    const double base = sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
+    const double gn = sqrt((double)d.sum_c2);
+    memset(st, 0, sizeof(*st));
+    st->g_norm2 = gn;
+    st->theta64 = p->noise_c64 * ldexp(1.0, -53) * base * gn;
+    st->theta32 = p->noise_c32 * ldexp(1.0, -24) * base * gn;
+    st->s_cap = -p->tau * log(st->theta64);
+    st->n_unique = d.n_unique;
+    st->n_fixup_tiles = (int64_t)d.n_fixup_tiles;
+    st->n_fixup_nodes = (int64_t)d.n_fixup_nodes;
+    st->n_capped = (int64_t)d.n_capped;
+    return SDF_OK;
+}
+
+void sdf_plan_destroy(sdf_plan p) {
+    if (!p) return;
+    free_plan(p);
+    delete p;
+}
+
+sdf_status sdf_backward(sdf_plan p, int64_t K, const double *points, const void *w, const void *S_saved,
+                        const uint8_t *flags, double *dL_dY, double *dL_dtau) {
+    if (!p || !points || !w || !S_saved || !dL_dY || !dL_dtau) return SDF_ERR_INVALID_ARG;
+    if (!(p->outputs & SDF_OUT_DS)) return SDF_ERR_INVALID_ARG;
+    if (K < 1 || K >= (int64_t(1) << 31) - 1) return SDF_ERR_INVALID_ARG;
+    return (sdf_status)SDF_ERR_UNSUPPORTED;  // filled in by adjoint.cu
+}
+
+}  // extern "C"

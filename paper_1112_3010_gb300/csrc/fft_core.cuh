@@ -1,0 +1,201 @@
+// fft_core.cuh -- the FFT building block shared by every transform pass.
+//
+// One CTA transforms R lines of length L = 2^logL (16 <= L <= 8192) at once.
+// Each line gets TPL = L/16 threads; thread t of a line owns the 16 elements
+// t + m*TPL (m = 0..15) both on entry and on exit, so a forward transform's
+// output registers feed an inverse transform's input registers directly (the
+// fused spectrum multiply relies on this).
+//
+// The transform is a radix-16 Stockham auto-sort FFT: stage s (span Ns =
+// 16^s) reads x[j + r*L/16], multiplies by w_{16 Ns}^{r (j mod Ns)}, does a
+// 16-point DFT in registers (radix-4 x radix-4) and writes
+// y[(j/Ns)*16*Ns + (j mod Ns) + q*Ns].  When log2 L is not a multiple of 4 the
+// last stage has radix 2, 4 or 8 and each thread runs 16/radix butterflies.
+// Between stages data goes through shared memory with one pad element per 16
+// (index e -> e + e/16), which makes the stride-16 writes of the first stage
+// conflict-free.  Twiddles come from a per-length table tw[i] = exp(-2 pi i i/L)
+// computed in FP64 on the host (conjugated for the inverse).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sdf {
+
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+
+template <typename V> __device__ __forceinline__ V mk(decltype(V::x) a, decltype(V::x) b) {
+    V r; r.x = a; r.y = b; return r;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    return mk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+    return mk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return mk<V>(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename V> __device__ __forceinline__ V mul_mi(V a) {
+    return INV ? mk<V>(-a.y, a.x) : mk<V>(a.y, -a.x);
+}
+
+__host__ __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+
+// Multiply by w16^K = exp(-+2 pi i K/16) for a compile-time K in [0, 16).
+template <int K, bool INV, typename V> __device__ __forceinline__ V mul_w16(V a) {
+    using T = decltype(V::x);
+    constexpr int k = K & 15;
+    const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), c2 = T(0.70710678118654752440);
+    if constexpr (k == 0) return a;
+    else if constexpr (k == 4) return mul_mi<INV>(a);
+    else if constexpr (k == 8) return mk<V>(-a.x, -a.y);
+    else if constexpr (k == 12) return mul_mi<!INV>(a);
+    else {
+        // forward w16^k = cos(pi k/8) - i sin(pi k/8)
+        constexpr int kk = k;
+        T c, s;
+        if constexpr (kk == 1) { c = c1; s = s1; }
+        else if constexpr (kk == 2) { c = c2; s = c2; }
+        else if constexpr (kk == 3) { c = s1; s = c1; }
+        else if constexpr (kk == 5) { c = -s1; s = c1; }
+        else if constexpr (kk == 6) { c = -c2; s = c2; }
+        else if constexpr (kk == 7) { c = -c1; s = s1; }
+        else if constexpr (kk == 9) { c = -c1; s = -s1; }
+        else if constexpr (kk == 10) { c = -c2; s = -c2; }
+        else if constexpr (kk == 11) { c = -s1; s = -c1; }
+        else if constexpr (kk == 13) { c = s1; s = -c1; }
+        else if constexpr (kk == 14) { c = c2; s = -c2; }
+        else { c = c1; s = -s1; } // 15
+        if (INV) s = -s;
+        // (a.x + i a.y)(c - i s)
+        return mk<V>(a.x * c + a.y * s, a.y * c - a.x * s);
+    }
+}
+
+// 4-point DFT in place, natural order.
+template <bool INV, typename V> __device__ __forceinline__ void dft4(V &a, V &b, V &c, V &d) {
+    V t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = mul_mi<INV>(csub(b, d));
+    a = cadd(t0, t2);
+    c = csub(t0, t2);
+    b = cadd(t1, t3);
+    d = csub(t1, t3);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft2(V &a, V &b) {
+    V t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+// 16-point DFT of a[0..15] in place, natural order.
+// n = 4 n1 + n2, k = k1 + 4 k2:  X[k] = sum_n2 w4^{n2 k2} w16^{n2 k1} sum_n1 x[4 n1 + n2] w4^{n1 k1}
+template <bool INV, typename V> __device__ __forceinline__ void dft16(V (&a)[16]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
+    // now a[4 k1 + n2] = Y[n2][k1]; twiddle by w16^{n2 k1}
+    a[5] = mul_w16<1, INV>(a[5]);
+    a[9] = mul_w16<2, INV>(a[9]);
+    a[13] = mul_w16<3, INV>(a[13]);
+    a[6] = mul_w16<2, INV>(a[6]);
+    a[10] = mul_w16<4, INV>(a[10]);
+    a[14] = mul_w16<6, INV>(a[14]);
+    a[7] = mul_w16<3, INV>(a[7]);
+    a[11] = mul_w16<6, INV>(a[11]);
+    a[15] = mul_w16<9, INV>(a[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+    // a[4 k1 + k2] = X[k1 + 4 k2]; transpose to natural order
+    V b[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) b[q] = a[4 * (q & 3) + (q >> 2)];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) a[q] = b[q];
+}
+
+// 8-point DFT of x[e] = a[b0 + e*S] (e = 0..7), in place, natural order.
+template <bool INV, int S, typename V> __device__ __forceinline__ void dft8s(V *a) {
+    // n = 2 n1 + n2, k = k1 + 4 k2
+#pragma unroll
+    for (int n2 = 0; n2 < 2; ++n2) dft4<INV>(a[n2 * S], a[(2 + n2) * S], a[(4 + n2) * S], a[(6 + n2) * S]);
+    // a[(2 k1 + n2) S] = Y[n2][k1]; twiddle n2 = 1 by w8^{k1} = w16^{2 k1}
+    a[3 * S] = mul_w16<2, INV>(a[3 * S]);
+    a[5 * S] = mul_w16<4, INV>(a[5 * S]);
+    a[7 * S] = mul_w16<6, INV>(a[7 * S]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft2<INV>(a[(2 * k1) * S], a[(2 * k1 + 1) * S]);
+    // a[(2 k1 + k2) S] = X[k1 + 4 k2]
+    V b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) b[q] = a[(2 * (q & 3) + (q >> 2)) * S];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q * S] = b[q];
+}
+
+template <typename V> __device__ __forceinline__ V ldtw(const V *__restrict__ tw, int i) { return __ldg(tw + i); }
+
+// Final stage of radix P (2, 4 or 8): Ns = L/P, thread t runs butterflies
+// j = t + b*TPL (b < 16/P) on registers v[b + r*(16/P)].
+template <int P, bool INV, typename V>
+__device__ __forceinline__ void final_stage(V (&v)[16], int t, int TPL, const V *__restrict__ tw) {
+    constexpr int B = 16 / P;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = t + b * TPL;  // < Ns, so k = j
+#pragma unroll
+        for (int r = 1; r < P; ++r) {
+            V w = ldtw(tw, r * j);
+            v[b + r * B] = INV ? cmulc(v[b + r * B], w) : cmul(v[b + r * B], w);
+        }
+        if constexpr (P == 2) {
+            dft2<INV>(v[b], v[b + B]);
+        } else if constexpr (P == 4) {
+            dft4<INV>(v[b], v[b + B], v[b + 2 * B], v[b + 3 * B]);
+        } else {
+            dft8s<INV, B>(&v[b]);
+        }
+    }
+}
+
+// L-point FFT (forward: exp(-2 pi i nk/L); inverse: exp(+2 pi i nk/L), not
+// normalised) of one line.  On entry v[m] = x[t + m*TPL]; on exit
+// v[m] = X[t + m*TPL].  `sm` is this line's shared buffer of pad16(L) elements.
+// Every thread of the CTA must call this with the same logL (it synchronises).
+template <bool INV, typename V>
+__device__ __forceinline__ void fft_line(V (&v)[16], V *sm, int t, int logL, const V *__restrict__ tw) {
+    const int L = 1 << logL;
+    const int TPL = L >> 4;
+    const int nst = logL >> 2;
+    const int rem = logL & 3;
+    int logNs = 0;
+    for (int s = 0; s < nst; ++s) {
+        const int Ns = 1 << logNs;
+        const int k = t & (Ns - 1);
+        if (s > 0) {
+            const int step = k << (logL - 4 - logNs);  // k * L/(16 Ns)
+#pragma unroll
+            for (int r = 1; r < 16; ++r) {
+                V w = ldtw(tw, r * step);
+                v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+            }
+        }
+        dft16<INV>(v);
+        if (s == nst - 1 && rem == 0) return;  // Ns*16 == L: v[q] = X[t + q*TPL]
+        __syncthreads();
+        const int base = ((t - k) << 4) + k;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) sm[pad16(base + (q << logNs))] = v[q];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = sm[pad16(t + m * TPL)];
+        logNs += 4;
+    }
+    if (rem == 1) final_stage<2, INV>(v, t, TPL, tw);
+    else if (rem == 2) final_stage<4, INV>(v, t, TPL, tw);
+    else if (rem == 3) final_stage<8, INV>(v, t, TPL, tw);
+}
+
+}  // namespace sdf

@@ -1,0 +1,304 @@
+// fixup.cu -- step A6 (SDF_FP32 plans): nodes where the float transform's phi
+// fell below its trust threshold theta_32 but may lie inside the FP64 trust
+// region are recomputed by a direct sum over the occupied nodes near them,
+// with the log-sum-exp shift of Sec. 2.4 (eq. Bound1):
+//   S = m - tau log sum_k c_k exp(-(r_k - m)/tau),   m = min_k r_k,
+// plus grad S (eq. SxSy) and the Hessian (eqs. Sxx, Syy, Sxy).  The shift makes
+// float arithmetic sufficient: there is no dynamic-range floor.  The paper
+// motivates the problem (Sec. 3.3, double precision fails far from the points)
+// but gives no mechanism; this one is ours.
+//
+// One CTA per flagged 8^D tile (one thread per node).  Candidate bins are
+// visited in rings of Chebyshev distance k = 0, 1, 2, ... around the tile,
+// and the search stops once every node of the ring lies farther than
+// min_k r_k + c_cut from every flagged node (c_cut = tau ln(K/1e-7), so the
+// dropped terms weigh less than 1e-7 of the sum).  A tile whose nearest
+// occupied bin is so far that K exp(-d/tau) < theta_64 keeps the capped value.
+// Visiting order is fixed, so the sums are deterministic.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sdf_internal.cuh"
+
+namespace sdf {
+
+struct FixParams {
+    const int *bin_start, *bin_nuniq, *ucell, *ucount;
+    const unsigned char *cheb, *tile_flag;
+    const DevScalars *dsc;
+    DevScalars *dsc_w;
+    void *S, *dS, *d2S;
+    const int8_t *sign;
+    uint8_t *flags;
+    int N0, N1, N2;
+    int nb0, nb1, nb2;
+    int64_t nnodes;
+    double h, tau, coef64;
+    double logK;
+    int fp64_out;
+};
+
+constexpr int kFixCap = 2048;  // cells staged in shared memory at once
+
+// Bin offset of ring element i (ring k > 0) in 2D: walk the square's border.
+__device__ __forceinline__ void ring2(int k, int i, int &dx, int &dy) {
+    const int side = 2 * k;
+    const int s = i / side, o = i % side;
+    switch (s) {
+        case 0: dx = -k + o; dy = -k; break;
+        case 1: dx = k; dy = -k + o; break;
+        case 2: dx = k - o; dy = k; break;
+        default: dx = -k; dy = k - o; break;
+    }
+}
+
+// 3D ring element i: enumerate the (2k+1)^3 cube and skip the interior by
+// index arithmetic: layers z = -k and z = k are full squares, the others are
+// square borders.
+__device__ __forceinline__ void ring3(int k, int i, int &dx, int &dy, int &dz) {
+    const int w = 2 * k + 1, full = w * w, border = 8 * k;
+    if (i < full) {
+        dz = -k;
+        dx = i % w - k;
+        dy = i / w - k;
+        return;
+    }
+    i -= full;
+    const int nmid = 2 * k - 1;
+    if (i < nmid * border) {
+        dz = -k + 1 + i / border;
+        ring2(k, i % border, dx, dy);
+        return;
+    }
+    i -= nmid * border;
+    dz = k;
+    dx = i % w - k;
+    dy = i / w - k;
+}
+
+template <int D, typename TO>
+__global__ void __launch_bounds__(D == 2 ? 64 : 512) k_fixup(FixParams P) {
+    constexpr int NT = (D == 2) ? 64 : 512;
+    constexpr int NH = D * (D + 1) / 2;
+    __shared__ int cx[kFixCap], cy[kFixCap], cz[kFixCap], cc[kFixCap];
+    __shared__ int soff[1];
+    __shared__ float red[NT];
+    __shared__ int wtot[32];
+    const int64_t b = blockIdx.x;
+    if (!P.tile_flag[b]) return;
+    const int tid = threadIdx.x;
+    const int bx = (int)(b % P.nb0), by = (int)((b / P.nb0) % P.nb1), bz = (int)(b / ((int64_t)P.nb0 * P.nb1));
+    const double theta64 = P.coef64 * sqrt((double)P.dsc->sum_c2);
+    const double lt = log(theta64);
+    const int c = P.cheb[b];
+    const double dlo = (c >= 1) ? (8.0 * (c - 1) + 1.0) * P.h : 0.0;
+    // every node of the tile: phi <= K exp(-dlo/tau) < theta64 -> stays capped
+    if (c >= 255 || P.logK - dlo / P.tau < lt) return;
+
+    const int x = bx * 8 + (tid & 7), y = by * 8 + ((tid >> 3) & 7), z = bz * 8 + (tid >> 6);
+    const bool inb = x < P.N0 && y < P.N1 && (D == 2 || z < P.N2);
+    const int64_t node = (int64_t)x + (int64_t)P.N0 * (y + (int64_t)P.N1 * z);
+    bool mine = false;
+    if (inb) mine = (P.flags[node] & SDF_FLAG_CAPPED) != 0;
+    const float h = (float)P.h, tau = (float)P.tau;
+    const float l2e_tau = 1.4426950408889634f / tau;
+    const float ccut = (float)(P.tau * (P.logK + 16.118095650958319));  // tau ln(K / 1e-7)
+    float m = INFINITY, sE = 0.f, sG[D], sH[NH];
+#pragma unroll
+    for (int a = 0; a < D; ++a) sG[a] = 0.f;
+#pragma unroll
+    for (int a = 0; a < NH; ++a) sH[a] = 0.f;
+
+    const int kmax = max(max(P.nb0, P.nb1), (D == 3) ? P.nb2 : 0);
+    for (int k = 0; k <= kmax; ++k) {
+        // stop when the ring is beyond every flagged node's cut-off
+        if (k >= 2) {
+            red[tid] = mine ? m + ccut : -INFINITY;
+            __syncthreads();
+            for (int s = NT / 2; s > 0; s >>= 1) {
+                if (tid < s) red[tid] = fmaxf(red[tid], red[tid + s]);
+                __syncthreads();
+            }
+            const float need = red[0];
+            __syncthreads();
+            const float lb = (8.f * (k - 1) + 1.f) * h;
+            if (!(lb <= need)) break;
+        }
+        const int nring = (k == 0) ? 1 : ((D == 2) ? 8 * k : (2 * k + 1) * (2 * k + 1) * (2 * k + 1) -
+                                                                (2 * k - 1) * (2 * k - 1) * (2 * k - 1));
+        for (int i0 = 0; i0 < nring;) {
+            // one candidate bin per thread
+            const int i = i0 + tid;
+            int nb = 0, gb = -1;
+            if (i < nring) {
+                int dx = 0, dy = 0, dz = 0;
+                if (k > 0) {
+                    if (D == 2) ring2(k, i, dx, dy);
+                    else ring3(k, i, dx, dy, dz);
+                }
+                const int qx = bx + dx, qy = by + dy, qz = bz + dz;
+                if (qx >= 0 && qx < P.nb0 && qy >= 0 && qy < P.nb1 && (D == 2 || (qz >= 0 && qz < P.nb2))) {
+                    gb = qx + P.nb0 * (qy + P.nb1 * qz);
+                    nb = P.bin_nuniq[gb];
+                }
+            }
+            // block exclusive scan of nb
+            const int lane = tid & 31, wid = tid >> 5;
+            int incl = nb;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) wtot[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                const int v = (lane < NT / 32) ? wtot[lane] : 0;
+                int i2 = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, i2, o);
+                    if (lane >= o) i2 += u;
+                }
+                wtot[lane] = i2 - v;
+            }
+            __syncthreads();
+            const int off = wtot[wid] + incl - nb;
+            const bool take = (i < nring) && (off + nb <= kFixCap);
+            const int taken = __syncthreads_count(take);  // taken bins form a prefix
+            if (tid == taken - 1) soff[0] = off + nb;
+            __syncthreads();
+            const int ncell = (taken > 0) ? soff[0] : 0;
+            // copy cells of taken bins
+            if (take && nb > 0) {
+                const int s0 = P.bin_start[gb];
+                const int qb = gb;
+                const int qx = qb % P.nb0, qy = (qb / P.nb0) % P.nb1, qz = qb / (P.nb0 * P.nb1);
+                for (int e = 0; e < nb; ++e) {
+                    const int lc = P.ucell[s0 + e];
+                    cx[off + e] = qx * 8 + (lc & 7);
+                    cy[off + e] = qy * 8 + ((lc >> 3) & 7);
+                    cz[off + e] = qz * 8 + (lc >> 6);
+                    cc[off + e] = P.ucount[s0 + e];
+                }
+            }
+            __syncthreads();
+            if (mine) {
+                for (int e = 0; e < ncell; ++e) {
+                    const int ddx = x - cx[e], ddy = y - cy[e], ddz = (D == 3) ? z - cz[e] : 0;
+                    const int r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    const float rg = sqrtf((float)r2);
+                    const float r = rg * h;
+                    if (r - m > ccut) continue;
+                    if (r < m) {
+                        const float sc = exp2f((r - m) * l2e_tau);
+                        sE *= sc;
+#pragma unroll
+                        for (int a = 0; a < D; ++a) sG[a] *= sc;
+#pragma unroll
+                        for (int a = 0; a < NH; ++a) sH[a] *= sc;
+                        m = r;
+                    }
+                    const float E = (float)cc[e] * exp2f((m - r) * l2e_tau);
+                    sE += E;
+                    if (r2 > 0) {
+                        const float ir = 1.f / rg;
+                        const float n0 = ddx * ir, n1 = ddy * ir, n2 = ddz * ir;
+                        const float nn[3] = {n0, n1, n2};
+                        const float irw = 1.f / r, it = 1.f / tau;
+#pragma unroll
+                        for (int a = 0; a < D; ++a) sG[a] += E * nn[a];
+                        int q = 0;
+#pragma unroll
+                        for (int a = 0; a < D; ++a, ++q) sH[q] += E * ((1.f - nn[a] * nn[a]) * irw - nn[a] * nn[a] * it);
+#pragma unroll
+                        for (int a = 0; a < D; ++a)
+#pragma unroll
+                            for (int bb = a + 1; bb < D; ++bb, ++q) sH[q] += E * (-nn[a] * nn[bb] * (irw + it));
+                    }
+                }
+            }
+            __syncthreads();
+            i0 += max(taken, 1);
+            if (taken == 0) break;  // cannot happen: one bin never exceeds kFixCap
+        }
+    }
+    int fixed = 0, capped = 0;
+    if (mine) {
+        const double S = (double)m - P.tau * log((double)sE);
+        const double scap = -P.tau * lt;
+        TO *So = reinterpret_cast<TO *>(P.S);
+        TO *dS = reinterpret_cast<TO *>(P.dS);
+        TO *d2S = reinterpret_cast<TO *>(P.d2S);
+        const double sg = (P.sign && P.sign[node] < 0) ? -1.0 : 1.0;
+        if (!(S <= scap)) {
+            capped = 1;
+            P.flags[node] = SDF_FLAG_CAPPED | SDF_FLAG_FIXUP;
+        } else {
+            fixed = 1;
+            if (So) So[node] = (TO)(sg * S);
+            const float inv = 1.f / sE;
+            float g[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                g[a] = sG[a] * inv;
+                if (dS) dS[a * P.nnodes + node] = (TO)g[a];
+            }
+            if (d2S) {
+                int q = 0;
+                const float it = 1.f / tau;
+#pragma unroll
+                for (int a = 0; a < D; ++a, ++q) d2S[q * P.nnodes + node] = (TO)(sH[q] * inv + g[a] * g[a] * it);
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+#pragma unroll
+                    for (int bb = a + 1; bb < D; ++bb, ++q)
+                        d2S[q * P.nnodes + node] = (TO)(sH[q] * inv + g[a] * g[bb] * it);
+            }
+            P.flags[node] = SDF_FLAG_FIXUP;
+        }
+    }
+    // statistics
+    const unsigned fb = __ballot_sync(0xffffffffu, fixed), cb = __ballot_sync(0xffffffffu, capped);
+    if ((tid & 31) == 0) {
+        if (fb) atomicAdd(&P.dsc_w->n_fixup_nodes, (unsigned long long)__popc(fb));
+        if (cb) atomicAdd(&P.dsc_w->n_capped, (unsigned long long)__popc(cb));
+    }
+    if (tid == 0) atomicAdd(&P.dsc_w->n_fixup_tiles, 1ull);
+}
+
+cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS, void *d2S, const int8_t *sign,
+                         uint8_t *flags) {
+    FixParams F;
+    F.bin_start = p->bin_start;
+    F.bin_nuniq = p->bin_nuniq;
+    F.ucell = p->ucell;
+    F.ucount = p->ucount;
+    F.cheb = p->cheb;
+    F.tile_flag = p->tile_flag;
+    F.dsc = p->dsc;
+    F.dsc_w = p->dsc;
+    F.S = S;
+    F.dS = dS;
+    F.d2S = d2S;
+    F.sign = sign;
+    F.flags = flags;
+    F.N0 = (int)p->N[0];
+    F.N1 = (int)p->N[1];
+    F.N2 = (int)p->N[2];
+    F.nb0 = (int)p->nb[0];
+    F.nb1 = (int)p->nb[1];
+    F.nb2 = (int)p->nb[2];
+    F.nnodes = p->nnodes;
+    F.h = p->h;
+    F.tau = p->tau;
+    const int D = p->D;
+    const double n = (double)p->M[0] * (double)p->M[1] * (D == 3 ? (double)p->M[2] : 1.0);
+    F.coef64 = p->noise_c64 * ldexp(1.0, -53) * sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
+    F.logK = log((double)p->last_K);
+    F.fp64_out = 0;
+    if (D == 2) k_fixup<2, float><<<(unsigned)p->nbins, 64, 0, p->stream>>>(F);
+    else k_fixup<3, float><<<(unsigned)p->nbins, 512, 0, p->stream>>>(F);
+    return cudaGetLastError();
+}
+
+}  // namespace sdf

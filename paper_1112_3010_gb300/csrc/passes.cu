@@ -1,0 +1,704 @@
+// passes.cu -- the FFT passes of one execute (Table 1 steps 2-6 of the paper,
+// and the same steps for the derivative kernels of Sec. 5 and the sign
+// kernels of Sec. 4).
+//
+// Grid layouts (x fastest unless stated; N_a nodes, M_a padded, M_a >= 2 N_a):
+//   2D:  x-pass   cells      -> T1[u][y]      (u < M0, y < N1)
+//        fused    T1[u][.]   -> O[g][u][y']   (forward along y, multiply, inverse, y' < N1)
+//        epilogue O[g][.][y']-> out[y'][x]    (inverse along x, x < N0)
+//   3D:  x-pass   cells      -> T1[u][z][y]
+//        y-pass   T1[u][z][.]-> T2[v][u][z]
+//        fused    T2[v][u][.]-> O[g][v][u][z']
+//        inv-y    O[g][.][u][z'] -> O2[g][u][z'][y']
+//        epilogue O2[g][.][z'][y'] -> out[z'][y'][x]
+// A "transposed" side reads or writes element i of line l at i*n_lines + l; a
+// CTA handles R consecutive lines so those accesses are R-element segments.
+// Input pruning: only the first N of M inputs of a forward line are nonzero.
+// Output pruning: only the first N outputs of an inverse line are kept.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sdf_internal.cuh"
+
+namespace sdf {
+
+template <typename T> using cx = typename cplx_t<T>::type;
+
+// Thread bound per precision: a double line needs twice the registers.
+#define SDF_LB(T) __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
+template <typename T> constexpr int max_threads() { return sizeof(T) == 8 ? 512 : 1024; }
+
+struct LineCfg {
+    int logL, L, TPL, PL, R;
+};
+
+static inline LineCfg line_cfg(int logL, int R) {
+    LineCfg c;
+    c.logL = logL;
+    c.L = 1 << logL;
+    c.TPL = c.L >> 4;
+    c.PL = pad16(c.L);
+    c.R = R;
+    return c;
+}
+
+// Lines per CTA: the largest power of two with R*TPL <= max_threads,
+// R*padded*sizeof(V) <= smem budget and R <= r_cap.
+static inline int pick_R(int logL, size_t vbytes, int max_threads, int r_cap, size_t smem_budget) {
+    int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    int R = 1;
+    while (R * 2 <= r_cap && (R * 2) * TPL <= max_threads && (size_t)(R * 2) * PL * vbytes <= smem_budget) R *= 2;
+    return R;
+}
+
+// ---------------------------------------------------------------- x-pass
+// Builds each line of the point fields from the deduplicated node list
+// (bin-grouped), transforms it along x and writes it transposed.
+// Field 0: (count, 0); field 1: (w_0, w_1); field 2: (w_2, 0).
+template <typename T>
+__global__ void SDF_LB(T) k_xpass_cells(const int *__restrict__ bin_start, const int *__restrict__ bin_nuniq,
+                                                      const int *__restrict__ ucell, const int *__restrict__ ucount,
+                                                      const double *__restrict__ uw, int N1, int nb0, int nb1,
+                                                      int logL, int R, int nfield, int64_t n_lines, cx<T> *out,
+                                                      int64_t out_fs, const cx<T> *__restrict__ tw) {
+    using V = cx<T>;
+    extern __shared__ unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int tid = threadIdx.x, lr = tid % R, t = tid / R;
+    const int64_t line = (int64_t)blockIdx.x * R + lr;
+    const bool valid = line < n_lines;
+    const int y = valid ? (int)(line % N1) : 0;
+    const int z = valid ? (int)(line / N1) : 0;
+    const int by = y >> 3, bz = z >> 3, ly = y & 7, lz = z & 7;
+    const int64_t brow = (int64_t)nb0 * (by + (int64_t)nb1 * bz);
+    V *my = sm + lr * PL;
+    for (int f = 0; f < nfield; ++f) {
+        if (f > 0) __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 8; ++m) my[pad16(t + m * TPL)] = mk<V>(T(0), T(0));
+        __syncthreads();
+        if (valid) {
+            for (int bx = t; bx < nb0; bx += TPL) {
+                const int64_t b = brow + bx;
+                const int n = bin_nuniq[b];
+                const int s = bin_start[b];
+                for (int i = 0; i < n; ++i) {
+                    const int lc = ucell[s + i];
+                    if (((lc >> 3) & 7) != ly || (lc >> 6) != lz) continue;
+                    const int x = bx * 8 + (lc & 7);
+                    V val;
+                    if (f == 0) val = mk<V>(T(ucount[s + i]), T(0));
+                    else if (f == 1) val = mk<V>(T(uw[3 * (int64_t)(s + i)]), T(uw[3 * (int64_t)(s + i) + 1]));
+                    else val = mk<V>(T(uw[3 * (int64_t)(s + i) + 2]), T(0));
+                    my[pad16(x)] = val;
+                }
+            }
+        }
+        __syncthreads();
+        V v[16];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = my[pad16(t + m * TPL)];
+#pragma unroll
+        for (int m = 8; m < 16; ++m) v[m] = mk<V>(T(0), T(0));
+        fft_line<false>(v, my, t, logL, tw);
+        if (valid) {
+            V *o = out + f * out_fs + line;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) o[(int64_t)(t + m * TPL) * n_lines] = v[m];
+        }
+    }
+}
+
+// x-pass of a dense real grid a(X) = w(X)/phi(X) (the adjoint's input), with
+// phi = exp(-S/tau) from the forward's unsigned S; nodes flagged CAPPED give 0.
+template <typename T>
+__global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__restrict__ Ssaved,
+                                                      const uint8_t *__restrict__ flags, double inv_tau, int N0,
+                                                      int logL, int R, int64_t n_lines, cx<T> *out,
+                                                      const cx<T> *__restrict__ tw) {
+    using V = cx<T>;
+    extern __shared__ unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int tid = threadIdx.x, lr = tid % R, t = tid / R;
+    const int64_t line = (int64_t)blockIdx.x * R + lr;
+    const bool valid = line < n_lines;
+    V *my = sm + lr * PL;
+    V v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int x = t + m * TPL;
+        T a = T(0);
+        if (m < 8 && valid && x < N0) {
+            const int64_t node = line * N0 + x;
+            if (!(flags && (flags[node] & SDF_FLAG_CAPPED))) {
+                // a = w / phi = w exp(S/tau)
+                a = T((double)w[node] * exp((double)Ssaved[node] * inv_tau));
+            }
+        }
+        v[m] = mk<V>(a, T(0));
+    }
+    __syncthreads();
+    fft_line<false>(v, my, t, logL, tw);
+    if (valid) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) out[(int64_t)(t + m * TPL) * n_lines + line] = v[m];
+    }
+}
+
+// ---------------------------------------------------------------- generic forward
+// Contiguous lines of n_in stored values (the rest of the L inputs are zero),
+// forward transform, transposed output.  Used for the 3D y-pass and for the
+// plan-time kernel transforms (n_in = L).
+template <typename T>
+__global__ void SDF_LB(T) k_fwd_T(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int R,
+                                                int64_t n_lines, int nfield, int64_t in_fs, int64_t out_fs,
+                                                const cx<T> *__restrict__ tw) {
+    using V = cx<T>;
+    extern __shared__ unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int tid = threadIdx.x, lr = tid % R, t = tid / R;
+    const int64_t line = (int64_t)blockIdx.x * R + lr;
+    const bool valid = line < n_lines;
+    V *my = sm + lr * PL;
+    for (int f = 0; f < nfield; ++f) {
+        V v[16];
+        const V *src = in + f * in_fs + line * n_in;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int e = t + m * TPL;
+            v[m] = (valid && e < n_in) ? src[e] : mk<V>(T(0), T(0));
+        }
+        __syncthreads();
+        fft_line<false>(v, my, t, logL, tw);
+        if (valid) {
+            V *o = out + f * out_fs + line;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) o[(int64_t)(t + m * TPL) * n_lines] = v[m];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- fused pass
+struct FusedParams {
+    int ngroup;
+    int nterm[kMaxGroups];
+    int tk[kMaxGroups][3];     // kernel slot
+    int tf[kMaxGroups][3];     // field
+    double br[kMaxGroups][3], bi[kMaxGroups][3];
+    const void *kc[kMaxKernels];  // compressed spectra
+    int kpar[kMaxKernels];        // parity bits
+    int D;
+    int M0, M1;                   // padded sizes of the line axes (3D: M0 = axis0, M1 = axis1)
+    int nfield;
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void line_fold(int64_t line, const FusedParams &P, int64_t &cbase, int &flips) {
+    // flips bit a: frequency on axis a is above M_a/2
+    if (D == 2) {
+        const int u = (int)line;
+        const int fu = u <= P.M0 / 2 ? u : P.M0 - u;
+        flips = (u > P.M0 / 2) ? 1 : 0;
+        cbase = (int64_t)fu;  // times (M1/2+1) added by caller
+    } else {
+        const int u = (int)(line % P.M0), vv = (int)(line / P.M0);
+        const int fu = u <= P.M0 / 2 ? u : P.M0 - u;
+        const int fv = vv <= P.M1 / 2 ? vv : P.M1 - vv;
+        flips = ((u > P.M0 / 2) ? 1 : 0) | ((vv > P.M1 / 2) ? 2 : 0);
+        cbase = (int64_t)fv * (P.M0 / 2 + 1) + fu;
+    }
+}
+
+// Forward along the last axis, multiply by the kernel spectra, inverse along the
+// same axis, keep the first n_out outputs.  Field spectra stay in registers.
+template <typename T, int D>
+__global__ void __launch_bounds__(512) k_fused(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int n_out,
+                                               int R, int64_t n_lines, int64_t in_fs, int64_t out_fs, FusedParams P,
+                                               const cx<T> *__restrict__ tw) {
+    using V = cx<T>;
+    extern __shared__ unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L), half = L >> 1;
+    const int tid = threadIdx.x, lr = tid % R, t = tid / R;
+    const int64_t line = (int64_t)blockIdx.x * R + lr;
+    const bool valid = line < n_lines;
+    V *my = sm + lr * PL;
+    int64_t cb;
+    int flips;
+    line_fold<T, D>(valid ? line : 0, P, cb, flips);
+    cb *= (half + 1);
+    const int waxis = D - 1;
+
+    V F0[16], F1[16], F2[16];
+    auto load_fwd = [&](int f, V (&v)[16]) {
+        const V *src = in + f * in_fs + line * n_in;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int e = t + m * TPL;
+            v[m] = (valid && m < 8 && e < n_in) ? src[e] : mk<V>(T(0), T(0));
+        }
+        __syncthreads();
+        fft_line<false>(v, my, t, logL, tw);
+    };
+    auto run_group = [&](int g, const V (&A)[16], const V (&B)[16], const V (&C)[16]) {
+        V v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = mk<V>(T(0), T(0));
+        for (int k = 0; k < P.nterm[g]; ++k) {
+            const int slot = P.tk[g][k];
+            const T *c = reinterpret_cast<const T *>(P.kc[slot]);
+            const int par = P.kpar[slot];
+            const T br = T(P.br[g][k]), bi = T(P.bi[g][k]);
+            const int f = P.tf[g][k];
+            const bool lflip = (__popc(par & flips) & 1) != 0;
+            const bool wodd = (par >> waxis) & 1;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                const int w = t + m * TPL;
+                const int fw = w <= half ? w : L - w;
+                T val = __ldg(c + cb + fw);
+                if (lflip ^ (wodd && w > half)) val = -val;
+                const V s = (f == 0) ? A[m] : ((f == 1) ? B[m] : C[m]);
+                // v += (br + i bi) * val * s
+                const T pr = br * val, pi = bi * val;
+                v[m].x += pr * s.x - pi * s.y;
+                v[m].y += pr * s.y + pi * s.x;
+            }
+        }
+        __syncthreads();
+        fft_line<true>(v, my, t, logL, tw);
+        if (valid) {
+            V *o = out + g * out_fs + line * n_out;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                const int e = t + m * TPL;
+                if (m < 8 && e < n_out) o[e] = v[m];
+            }
+        }
+    };
+    // groups that use field 0 only come first; the sign group (fields 1[,2]) last
+    load_fwd(0, F0);
+    int g = 0;
+    for (; g < P.ngroup; ++g) {
+        bool only0 = true;
+        for (int k = 0; k < P.nterm[g]; ++k) only0 &= (P.tf[g][k] == 0);
+        if (!only0) break;
+        run_group(g, F0, F0, F0);
+    }
+    if (g < P.ngroup) {
+        load_fwd(1, F1);
+        if (P.nfield > 2) load_fwd(2, F2);
+        else {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) F2[m] = mk<V>(T(0), T(0));
+        }
+        // no sign-group term reads field 0, so F0 is dead here
+        for (; g < P.ngroup; ++g) run_group(g, F1, F1, F2);
+    }
+}
+
+// ---------------------------------------------------------------- inverse (3D y)
+// Transposed input (all L elements), inverse transform, contiguous output of
+// the first n_out elements.
+template <typename T>
+__global__ void SDF_LB(T) k_inv_T(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_out, int R,
+                                                int64_t n_lines, int nfield, int64_t in_fs, int64_t out_fs,
+                                                const cx<T> *__restrict__ tw) {
+    using V = cx<T>;
+    extern __shared__ unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int tid = threadIdx.x, lr = tid % R, t = tid / R;
+    const int64_t line = (int64_t)blockIdx.x * R + lr;
+    const bool valid = line < n_lines;
+    V *my = sm + lr * PL;
+    for (int f = 0; f < nfield; ++f) {
+        V v[16];
+        const V *src = in + f * in_fs + line;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
+        __syncthreads();
+        fft_line<true>(v, my, t, logL, tw);
+        if (valid) {
+            V *o = out + f * out_fs + line * n_out;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                const int e = t + m * TPL;
+                if (m < 8 && e < n_out) o[e] = v[m];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- epilogue
+struct EpiParams {
+    int ngroup;
+    int order[kMaxGroups];
+    int gch[kMaxGroups][2];
+    int64_t in_fs;
+    void *S, *dS, *d2S;
+    int8_t *sign;
+    uint8_t *flags;
+    uint8_t *tile_flag;
+    const DevScalars *dsc;
+    double tau, coef64, coef32;
+    int64_t nnodes;
+    int N0, N1;
+    int nb0, nb1;
+    int D;
+    int fixup;  // FP32 plan: nodes below theta32 go to the fix-up
+};
+
+template <typename T, int D>
+__global__ void SDF_LB(T) k_epilogue(const cx<T> *__restrict__ in, int logL, int R, int64_t n_lines,
+                                                   EpiParams P, const cx<T> *__restrict__ tw) {
+    using V = cx<T>;
+    extern __shared__ unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int tid = threadIdx.x, lr = tid % R, t = tid / R;
+    const int64_t line = (int64_t)blockIdx.x * R + lr;
+    const bool valid = line < n_lines;
+    V *my = sm + lr * PL;
+    const int N0 = P.N0;
+    const double c2 = (double)P.dsc->sum_c2;
+    const double gn = sqrt(c2);
+    const double theta64 = P.coef64 * gn;
+    const double theta32 = P.coef32 * gn;
+    const T theta = T(P.fixup ? theta32 : theta64);
+    const T scap = T(-P.tau * log(theta64));
+    const T tau = T(P.tau), itau = T(1.0 / P.tau);
+    constexpr int NH = D * (D + 1) / 2;
+
+    T phi[8];
+    T gs[D][8];
+    unsigned sgn = 0xffu;   // bit m: +1 (no sign requested: all +1)
+    unsigned trusted = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        phi[m] = T(1);
+#pragma unroll
+        for (int a = 0; a < D; ++a) gs[a][m] = T(0);
+    }
+    T *Sout = reinterpret_cast<T *>(P.S);
+    T *dS = reinterpret_cast<T *>(P.dS);
+    T *d2S = reinterpret_cast<T *>(P.d2S);
+
+    for (int gi = 0; gi < P.ngroup; ++gi) {
+        const int g = P.order[gi];
+        V v[16];
+        const V *src = in + g * P.in_fs + line;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
+        __syncthreads();
+        fft_line<true>(v, my, t, logL, tw);
+        if (!valid) continue;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int ch = P.gch[g][half];
+            if (ch == CH_NONE) continue;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int x = t + m * TPL;
+                if (x >= N0) continue;
+                const int64_t node = line * N0 + x;
+                const T val = half ? v[m].y : v[m].x;
+                const bool tr = (trusted >> m) & 1;
+                switch (ch) {
+                    case CH_MU: {
+                        const bool inside = fabs((double)val) >= 0.5;
+                        if (!inside) sgn &= ~(1u << m);
+                        if (P.sign) P.sign[node] = inside ? 1 : -1;
+                        break;
+                    }
+                    case CH_PHI: {
+                        phi[m] = val;
+                        const bool ok = val >= theta;
+                        if (ok) trusted |= 1u << m;
+                        const T s = ok ? -tau * log(val) : scap;
+                        const T sv = ((sgn >> m) & 1) ? s : -s;
+                        if (Sout) Sout[node] = sv;
+                        if (P.flags) P.flags[node] = ok ? 0 : SDF_FLAG_CAPPED;
+                        if (!ok && P.fixup && P.tile_flag) {
+                            const int y = (int)(line % P.N1), z = (int)(line / P.N1);
+                            const int64_t b = (x >> 3) + (int64_t)P.nb0 * ((y >> 3) + (int64_t)P.nb1 * (z >> 3));
+                            P.tile_flag[b] = 1;
+                        }
+                        break;
+                    }
+                    case CH_GX:
+                    case CH_GY:
+                    case CH_GZ: {
+                        const int a = ch - CH_GX;
+                        const T gv = tr ? val / phi[m] : T(0);
+                        if (a == 0) gs[0][m] = gv;
+                        if (D > 1 && a == 1) gs[1][m] = gv;
+                        if (D > 2 && a == 2) gs[D - 1][m] = gv;
+                        if (dS) dS[a * P.nnodes + node] = gv;
+                        break;
+                    }
+                    default: {
+                        // Hessian channel: num/phi + S_a S_b / tau
+                        int a = 0, b = 0, c = 0;
+                        switch (ch) {
+                            case CH_HXX: a = 0; b = 0; c = 0; break;
+                            case CH_HYY: a = 1; b = 1; c = 1; break;
+                            case CH_HZZ: a = 2; b = 2; c = 2; break;
+                            case CH_HXY: a = 0; b = 1; c = D; break;
+                            case CH_HXZ: a = 0; b = 2; c = 4; break;
+                            default: a = 1; b = 2; c = 5; break;
+                        }
+                        T ga = gs[0][m], gb = gs[0][m];
+                        if (a == 1) ga = gs[1][m];
+                        if (D > 2 && a == 2) ga = gs[D - 1][m];
+                        if (b == 1) gb = gs[1][m];
+                        if (D > 2 && b == 2) gb = gs[D - 1][m];
+                        const T hv = tr ? val / phi[m] + ga * gb * itau : T(0);
+                        if (d2S && c < NH) d2S[c * P.nnodes + node] = hv;
+                        break;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+static cudaError_t set_smem(const void *fn, size_t bytes) {
+    if (bytes > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+constexpr size_t kSmemBudget = 200 * 1024;
+
+template <typename T>
+cudaError_t fwd_T_launch(const cx<T> *in, cx<T> *out, int logL, int n_in, int64_t n_lines, int nfield, int64_t in_fs,
+                         int64_t out_fs, const cx<T> *tw, cudaStream_t st) {
+    const int R = pick_R(logL, sizeof(cx<T>), max_threads<T>(), 16, kSmemBudget);
+    LineCfg c = line_cfg(logL, R);
+    const size_t smem = (size_t)R * c.PL * sizeof(cx<T>);
+    cudaError_t e = set_smem<T>((const void *)k_fwd_T<T>, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (n_lines + R - 1) / R;
+    k_fwd_T<T><<<(unsigned)grid, R * c.TPL, smem, st>>>(in, out, logL, n_in, R, n_lines, nfield, in_fs, out_fs, tw);
+    return cudaGetLastError();
+}
+template cudaError_t fwd_T_launch<double>(const double2 *, double2 *, int, int, int64_t, int, int64_t, int64_t,
+                                          const double2 *, cudaStream_t);
+template cudaError_t fwd_T_launch<float>(const float2 *, float2 *, int, int, int64_t, int, int64_t, int64_t,
+                                         const float2 *, cudaStream_t);
+
+static FusedParams make_fused_params(const sdf_plan_impl *p) {
+    FusedParams F;
+    memset(&F, 0, sizeof(F));
+    F.ngroup = p->ngroup;
+    for (int g = 0; g < p->ngroup; ++g) {
+        F.nterm[g] = p->group[g].nterm;
+        for (int k = 0; k < p->group[g].nterm; ++k) {
+            F.tk[g][k] = p->group[g].term[k].kslot;
+            F.tf[g][k] = p->group[g].term[k].field;
+            F.br[g][k] = p->group[g].term[k].br;
+            F.bi[g][k] = p->group[g].term[k].bi;
+        }
+    }
+    for (size_t s = 0; s < p->kernels.size() && s < (size_t)kMaxKernels; ++s) {
+        F.kc[s] = p->kernels[s].c;
+        F.kpar[s] = p->kernels[s].parity;
+    }
+    F.D = p->D;
+    F.M0 = (int)p->M[0];
+    F.M1 = (int)p->M[1];
+    F.nfield = p->nfield;
+    return F;
+}
+
+template <typename T>
+static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void *dense_in, const uint8_t *flags_in) {
+    using V = cx<T>;
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    const int D = p->D;
+    const int nfield = dense_in ? 1 : (with_weights ? p->nfield : 1);
+    V *A = reinterpret_cast<V *>(p->bufA);
+    V *B = reinterpret_cast<V *>(p->bufB);
+    const int64_t N0 = p->N[0], N1 = p->N[1], N2 = p->N[2];
+    const int64_t M0 = p->M[0], M1 = p->M[1];
+    // ---- x-pass
+    {
+        const int logL = p->logM[0];
+        const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
+        LineCfg c = line_cfg(logL, R);
+        const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
+        const size_t smem = (size_t)R * c.PL * sizeof(V);
+        const int64_t grid = (n_lines + R - 1) / R;
+        const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
+        if (dense_in) {
+            const T *const *pair = reinterpret_cast<const T *const *>(dense_in);
+            if ((e = set_smem<T>((const void *)k_xpass_dense<T>, smem)) != cudaSuccess) return e;
+            k_xpass_dense<T><<<(unsigned)grid, R * c.TPL, smem, st>>>(pair[0], pair[1], flags_in, 1.0 / p->tau,
+                                                                     (int)N0, logL, R, n_lines, A, tw0);
+        } else {
+            if ((e = set_smem<T>((const void *)k_xpass_cells<T>, smem)) != cudaSuccess) return e;
+            k_xpass_cells<T><<<(unsigned)grid, R * c.TPL, smem, st>>>(
+                p->bin_start, p->bin_nuniq, p->ucell, p->ucount, p->uw, (int)N1, (int)p->nb[0], (int)p->nb[1], logL,
+                R, nfield, n_lines, A, M0 * n_lines, tw0);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const V *fin = A;
+    V *fout = B;
+    int64_t fused_lines = M0;
+    int fused_logL = p->logM[1];
+    int fused_nin = (int)N1;
+    int64_t in_fs = M0 * N1;
+    if (D == 3) {
+        // ---- y-pass: T1[u][z][y] (lines (u,z), contiguous y) -> T2[v][u][z]
+        const int64_t n_lines = M0 * N2;
+        if ((e = fwd_T_launch<T>(A, B, p->logM[1], (int)N1, n_lines, nfield, M0 * N2 * N1, M1 * n_lines,
+                                 reinterpret_cast<const V *>(p->tw[1]), st)) != cudaSuccess)
+            return e;
+        fin = B;
+        fout = A;
+        fused_lines = M1 * M0;
+        fused_logL = p->logM[2];
+        fused_nin = (int)N2;
+        in_fs = M1 * M0 * N2;
+    }
+    // ---- fused: forward along the last axis, multiply, inverse
+    {
+        const int logL = fused_logL;
+        const int TPL = (1 << logL) >> 4;
+        int R = 1;
+        while (R * 2 * TPL <= 256) R *= 2;
+        LineCfg c = line_cfg(logL, R);
+        const size_t smem = (size_t)R * c.PL * sizeof(V);
+        FusedParams F = make_fused_params(p);
+        if (dense_in) F.nfield = 1;
+        const int64_t n_out = (D == 2) ? N1 : N2;
+        const int64_t out_fs = fused_lines * n_out;
+        const int64_t grid = (fused_lines + R - 1) / R;
+        const V *twl = reinterpret_cast<const V *>(p->tw[D - 1]);
+        if (D == 2) {
+            if ((e = set_smem<T>((const void *)k_fused<T, 2>, smem)) != cudaSuccess) return e;
+            k_fused<T, 2><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, fused_nin, (int)n_out, R,
+                                                                  fused_lines, in_fs, out_fs, F, twl);
+        } else {
+            if ((e = set_smem<T>((const void *)k_fused<T, 3>, smem)) != cudaSuccess) return e;
+            k_fused<T, 3><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, fused_nin, (int)n_out, R,
+                                                                  fused_lines, in_fs, out_fs, F, twl);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_forward(sdf_plan_impl *p, bool with_weights, const void *dense_in, int /*dense_mode*/,
+                           const uint8_t *flags_in) {
+    if (p->prec == SDF_FP64) return forward_impl<double>(p, with_weights, dense_in, flags_in);
+    return forward_impl<float>(p, with_weights, dense_in, flags_in);
+}
+
+// Inverse passes after the fused pass; the result of the fused pass is in
+// bufB (2D) or bufA (3D).  For 3D the inverse y-pass goes bufA -> bufB.
+template <typename T>
+static cudaError_t inverse_mid(sdf_plan_impl *p, int ngroup, const cx<T> **last_in) {
+    using V = cx<T>;
+    const int D = p->D;
+    if (D == 2) {
+        *last_in = reinterpret_cast<const V *>(p->bufB);
+        return cudaSuccess;
+    }
+    const int64_t N1 = p->N[1], N2 = p->N[2], M0 = p->M[0], M1 = p->M[1];
+    const int logL = p->logM[1];
+    const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
+    LineCfg c = line_cfg(logL, R);
+    const size_t smem = (size_t)R * c.PL * sizeof(V);
+    cudaError_t e = set_smem<T>((const void *)k_inv_T<T>, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t n_lines = M0 * N2;  // lines (u, z')
+    const int64_t grid = (n_lines + R - 1) / R;
+    k_inv_T<T><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(
+        reinterpret_cast<const V *>(p->bufA), reinterpret_cast<V *>(p->bufB), logL, (int)N1, R, n_lines, ngroup,
+        M1 * n_lines, n_lines * N1, reinterpret_cast<const V *>(p->tw[1]));
+    *last_in = reinterpret_cast<const V *>(p->bufB);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, void *S, void *dS, void *d2S,
+                                         int8_t *sign, uint8_t *flags) {
+    using V = cx<T>;
+    const int D = p->D;
+    // groups actually computed: the sign group only with weights
+    int ng = p->ngroup;
+    if (!with_weights) {
+        while (ng > 0 && p->gch[ng - 1][0] == CH_MU) --ng;
+    }
+    const V *lin = nullptr;
+    cudaError_t e = inverse_mid<T>(p, ng, &lin);
+    if (e != cudaSuccess) return e;
+    EpiParams E;
+    memset(&E, 0, sizeof(E));
+    E.ngroup = ng;
+    int k = 0;
+    for (int g = 0; g < ng; ++g)
+        if (p->gch[g][0] == CH_MU) E.order[k++] = g;
+    for (int g = 0; g < ng; ++g)
+        if (p->gch[g][0] != CH_MU) E.order[k++] = g;
+    for (int g = 0; g < ng; ++g) {
+        E.gch[g][0] = p->gch[g][0];
+        E.gch[g][1] = p->gch[g][1];
+    }
+    const int64_t N0 = p->N[0], N1 = p->N[1], N2 = p->N[2], M0 = p->M[0];
+    const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
+    E.in_fs = M0 * n_lines;
+    E.S = S;
+    E.dS = dS;
+    E.d2S = d2S;
+    E.sign = with_weights ? sign : nullptr;
+    E.flags = flags;
+    E.tile_flag = p->tile_flag;
+    E.dsc = p->dsc;
+    E.tau = p->tau;
+    {
+        const double n = (double)p->M[0] * (double)p->M[1] * (D == 3 ? (double)p->M[2] : 1.0);
+        const double base = sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
+        E.coef64 = p->noise_c64 * ldexp(1.0, -53) * base;
+        E.coef32 = p->noise_c32 * ldexp(1.0, -24) * base;
+    }
+    E.nnodes = p->nnodes;
+    E.N0 = (int)N0;
+    E.N1 = (int)N1;
+    E.nb0 = (int)p->nb[0];
+    E.nb1 = (int)p->nb[1];
+    E.D = D;
+    E.fixup = (p->prec == SDF_FP32) ? 1 : 0;
+    const int logL = p->logM[0];
+    const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
+    LineCfg c = line_cfg(logL, R);
+    const size_t smem = (size_t)R * c.PL * sizeof(V);
+    const int64_t grid = (n_lines + R - 1) / R;
+    const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
+    if (D == 2) {
+        if ((e = set_smem<T>((const void *)k_epilogue<T, 2>, smem)) != cudaSuccess) return e;
+        k_epilogue<T, 2><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0);
+    } else {
+        if ((e = set_smem<T>((const void *)k_epilogue<T, 3>, smem)) != cudaSuccess) return e;
+        k_epilogue<T, 3><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0);
+    }
+    (void)N2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_epilogue(sdf_plan_impl *p, bool with_weights, void *S, void *dS, void *d2S, int8_t *sign,
+                                    uint8_t *flags) {
+    if (p->prec == SDF_FP64) return inverse_epilogue_impl<double>(p, with_weights, S, dS, d2S, sign, flags);
+    return inverse_epilogue_impl<float>(p, with_weights, S, dS, d2S, sign, flags);
+}
+
+}  // namespace sdf

@@ -1,0 +1,283 @@
+// points.cu -- step A1: snap the points to their nearest nodes (Sec. 6,
+// Examples 3-4: "rounded ... to the nearest grid points") and form the
+// scattered fields of eq. function_g (counts) and of Secs. 4.1-4.2
+// (tangent- or normal-weighted sums), as a list of distinct occupied nodes
+// grouped by 8^D-node bins.
+//
+// Determinism: every per-node sum is an integer sum (counts, and weights in
+// 62-bit fixed point scaled to max|weight|), so the result does not depend on
+// the order in which atomics land.
+//
+// Steps: k_snap (node, bin, count per bin, max|w|) -> k_scan (bin offsets) ->
+// k_fill (bucket the points by bin) -> k_dedupe (per bin: per-node sums in
+// shared memory, compaction in node order) -> k_cheb_* (Chebyshev distance in
+// bins to the nearest occupied bin, used by the fix-up).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sdf_internal.cuh"
+
+namespace sdf {
+
+__device__ __forceinline__ void set_status(DevScalars *d, int code) { atomicCAS(&d->status, 0, code); }
+
+__global__ void k_snap(int D, int64_t K, const double *__restrict__ P, const double *__restrict__ W, double h,
+                       int N0, int N1, int N2, int nb0, int nb1, int *pt_bin, int *pt_lc, int *bin_count,
+                       DevScalars *dsc) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int j[3] = {0, 0, 0};
+    const int Nn[3] = {N0, N1, N2};
+    bool ok = true;
+    for (int a = 0; a < D; ++a) {
+        const double y = P[k * D + a];
+        // nearest node, ties up: floor(y/h + 0.5)
+        const double q = floor(y / h + 0.5);
+        if (!(q >= 0.0 && q < (double)Nn[a])) {
+            ok = false;
+        } else {
+            j[a] = (int)q;
+        }
+    }
+    if (!ok) {
+        pt_lc[k] = -1;
+        set_status(dsc, SDF_ERR_POINT_OUT_OF_GRID);
+        return;
+    }
+    const int b = (j[0] >> 3) + nb0 * ((j[1] >> 3) + nb1 * (j[2] >> 3));
+    const int lc = (j[0] & 7) | ((j[1] & 7) << 3) | ((j[2] & 7) << 6);
+    pt_bin[k] = b;
+    pt_lc[k] = lc;
+    atomicAdd(&bin_count[b], 1);
+    if (W) {
+        double m = 0.0;
+        for (int a = 0; a < D; ++a) m = fmax(m, fabs(W[k * D + a]));
+        if (isfinite(m) && m > 0.0) atomicMax(&dsc->wmax, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// Exclusive scan of n counts into start[0..n] by one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan(const int *__restrict__ count, int *start, int64_t n) {
+    __shared__ long long part[1024];
+    const int tid = threadIdx.x;
+    const int64_t chunk = (n + 1023) / 1024;
+    const int64_t lo = tid * chunk, hi = min(n, lo + chunk);
+    long long s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += count[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        long long v = (tid >= off) ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    long long run = part[tid] - s;
+    for (int64_t i = lo; i < hi; ++i) {
+        start[i] = (int)run;
+        run += count[i];
+    }
+    if (tid == 1023) start[n] = (int)part[1023];
+}
+
+__global__ void k_fill(int64_t K, const int *__restrict__ pt_bin, const int *__restrict__ pt_lc,
+                       const int *__restrict__ bin_start, int *bin_fill, long long *entry) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int lc = pt_lc[k];
+    if (lc < 0) return;
+    const int b = pt_bin[k];
+    const int slot = bin_start[b] + atomicAdd(&bin_fill[b], 1);
+    entry[slot] = ((long long)lc << 40) | (long long)k;
+}
+
+// One CTA per bin: per-node counts and fixed-point weight sums in shared
+// memory, then the occupied nodes in node order.
+template <int NC>
+__global__ void k_dedupe(int D, int64_t K, const double *__restrict__ W, const int *__restrict__ bin_start,
+                         const long long *__restrict__ entry, int *bin_nuniq, int *ucell, int *ucount, double *uw,
+                         DevScalars *dsc) {
+    __shared__ int cnt[NC];
+    __shared__ long long wf[3][NC];
+    __shared__ int wsum[32];
+    const int b = blockIdx.x;
+    const int s = bin_start[b], e = bin_start[b + 1];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (s == e) {
+        if (tid == 0) bin_nuniq[b] = 0;
+        return;
+    }
+    for (int i = tid; i < NC; i += nt) {
+        cnt[i] = 0;
+        wf[0][i] = wf[1][i] = wf[2][i] = 0;
+    }
+    // fixed-point scale: |w| * scale * K < 2^61
+    double scale = 0.0;
+    if (W) {
+        const double wm = __longlong_as_double((long long)dsc->wmax);
+        if (wm > 0.0) {
+            const int ex = ilogb((double)K * wm) + 1;  // K*wm < 2^ex
+            scale = ldexp(1.0, 61 - ex);
+        }
+    }
+    __syncthreads();
+    for (int i = s + tid; i < e; i += nt) {
+        const long long en = entry[i];
+        const int lc = (int)(en >> 40);
+        const int64_t k = en & ((1LL << 40) - 1);
+        atomicAdd(&cnt[lc], 1);
+        if (W) {
+            for (int a = 0; a < D; ++a) {
+                const long long q = llrint(W[k * D + a] * scale);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&wf[a][lc]), (unsigned long long)q);
+            }
+        }
+    }
+    __syncthreads();
+    // compaction in node order: each thread owns a contiguous range of cells
+    const int per = (NC + nt - 1) / nt;
+    const int c0 = tid * per, c1 = min(NC, c0 + per);
+    int mine = 0;
+    unsigned long long c2 = 0;
+    for (int c = c0; c < c1; ++c)
+        if (cnt[c]) {
+            ++mine;
+            c2 += (unsigned long long)cnt[c] * (unsigned long long)cnt[c];
+        }
+    // block exclusive scan of `mine` (nt <= 1024)
+    const int lane = tid & 31, wid = tid >> 5;
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int v = (lane < (nt + 31) / 32) ? wsum[lane] : 0;
+        int inc2 = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, inc2, o);
+            if (lane >= o) inc2 += u;
+        }
+        if (lane < 32) wsum[lane] = inc2 - v;  // exclusive warp offsets
+    }
+    __syncthreads();
+    int pos = s + wsum[wid] + incl - mine;
+    const double inv = (scale > 0.0) ? 1.0 / scale : 0.0;
+    for (int c = c0; c < c1; ++c) {
+        if (!cnt[c]) continue;
+        ucell[pos] = c;
+        ucount[pos] = cnt[c];
+        uw[3 * (int64_t)pos + 0] = (double)wf[0][c] * inv;
+        uw[3 * (int64_t)pos + 1] = (double)wf[1][c] * inv;
+        uw[3 * (int64_t)pos + 2] = (double)wf[2][c] * inv;
+        ++pos;
+    }
+    // totals
+    for (int o = 16; o > 0; o >>= 1) c2 += __shfl_down_sync(0xffffffffu, c2, o);
+    if (lane == 0 && c2) atomicAdd(&dsc->sum_c2, c2);
+    if (tid == nt - 1) {
+        const int total = wsum[wid] + incl;
+        bin_nuniq[b] = total;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&dsc->n_unique), (unsigned long long)total);
+    }
+}
+
+// Chebyshev distance (in bins, capped at 255) to the nearest occupied bin:
+// separable, one axis at a time.
+__global__ void k_cheb_x(const int *__restrict__ nuniq, unsigned char *out, int nb0, int64_t nrows) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const int64_t base = r * nb0;
+    int d = 255;
+    for (int x = 0; x < nb0; ++x) {
+        d = nuniq[base + x] > 0 ? 0 : min(255, d + 1);
+        out[base + x] = (unsigned char)d;
+    }
+    d = 255;
+    for (int x = nb0 - 1; x >= 0; --x) {
+        d = nuniq[base + x] > 0 ? 0 : min(255, d + 1);
+        if (d < out[base + x]) out[base + x] = (unsigned char)d;
+    }
+}
+
+// pass along an axis with stride `st` and length `n`: d(b) = min_j max(|i-j|, in(b_j))
+__global__ void k_cheb_axis(const unsigned char *__restrict__ in, unsigned char *out, int64_t nbins, int64_t st, int n) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int i = (int)((b / st) % n);
+    const int64_t b0 = b - (int64_t)i * st;
+    int best = in[b];
+    for (int dj = 1; dj < best && dj < n; ++dj) {
+        if (i - dj >= 0) best = min(best, max(dj, (int)in[b0 + (int64_t)(i - dj) * st]));
+        if (i + dj < n) best = min(best, max(dj, (int)in[b0 + (int64_t)(i + dj) * st]));
+    }
+    out[b] = (unsigned char)best;
+}
+
+__global__ void k_source_flags(int64_t nb_total, const int *__restrict__ bin_start, const int *__restrict__ nuniq,
+                               const int *__restrict__ ucell, int N0, int N1, int nb0, int nb1, uint8_t *flags) {
+    const int64_t b = blockIdx.x;
+    if (b >= nb_total) return;
+    const int n = nuniq[b], s = bin_start[b];
+    const int bx = (int)(b % nb0), by = (int)((b / nb0) % nb1), bz = (int)(b / ((int64_t)nb0 * nb1));
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int lc = ucell[s + i];
+        const int x = bx * 8 + (lc & 7), y = by * 8 + ((lc >> 3) & 7), z = bz * 8 + (lc >> 6);
+        const int64_t node = x + (int64_t)N0 * (y + (int64_t)N1 * z);
+        flags[node] |= SDF_FLAG_SOURCE;
+    }
+}
+
+cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, const double *weights) {
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->bin_count, 0, sizeof(int) * (p->nbins + 1), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p->bin_fill, 0, sizeof(int) * p->nbins, st)) != cudaSuccess) return e;
+    // clear the per-execute scalars but keep `status` (reported by sdf_sync)
+    if ((e = cudaMemsetAsync(reinterpret_cast<char *>(p->dsc) + offsetof(DevScalars, wmax), 0,
+                             sizeof(DevScalars) - offsetof(DevScalars, wmax), st)) != cudaSuccess)
+        return e;
+    const int tb = 256;
+    const unsigned gk = (unsigned)((K + tb - 1) / tb);
+    k_snap<<<gk, tb, 0, st>>>(p->D, K, points, weights, p->h, (int)p->N[0], (int)p->N[1], (int)p->N[2],
+                              (int)p->nb[0], (int)p->nb[1], p->pt_key, p->pt_lc, p->bin_count, p->dsc);
+    k_scan<<<1, 1024, 0, st>>>(p->bin_count, p->bin_start, p->nbins);
+    k_fill<<<gk, tb, 0, st>>>(K, p->pt_key, p->pt_lc, p->bin_start, p->bin_fill, p->pt_entry);
+    if (p->D == 2)
+        k_dedupe<64><<<(unsigned)p->nbins, 64, 0, st>>>(p->D, K, weights, p->bin_start, p->pt_entry, p->bin_nuniq,
+                                                       p->ucell, p->ucount, p->uw, p->dsc);
+    else
+        k_dedupe<512><<<(unsigned)p->nbins, 128, 0, st>>>(p->D, K, weights, p->bin_start, p->pt_entry,
+                                                         p->bin_nuniq, p->ucell, p->ucount, p->uw, p->dsc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cheb(sdf_plan_impl *p) {
+    cudaStream_t st = p->stream;
+    const int64_t nb0 = p->nb[0], nb1 = p->nb[1], nb2 = p->nb[2];
+    const int64_t nrows = nb1 * nb2;
+    unsigned char *tmp = p->cheb + p->nbins;  // second half of the allocation
+    k_cheb_x<<<(unsigned)((nrows + 127) / 128), 128, 0, st>>>(p->bin_nuniq, tmp, (int)nb0, nrows);
+    const unsigned g = (unsigned)((p->nbins + 255) / 256);
+    if (p->D == 2) {
+        k_cheb_axis<<<g, 256, 0, st>>>(tmp, p->cheb, p->nbins, nb0, (int)nb1);
+    } else {
+        k_cheb_axis<<<g, 256, 0, st>>>(tmp, p->cheb, p->nbins, nb0, (int)nb1);
+        k_cheb_axis<<<g, 256, 0, st>>>(p->cheb, tmp, p->nbins, nb0 * nb1, (int)nb2);
+        cudaError_t e = cudaMemcpyAsync(p->cheb, tmp, p->nbins, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags) {
+    k_source_flags<<<(unsigned)p->nbins, 64, 0, p->stream>>>(p->nbins, p->bin_start, p->bin_nuniq, p->ucell,
+                                                             (int)p->N[0], (int)p->N[1], (int)p->nb[0],
+                                                             (int)p->nb[1], flags);
+    return cudaGetLastError();
+}
+
+}  // namespace sdf

@@ -1,0 +1,130 @@
+// sdf_internal.cuh -- plan layout and kernel launchers shared by the .cu files
+// of the library.  Nothing here is part of the C ABI (include/sdf.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sdf.h"
+#include "fft_core.cuh"
+
+namespace sdf {
+
+constexpr int kBin = 8;          // bin edge in nodes (8x8 in 2D, 8x8x8 in 3D)
+constexpr int kMaxKernels = 16;  // kernel spectra per plan
+constexpr int kMaxGroups = 8;    // complex inverse transforms per execute
+
+// Kernels sampled on the padded grid (Table 1 step 1, Secs. 4-5).  Offsets o
+// are in world units (node offset times h), r = ||o||, n = o/r, E = exp(-r/tau).
+enum KernelId {
+    KER_PHI = 0,  // E                                   (eq. function_f)
+    KER_GX, KER_GY, KER_GZ,  // n_j E                    (eq. SxSyconv)
+    KER_HXX, KER_HYY, KER_HZZ, KER_HXY, KER_HXZ, KER_HYZ,  // [(d_ij - n_i n_j)/r - n_i n_j/tau] E
+    KER_W1, KER_W2, KER_W3,  // 2D: o_2/r^2, o_1/r^2 (eq. fcfsfr products); 3D: o_j/r^3 (eq. mudef)
+    KER_RF,                  // r E (derivative in tau, adjoint only)
+    KER_COUNT
+};
+
+struct KernelSpec {
+    int id;
+    int parity;     // bit a set: kernel odd along axis a
+    double l1;      // sum over the padded grid of |k|
+    void *c;        // device, compressed real spectrum (plan precision)
+};
+
+// One complex inverse transform: out = sum_t beta_t * Khat_{kernel_t} * Fhat_{field_t}.
+// Terms 0..n-1; the real and imaginary parts of the inverse are two real channels.
+struct Term {
+    int kslot;      // index into plan->kernels
+    int field;      // input field 0..2
+    double br, bi;  // complex coefficient beta (includes the kernel's i^odd factor)
+};
+struct Group {
+    int nterm;
+    Term term[3];
+};
+
+// Epilogue channel layout of each group (what the real / imaginary parts hold).
+enum Channel { CH_NONE = 0, CH_PHI, CH_GX, CH_GY, CH_GZ, CH_HXX, CH_HYY, CH_HZZ, CH_HXY, CH_HXZ, CH_HYZ, CH_MU,
+               CH_AGX, CH_AGY, CH_AGZ, CH_ARF };
+
+// Device-side scalars of one plan.
+struct DevScalars {
+    int status;                 // sdf_status recorded on the device
+    int pad0;
+    unsigned long long wmax;    // bits of max |weight| (positive doubles order as integers)
+    unsigned long long sum_c2;  // sum over nodes of count^2
+    unsigned long long n_fixup_tiles, n_fixup_nodes, n_capped;
+    int64_t n_unique;
+    double dl_dtau_acc;         // adjoint partial sum (deterministic order not required)
+};
+
+struct sdf_plan_impl {
+    int D = 0;
+    int prec = SDF_FP32;
+    unsigned outputs = 0;
+    int64_t N[3] = {1, 1, 1}, M[3] = {1, 1, 1};
+    int logM[3] = {0, 0, 0};
+    int64_t nb[3] = {1, 1, 1};  // bins per axis
+    int64_t nbins = 0, nnodes = 0;
+    double h = 0, tau = 0;
+    cudaStream_t stream = nullptr;
+    double plan_ms = 0;
+    double noise_c32 = 0, noise_c64 = 0;
+    double q_factor = 0;     // combination of kernel l1 norms entering theta
+    double q_factor_adj = 0;
+
+    void *tw[3] = {nullptr, nullptr, nullptr};  // per-axis twiddle tables (plan precision)
+    std::vector<KernelSpec> kernels;
+    int kslot[KER_COUNT];
+
+    // fixed transform programme (forward fields, output groups)
+    int nfield = 0;
+    int ngroup = 0;
+    Group group[kMaxGroups];
+    int gch[kMaxGroups][2];  // channel of real / imaginary part
+
+    // workspace
+    void *bufA = nullptr, *bufB = nullptr;
+    size_t bytesA = 0, bytesB = 0;
+    int64_t Kcap = 0;
+    int *pt_key = nullptr;    // per point: bin
+    int *pt_lc = nullptr;     // per point: local cell (or -1 when out of grid)
+    long long *pt_entry = nullptr;  // per bin slot: (local cell << 40) | point
+    int *bin_count = nullptr, *bin_start = nullptr, *bin_fill = nullptr, *bin_nuniq = nullptr;
+    int *ucell = nullptr, *ucount = nullptr;
+    double *uw = nullptr;
+    unsigned char *cheb = nullptr;   // Chebyshev bin distance to an occupied bin (capped)
+    unsigned char *tile_flag = nullptr;
+    uint8_t *flags_int = nullptr;    // FP32 plans: flags when the caller passes none
+    int8_t *sign_int = nullptr;      // FP32 plans: sign when the caller passes none
+    int64_t last_K = 0;
+    DevScalars *dsc = nullptr;
+    DevScalars *hsc = nullptr;       // pinned mirror
+    double *staging = nullptr;       // device copies for sdf_execute_host
+    size_t staging_bytes = 0;
+    size_t workspace_bytes = 0;
+    double last_theta64 = 0, last_theta32 = 0, last_scap = 0;
+};
+
+// ---- launchers (defined in the .cu files) ----
+cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, const double *weights);
+cudaError_t launch_cheb(sdf_plan_impl *p);
+cudaError_t launch_forward(sdf_plan_impl *p, bool with_weights, const void *dense_in, int dense_mode,
+                           const uint8_t *flags_in);
+cudaError_t launch_inverse_epilogue(sdf_plan_impl *p, bool with_weights, void *S, void *dS, void *d2S,
+                                    int8_t *sign, uint8_t *flags);
+cudaError_t launch_fixup(sdf_plan_impl *p, bool with_sign, void *S, void *dS, void *d2S, const int8_t *sign,
+                         uint8_t *flags);
+cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags);
+cudaError_t build_spectra(sdf_plan_impl *p);
+cudaError_t launch_adjoint(sdf_plan_impl *p, int64_t K, const double *points, double *dL_dY, double *dL_dtau);
+
+// noise model: floor_p = C_p u_p sqrt(log2 n) ||k||_1 ||g||_2 / sqrt(n), theta = floor/eps
+constexpr double kTrustEps = 2.5e-4;
+
+}  // namespace sdf
+
+struct sdf_plan_s : public sdf::sdf_plan_impl {};

@@ -1,0 +1,76 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+entry point include/sdf.h declares (no compute calls without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sdf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdf_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1112_3010_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_path(lib):
+    names = _declared()
+    for n in ("sdf_plan_create", "sdf_execute", "sdf_backward", "sdf_plan_destroy", "sdf_sync"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    import paper_1112_3010_gb300 as pkg
+    for n in _declared():
+        assert n in pkg.EXPORTED, n
+
+
+def test_status_strings(lib):
+    lib.sdf_status_string.restype = ctypes.c_char_p
+    for code in range(8):
+        assert lib.sdf_status_string(code)
+    assert lib.sdf_status_string(0) == b"ok"
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    """Argument checks run before any CUDA call, so they work without a GPU."""
+    lib.sdf_plan_create.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 3)(64, 64, 64)
+    # D = 4 -> SDF_ERR_UNSUPPORTED
+    assert lib.sdf_plan_create(ctypes.byref(h), 4, dims, ctypes.c_double(0.1),
+                               ctypes.c_double(0.01), 1, 1, None) == 2
+    # tau <= 0 -> SDF_ERR_INVALID_ARG
+    assert lib.sdf_plan_create(ctypes.byref(h), 2, dims, ctypes.c_double(0.1),
+                               ctypes.c_double(-1.0), 1, 1, None) == 1
+    # grid too large -> SDF_ERR_UNSUPPORTED
+    big = (ctypes.c_int64 * 3)(8192, 8192, 1)
+    assert lib.sdf_plan_create(ctypes.byref(h), 2, big, ctypes.c_double(0.1),
+                               ctypes.c_double(0.01), 1, 1, None) == 2
+    # execute on a NULL plan -> SDF_ERR_INVALID_ARG
+    lib.sdf_execute.restype = ctypes.c_int
+    assert lib.sdf_execute(None, ctypes.c_int64(10), None, None, None, None, None, None, None) == 1
+
+
+def test_oracle_is_not_linked_by_the_product():
+    """The product path never imports the oracle."""
+    pkg_dir = os.path.join(ROOT, "paper_1112_3010_gb300")
+    for dp, _, fs in os.walk(pkg_dir):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "import oracle" not in txt and "sdf_oracle" not in txt, f
