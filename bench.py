@@ -1,0 +1,372 @@
+"""Benchmark: signed S + grad S grid points per second on one GB300.
+
+Workload (the 2D mixed-precision configuration): a 2048^2 grid (h = 1/2048,
+padded to 4096^2), K = 40000 points sampled along 8 seeded non-intersecting
+star polygons with chord tangents, tau in {0.002, 0.0005}; outputs S (signed),
+grad S, Hessian and sign.  One step = one execute per tau value.  Inputs are
+resident in HBM before the timed region; L2 is flushed (256 MiB write) between
+timed steps, outside the CUDA-event brackets.
+
+Also reported: the same metric through sdf_execute_host (host buffers, copies
+inside the timed region), the plain FP64 GPU path with max|S - S_FP64| over its
+trust region, the dominant kernel's roofline from live CUDA events, the FP64
+oracle's throughput on the host cores (bounded sample), and SM clocks sampled
+during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "signed S+gradS grid pts/s, mixed-prec vs FP64 GPU path at fixed max|S-S_FP64|"
+UNIT = "grid_pts/s"
+N_GRID = 2048
+K_PTS = 40000
+TAUS = (0.002, 0.0005)
+WORKLOAD = "2D mixed precision: 2048^2 grid padded to 4096^2, K=40000 on 8 star polygons, tau in {0.002, 0.0005}"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons (every 200 ms)."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self, dev_index=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(dev_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def workloads():
+    from paper_1112_3010_gb300 import workloads as wl
+    return [wl.config_c2(tau=t) for t in TAUS]
+
+
+def cpu_baseline(shapes, n_nodes=12288, seed=0):
+    """The FP64 oracle (as it stands) on a seeded random sample of nodes of
+    each tau's grid: S, grad S, Hessian and mu.  Returns grid pts/s."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    total_t, total_n = 0.0, 0
+    for s in shapes:
+        idx, inside = oracle.snap(s.points, s.h, s.dims)
+        Y = idx[inside].astype(np.float64) * s.h
+        W = s.weights[inside]
+        sel = rng.choice(s.n_nodes, n_nodes // len(shapes), replace=False)
+        X = oracle.grid_nodes(s.dims, s.h, sel)
+        t0 = time.perf_counter()
+        oracle.evaluate(Y, X, s.tau, weights=W, want=("S", "dS", "d2S", "mu"))
+        total_t += time.perf_counter() - t0
+        total_n += len(sel)
+    return {"value": total_n / total_t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d random nodes per tau of the 2048^2 grid (direct FP64 sum over all K=40000 points), "
+                      "S, grad S, Hessian, mu; %.1f s" % (total_n // len(shapes), total_t)}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    shapes = workloads()
+    per_step = max(512, int(os.environ.get("SDF_REF_NODES", "4096")))
+    for _ in range(args.warmup):
+        cpu_baseline(shapes, n_nodes=256, seed=1)
+    t0 = time.perf_counter()
+    vals = []
+    for k in range(args.steps):
+        vals.append(cpu_baseline(shapes, n_nodes=per_step, seed=100 + k))
+    el = time.perf_counter() - t0
+    v = float(np.mean([x["value"] for x in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_nodes_per_step": per_step,
+                                             "l2": "n/a (host)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def algorithmic_bytes(plan_info, name, stats, n_field, n_group, n_kern):
+    """Algorithmic DRAM bytes of one launch of each 2D pass (FP32 plan)."""
+    N0, N1 = plan_info.dims[0], plan_info.dims[1]
+    M0, M1 = plan_info.padded[0], plan_info.padded[1]
+    c = 8  # complex float
+    if name == "xpass":
+        return n_field * M0 * N1 * c
+    if name == "fused":
+        return (n_field + n_group) * M0 * N1 * c + n_kern * (M0 // 2 + 1) * (M1 // 2 + 1) * 4
+    if name == "epilogue":
+        return n_group * M0 * N1 * c + N0 * N1 * (4 * (1 + 2 + 3) + 1 + 1)
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1112_3010_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.load_library()
+    stream = torch.cuda.Stream()
+    shapes = workloads()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        plans = [pkg.Plan(2, s.dims, s.h, s.tau, precision="fp32", outputs=("S", "dS", "d2S", "sign"),
+                          stream=stream) for s in shapes]
+        pts = [torch.from_numpy(s.points).cuda() for s in shapes]
+        wts = [torch.from_numpy(s.weights).cuda() for s in shapes]
+        outs = [p.alloc_outputs(["S", "dS", "d2S", "sign", "flags"]) for p in plans]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        for p, x, w, o in zip(plans, pts, wts, outs):
+            pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], o["flags"])
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    for p in plans:
+        p.sync()
+    for p in plans:
+        p.profile(True)
+        p.profile_read()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches = 0
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    for p in plans:
+        launches += p.stats().n_launches * args.steps
+    if dist:
+        dist.barrier()
+    time.sleep(0.2)
+    clk = clocks.stop(local)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pts_per_step = sum(s.n_nodes for s in shapes)
+    value = world * pts_per_step * args.steps / (total_ms * 1e-3)
+    prof = {}
+    for p in plans:
+        for name, (n, t) in p.profile_read().items():
+            a = prof.setdefault(name, [0, 0.0])
+            a[0] += n
+            a[1] += t
+        p.profile(False)
+    stats = [p.stats() for p in plans]
+
+    # roofline of the dominant kernel
+    peak, peak_kind = load_peaks()
+    info = plans[0].info
+    n_field, n_group, n_kern = 2, 4, info.n_kernels
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    if dom:
+        name, (n, t) = dom
+        bytes_ = algorithmic_bytes(info, name, None, n_field, n_group, n_kern)
+        if bytes_ is not None:
+            ach = bytes_ / (t / n * 1e-3) / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
+                    "avg_launch_ms": t / n}
+        else:
+            roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None,
+                    "frac": None, "traffic": None, "avg_launch_ms": t / n}
+    per_kernel = {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0]),
+                      "share": v[1] / max(1e-9, sum(x[1] for x in prof.values()))} for k, v in prof.items()}
+
+    # end to end through sdf_execute_host (host buffers, copies inside)
+    e2e = None
+    if rank == 0 or True:
+        shp = (N_GRID, N_GRID)
+        host_out = [{"S": torch.empty(shp, dtype=torch.float32).pin_memory(),
+                     "dS": torch.empty((2,) + shp, dtype=torch.float32).pin_memory(),
+                     "d2S": torch.empty((3,) + shp, dtype=torch.float32).pin_memory(),
+                     "sign": torch.empty(shp, dtype=torch.int8).pin_memory()} for _ in shapes]
+        hp = [torch.from_numpy(s.points).pin_memory() for s in shapes]
+        hw = [torch.from_numpy(s.weights).pin_memory() for s in shapes]
+
+        def host_step():
+            for p, x, w, o in zip(plans, hp, hw, host_out):
+                pkg.sdf_execute_host(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], None)
+
+        for _ in range(2):
+            host_step()
+        n_e2e = max(3, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            host_step()
+        el = time.perf_counter() - t0
+        h2d = sum(2 * s.K * 2 * 8 for s in shapes)
+        d2h = sum(s.n_nodes * (4 * 6 + 1) for s in shapes)
+        e2e = {"value": world * pts_per_step * n_e2e / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * el / n_e2e}
+
+    # the plain FP64 GPU path on the same workload, and max|S - S_FP64|
+    fp64 = None
+    if args.fp64_steps > 0:
+        with torch.cuda.stream(stream):
+            p64 = [pkg.Plan(2, s.dims, s.h, s.tau, precision="fp64", outputs=("S", "dS", "d2S", "sign"),
+                            stream=stream) for s in shapes]
+            o64 = [p.alloc_outputs(["S", "dS", "d2S", "sign", "flags"]) for p in p64]
+
+        def step64():
+            for p, x, w, o in zip(p64, pts, wts, o64):
+                pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], o["flags"])
+
+        with torch.cuda.stream(stream):
+            step64()
+        torch.cuda.synchronize()
+        e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.fp64_steps)]
+        for k in range(args.fp64_steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                e64[k][0].record(stream)
+                step64()
+                e64[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms64 = float(np.mean([a.elapsed_time(b) for a, b in e64]))
+        # accuracy of the mixed path against the FP64 path over the FP64 trust region
+        acc = []
+        for s, o32, o_64, p in zip(shapes, outs, o64, p64):
+            st64 = p.stats()
+            ok = (o_64["flags"] & pkg.SDF_FLAG_CAPPED) == 0
+            S64 = o_64["S"].double()
+            S32 = o32["S"].double()
+            # exclude nodes within 0.1% of the threshold (either path may decide)
+            near = (S64.abs() - st64.s_cap).abs() < s.tau * 1e-3
+            m = ok & ~near
+            dS = (S32 - S64).abs()[m].max().item() if m.any() else 0.0
+            dG = (o32["dS"].double() - o_64["dS"].double()).abs()[:, m].max().item() if m.any() else 0.0
+            dH = (o32["d2S"].double() - o_64["d2S"].double()).abs()[:, m].max().item() if m.any() else 0.0
+            sgn_mis = int(((o32["sign"] != o_64["sign"]) & m).sum().item())
+            acc.append({"tau": s.tau, "max_abs_S_minus_S64_over_tau": dS / s.tau, "max_abs_dS": dG,
+                        "max_abs_d2S_times_tau": dH * s.tau, "trusted_frac": m.float().mean().item(),
+                        "sign_diff_in_trust_region": sgn_mis})
+        fp64 = {"ms_per_step": ms64, "value": pts_per_step / (ms64 * 1e-3), "unit": UNIT,
+                "speedup_mixed_over_fp64": (pts_per_step / (ms64 * 1e-3)) / (value / world),
+                "accuracy": acc}
+        for p in p64:
+            p.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(shapes)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "padded": [info.padded[0], info.padded[1]],
+                       "K": K_PTS, "taus": list(TAUS), "outputs": "S,dS,d2S,sign,flags",
+                       "precision": "mixed (fp32 FFT + shifted direct-sum fix-up)",
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "kernels": per_kernel, "fp64_path": fp64,
+            "fixup": [{"tau": s.tau, "tiles": st.n_fixup_tiles, "nodes": st.n_fixup_nodes,
+                       "capped_in_fixup": st.n_capped, "theta32": st.theta32, "theta64": st.theta64}
+                      for s, st in zip(shapes, stats)]}
+    if rank == 0:
+        print(json.dumps(line))
+    for p in plans:
+        p.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

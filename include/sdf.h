@@ -109,7 +109,15 @@ typedef struct {
     int64_t n_fixup_tiles;  /* tiles the direct-sum fix-up visited             */
     int64_t n_fixup_nodes;  /* nodes it recomputed                            */
     int64_t n_capped;    /* nodes returned as S_cap                            */
+    int64_t n_launches;  /* kernels the last execute launched                  */
 } sdf_exec_stats;
+
+/* Per-kernel device time, filled by sdf_profile_read(). */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;     /* sum of CUDA-event durations on the plan's stream  */
+} sdf_kernel_time;
 
 /*
  * sdf_plan_create -- build a plan for a D-dimensional grid.
@@ -195,6 +203,32 @@ sdf_status sdf_plan_get_info(sdf_plan plan, sdf_plan_info *info);
 
 /* Statistics of the last execute (synchronises the stream). */
 sdf_status sdf_get_stats(sdf_plan plan, sdf_exec_stats *stats);
+
+/*
+ * sdf_plan_set_noise_constants -- replace the constants C_32 and C_64 of the
+ * transform error model (include/sdf.h, "Trust region"): the trust threshold
+ * is theta_p = C_p u_p sqrt(log2 n) Q ||g||_2 / (sqrt(n) * 2.5e-4), with
+ * n = prod(M_a), u_p the unit roundoff and Q a combination of kernel l1 norms.
+ * Values <= 0 keep the current constant.  Used to calibrate the model
+ * against the oracle; the built-in constants come from that calibration.
+ */
+sdf_status sdf_plan_set_noise_constants(sdf_plan plan, double c_fp32, double c_fp64);
+
+/*
+ * sdf_profile_enable -- when enable != 0, every kernel the plan launches is
+ * bracketed by a pair of CUDA events recorded on the plan's stream (the
+ * stream the kernel runs on), so the durations are device times of that
+ * kernel.  Costs two event records per launch; off by default.
+ */
+sdf_status sdf_profile_enable(sdf_plan plan, int enable);
+
+/*
+ * sdf_profile_read -- synchronise the stream and return, per kernel name, the
+ * launches and summed event durations recorded since the last read (at most
+ * max entries written to out, host memory).  Returns the number of entries
+ * written (>= 0) or -1 on error.  Resets the counters.
+ */
+int sdf_profile_read(sdf_plan plan, sdf_kernel_time *out, int max);
 
 /* Free the plan and everything it owns (synchronises its stream). */
 void sdf_plan_destroy(sdf_plan plan);

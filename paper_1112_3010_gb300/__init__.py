@@ -29,7 +29,8 @@ STATUS = {0: "SDF_OK", 1: "SDF_ERR_INVALID_ARG", 2: "SDF_ERR_UNSUPPORTED",
 
 EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
             "sdf_plan_get_info", "sdf_get_stats", "sdf_plan_destroy", "sdf_status_string",
-            "sdf_last_error"]
+            "sdf_last_error", "sdf_profile_enable", "sdf_profile_read",
+            "sdf_plan_set_noise_constants"]
 
 
 class SDFError(RuntimeError):
@@ -58,7 +59,11 @@ class ExecStats(ctypes.Structure):
     _fields_ = [("theta64", ctypes.c_double), ("theta32", ctypes.c_double), ("s_cap", ctypes.c_double),
                 ("g_norm2", ctypes.c_double), ("n_unique", ctypes.c_int64),
                 ("n_fixup_tiles", ctypes.c_int64), ("n_fixup_nodes", ctypes.c_int64),
-                ("n_capped", ctypes.c_int64)]
+                ("n_capped", ctypes.c_int64), ("n_launches", ctypes.c_int64)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
 _LIBH = None
@@ -90,6 +95,12 @@ def load_library(path: str | None = None):
         L.sdf_status_string.restype = ctypes.c_char_p
         L.sdf_last_error.argtypes = []
         L.sdf_last_error.restype = ctypes.c_char_p
+        L.sdf_plan_set_noise_constants.argtypes = [vp, d, d]
+        L.sdf_plan_set_noise_constants.restype = ctypes.c_int
+        L.sdf_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.sdf_profile_enable.restype = ctypes.c_int
+        L.sdf_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), ctypes.c_int]
+        L.sdf_profile_read.restype = ctypes.c_int
         for n in ("sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
                   "sdf_plan_get_info", "sdf_get_stats"):
             getattr(L, n).restype = ctypes.c_int
@@ -154,6 +165,24 @@ def sdf_get_stats(handle) -> ExecStats:
     return st
 
 
+def sdf_plan_set_noise_constants(handle, c_fp32, c_fp64):
+    _ck(_lib().sdf_plan_set_noise_constants(handle, float(c_fp32), float(c_fp64)),
+        "sdf_plan_set_noise_constants")
+
+
+def sdf_profile_enable(handle, enable):
+    _ck(_lib().sdf_profile_enable(handle, int(bool(enable))), "sdf_profile_enable")
+
+
+def sdf_profile_read(handle, max_entries=64):
+    """{kernel name: (launches, total_ms)} since the last read."""
+    arr = (KernelTime * max_entries)()
+    n = _lib().sdf_profile_read(handle, arr, max_entries)
+    if n < 0:
+        raise SDFError(5, "sdf_profile_read")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n)}
+
+
 def sdf_plan_destroy(handle):
     _lib().sdf_plan_destroy(handle)
 
@@ -203,6 +232,12 @@ class Plan:
 
     def stats(self) -> ExecStats:
         return sdf_get_stats(self.handle)
+
+    def profile(self, enable=True):
+        sdf_profile_enable(self.handle, enable)
+
+    def profile_read(self):
+        return sdf_profile_read(self.handle)
 
     def sync(self):
         _ck(sdf_sync(self.handle), "sdf_sync")

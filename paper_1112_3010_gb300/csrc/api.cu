@@ -55,6 +55,31 @@ static double zeta_im(int nodd) { const int q = nodd & 3; return q == 1 ? -1.0 :
 namespace sdf {
 cudaError_t build_spectra(sdf_plan_impl *p);
 
+double hessian_scale(const sdf_plan_impl *p) { return p->tau * p->h / (p->tau + p->h); }
+
+void prof_begin(sdf_plan_impl *p, const char *name, cudaStream_t st) {
+    ++p->nlaunch;
+    if (!p->prof_on) return;
+    ProfRec r;
+    r.name = name;
+    for (cudaEvent_t *ev : {&r.a, &r.b}) {
+        if (!p->prof_pool.empty()) {
+            *ev = p->prof_pool.back();
+            p->prof_pool.pop_back();
+        } else if (cudaEventCreate(ev) != cudaSuccess) {
+            *ev = nullptr;
+        }
+    }
+    if (r.a) cudaEventRecord(r.a, st);
+    p->prof_recs.push_back(r);
+}
+
+void prof_end(sdf_plan_impl *p, cudaStream_t st) {
+    if (!p->prof_on || p->prof_recs.empty()) return;
+    ProfRec &r = p->prof_recs.back();
+    if (r.b) cudaEventRecord(r.b, st);
+}
+
 // Add kernels (if absent) and build their spectra.
 cudaError_t build_kernel_list(sdf_plan_impl *p, const std::vector<int> &ids) {
     std::vector<KernelSpec> keep = p->kernels;
@@ -65,6 +90,11 @@ cudaError_t build_kernel_list(sdf_plan_impl *p, const std::vector<int> &ids) {
         k.id = id;
         k.parity = kernel_parity(id, p->D);
         k.l1 = 0;
+        // The Hessian kernels are up to (1/tau + 1/h) times larger than f; they
+        // are stored scaled to f's size so that a channel packed with one of
+        // them in a complex inverse transform does not inherit its rounding
+        // noise.  The epilogue undoes the scale.
+        k.scale = (id >= KER_HXX && id <= KER_HYZ) ? hessian_scale(p) : 1.0;
         k.c = nullptr;
         fresh.push_back(k);
     }
@@ -160,6 +190,11 @@ static void free_plan(sdf_plan_impl *p) {
     cudaFree(p->dsc);
     cudaFree(p->staging);
     if (p->hsc) cudaFreeHost(p->hsc);
+    for (auto &r : p->prof_recs) {
+        if (r.a) cudaEventDestroy(r.a);
+        if (r.b) cudaEventDestroy(r.b);
+    }
+    for (auto ev : p->prof_pool) cudaEventDestroy(ev);
 }
 
 template <typename T>
@@ -290,11 +325,34 @@ sdf_status sdf_plan_create(sdf_plan *out, int D, const int64_t *dims, double h, 
     if (sg) add_mu(p);
     // noise-model factor Q (how phi's error enters each requested output)
     {
-        auto l1 = [&](int id) { return p->kslot[id] >= 0 ? p->kernels[p->kslot[id]].l1 : 0.0; };
-        const double f = l1(KER_PHI);
-        double gmax = 0, hmax = 0;
-        for (int id = KER_GX; id <= KER_GZ; ++id) gmax = std::max(gmax, l1(id));
-        for (int id = KER_HXX; id <= KER_HYZ; ++id) hmax = std::max(hmax, l1(id));
+        // Noise of a channel ~ the larger stored l1 norm of its packed pair,
+        // times the channel's unscale factor.
+        const Channel base_ch[] = {CH_PHI, CH_GX, CH_GY, CH_GZ, CH_HXX, CH_HYY, CH_HZZ, CH_HXY, CH_HXZ, CH_HYZ};
+        const int base_k[] = {KER_PHI, KER_GX, KER_GY, KER_GZ, KER_HXX, KER_HYY, KER_HZZ, KER_HXY, KER_HXZ, KER_HYZ};
+        auto kern_of = [&](int ch) {
+            for (int i = 0; i < 10; ++i)
+                if (base_ch[i] == ch) return base_k[i];
+            return -1;
+        };
+        auto stored_l1 = [&](int ch) {
+            const int id = kern_of(ch);
+            if (id < 0 || p->kslot[id] < 0) return 0.0;
+            const KernelSpec &k = p->kernels[p->kslot[id]];
+            return k.l1 * k.scale;
+        };
+        double f = 0, gmax = 0, hmax = 0;
+        for (int g = 0; g < p->ngroup; ++g) {
+            const double pair = std::max(stored_l1(p->gch[g][0]), stored_l1(p->gch[g][1]));
+            for (int hh = 0; hh < 2; ++hh) {
+                const int ch = p->gch[g][hh];
+                const int id = kern_of(ch);
+                if (id < 0) continue;
+                const double n = pair / p->kernels[p->kslot[id]].scale;
+                if (ch == CH_PHI) f = n;
+                else if (ch >= CH_GX && ch <= CH_GZ) gmax = std::max(gmax, n);
+                else hmax = std::max(hmax, n);
+            }
+        }
         double q = f;
         if (ds) q = std::max(q, f + gmax);
         if (d2) q = std::max(q, tau * hmax + 2 * gmax + 2 * f);
@@ -382,6 +440,7 @@ sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double
     if (s != SDF_OK) return s;
     CK(ensure_points(p, K));
     p->last_K = K;
+    p->nlaunch = 0;
     const bool ww = weights != nullptr;
     CK(launch_points(p, K, points, weights));
     uint8_t *fl = flags;
@@ -486,7 +545,48 @@ sdf_status sdf_get_stats(sdf_plan p, sdf_exec_stats *st) {
     st->n_fixup_tiles = (int64_t)d.n_fixup_tiles;
     st->n_fixup_nodes = (int64_t)d.n_fixup_nodes;
     st->n_capped = (int64_t)d.n_capped;
+    st->n_launches = p->nlaunch;
     return SDF_OK;
+}
+
+sdf_status sdf_plan_set_noise_constants(sdf_plan p, double c32, double c64) {
+    if (!p) return SDF_ERR_INVALID_ARG;
+    if (c32 > 0) p->noise_c32 = c32;
+    if (c64 > 0) p->noise_c64 = c64;
+    return SDF_OK;
+}
+
+sdf_status sdf_profile_enable(sdf_plan p, int enable) {
+    if (!p) return SDF_ERR_INVALID_ARG;
+    p->prof_on = enable != 0;
+    return SDF_OK;
+}
+
+int sdf_profile_read(sdf_plan p, sdf_kernel_time *out, int max) {
+    if (!p || (max > 0 && !out)) return -1;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return -1;
+    std::vector<sdf_kernel_time> agg;
+    for (auto &r : p->prof_recs) {
+        float ms = 0.f;
+        if (r.a && r.b) cudaEventElapsedTime(&ms, r.a, r.b);
+        size_t i = 0;
+        for (; i < agg.size(); ++i)
+            if (strncmp(agg[i].name, r.name, sizeof(agg[i].name)) == 0) break;
+        if (i == agg.size()) {
+            sdf_kernel_time k;
+            memset(&k, 0, sizeof k);
+            snprintf(k.name, sizeof k.name, "%s", r.name);
+            agg.push_back(k);
+        }
+        agg[i].launches += 1;
+        agg[i].total_ms += ms;
+        if (r.a) p->prof_pool.push_back(r.a);
+        if (r.b) p->prof_pool.push_back(r.b);
+    }
+    p->prof_recs.clear();
+    int n = 0;
+    for (; n < (int)agg.size() && n < max; ++n) out[n] = agg[n];
+    return n;
 }
 
 void sdf_plan_destroy(sdf_plan p) {

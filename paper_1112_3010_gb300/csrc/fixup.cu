@@ -296,8 +296,10 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS
     F.coef64 = p->noise_c64 * ldexp(1.0, -53) * sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
     F.logK = log((double)p->last_K);
     F.fp64_out = 0;
+    prof_begin(p, "fixup", p->stream);
     if (D == 2) k_fixup<2, float><<<(unsigned)p->nbins, 64, 0, p->stream>>>(F);
     else k_fixup<3, float><<<(unsigned)p->nbins, 512, 0, p->stream>>>(F);
+    prof_end(p, p->stream);
     return cudaGetLastError();
 }
 

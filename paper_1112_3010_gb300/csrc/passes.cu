@@ -351,6 +351,7 @@ struct EpiParams {
     int nb0, nb1;
     int D;
     int fixup;  // FP32 plan: nodes below theta32 go to the fix-up
+    double hs_inv;  // 1 / scale of the stored Hessian kernels
 };
 
 template <typename T, int D>
@@ -371,7 +372,7 @@ __global__ void SDF_LB(T) k_epilogue(const cx<T> *__restrict__ in, int logL, int
     const double theta32 = P.coef32 * gn;
     const T theta = T(P.fixup ? theta32 : theta64);
     const T scap = T(-P.tau * log(theta64));
-    const T tau = T(P.tau), itau = T(1.0 / P.tau);
+    const T tau = T(P.tau), itau = T(1.0 / P.tau), hs_inv = T(P.hs_inv);
     constexpr int NH = D * (D + 1) / 2;
 
     T phi[8];
@@ -457,7 +458,7 @@ __global__ void SDF_LB(T) k_epilogue(const cx<T> *__restrict__ in, int logL, int
                         if (D > 2 && a == 2) ga = gs[D - 1][m];
                         if (b == 1) gb = gs[1][m];
                         if (D > 2 && b == 2) gb = gs[D - 1][m];
-                        const T hv = tr ? val / phi[m] + ga * gb * itau : T(0);
+                        const T hv = tr ? (val * hs_inv) / phi[m] + ga * gb * itau : T(0);
                         if (d2S && c < NH) d2S[c * P.nnodes + node] = hv;
                         break;
                     }
@@ -478,20 +479,22 @@ constexpr size_t kSmemBudget = 200 * 1024;
 
 template <typename T>
 cudaError_t fwd_T_launch(const cx<T> *in, cx<T> *out, int logL, int n_in, int64_t n_lines, int nfield, int64_t in_fs,
-                         int64_t out_fs, const cx<T> *tw, cudaStream_t st) {
+                         int64_t out_fs, const cx<T> *tw, cudaStream_t st, sdf_plan_impl *p) {
     const int R = pick_R(logL, sizeof(cx<T>), max_threads<T>(), 16, kSmemBudget);
     LineCfg c = line_cfg(logL, R);
     const size_t smem = (size_t)R * c.PL * sizeof(cx<T>);
     cudaError_t e = set_smem<T>((const void *)k_fwd_T<T>, smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = (n_lines + R - 1) / R;
+    if (p) prof_begin(p, "fwd_y", st);
     k_fwd_T<T><<<(unsigned)grid, R * c.TPL, smem, st>>>(in, out, logL, n_in, R, n_lines, nfield, in_fs, out_fs, tw);
+    if (p) prof_end(p, st);
     return cudaGetLastError();
 }
 template cudaError_t fwd_T_launch<double>(const double2 *, double2 *, int, int, int64_t, int, int64_t, int64_t,
-                                          const double2 *, cudaStream_t);
+                                          const double2 *, cudaStream_t, sdf_plan_impl *);
 template cudaError_t fwd_T_launch<float>(const float2 *, float2 *, int, int, int64_t, int, int64_t, int64_t,
-                                         const float2 *, cudaStream_t);
+                                         const float2 *, cudaStream_t, sdf_plan_impl *);
 
 static FusedParams make_fused_params(const sdf_plan_impl *p) {
     FusedParams F;
@@ -540,13 +543,17 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         if (dense_in) {
             const T *const *pair = reinterpret_cast<const T *const *>(dense_in);
             if ((e = set_smem<T>((const void *)k_xpass_dense<T>, smem)) != cudaSuccess) return e;
+            prof_begin(p, "xpass_dense", st);
             k_xpass_dense<T><<<(unsigned)grid, R * c.TPL, smem, st>>>(pair[0], pair[1], flags_in, 1.0 / p->tau,
                                                                      (int)N0, logL, R, n_lines, A, tw0);
+            prof_end(p, st);
         } else {
             if ((e = set_smem<T>((const void *)k_xpass_cells<T>, smem)) != cudaSuccess) return e;
+            prof_begin(p, "xpass", st);
             k_xpass_cells<T><<<(unsigned)grid, R * c.TPL, smem, st>>>(
                 p->bin_start, p->bin_nuniq, p->ucell, p->ucount, p->uw, (int)N1, (int)p->nb[0], (int)p->nb[1], logL,
                 R, nfield, n_lines, A, M0 * n_lines, tw0);
+            prof_end(p, st);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -560,7 +567,7 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         // ---- y-pass: T1[u][z][y] (lines (u,z), contiguous y) -> T2[v][u][z]
         const int64_t n_lines = M0 * N2;
         if ((e = fwd_T_launch<T>(A, B, p->logM[1], (int)N1, n_lines, nfield, M0 * N2 * N1, M1 * n_lines,
-                                 reinterpret_cast<const V *>(p->tw[1]), st)) != cudaSuccess)
+                                 reinterpret_cast<const V *>(p->tw[1]), st, p)) != cudaSuccess)
             return e;
         fin = B;
         fout = A;
@@ -583,6 +590,7 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         const int64_t out_fs = fused_lines * n_out;
         const int64_t grid = (fused_lines + R - 1) / R;
         const V *twl = reinterpret_cast<const V *>(p->tw[D - 1]);
+        prof_begin(p, "fused", st);
         if (D == 2) {
             if ((e = set_smem<T>((const void *)k_fused<T, 2>, smem)) != cudaSuccess) return e;
             k_fused<T, 2><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, fused_nin, (int)n_out, R,
@@ -592,6 +600,7 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
             k_fused<T, 3><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, fused_nin, (int)n_out, R,
                                                                   fused_lines, in_fs, out_fs, F, twl);
         }
+        prof_end(p, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -622,9 +631,11 @@ static cudaError_t inverse_mid(sdf_plan_impl *p, int ngroup, const cx<T> **last_
     if (e != cudaSuccess) return e;
     const int64_t n_lines = M0 * N2;  // lines (u, z')
     const int64_t grid = (n_lines + R - 1) / R;
+    prof_begin(p, "inv_y", p->stream);
     k_inv_T<T><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(
         reinterpret_cast<const V *>(p->bufA), reinterpret_cast<V *>(p->bufB), logL, (int)N1, R, n_lines, ngroup,
         M1 * n_lines, n_lines * N1, reinterpret_cast<const V *>(p->tw[1]));
+    prof_end(p, p->stream);
     *last_in = reinterpret_cast<const V *>(p->bufB);
     return cudaGetLastError();
 }
@@ -678,12 +689,14 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
     E.nb1 = (int)p->nb[1];
     E.D = D;
     E.fixup = (p->prec == SDF_FP32) ? 1 : 0;
+    E.hs_inv = 1.0 / hessian_scale(p);
     const int logL = p->logM[0];
     const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
     LineCfg c = line_cfg(logL, R);
     const size_t smem = (size_t)R * c.PL * sizeof(V);
     const int64_t grid = (n_lines + R - 1) / R;
     const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
+    prof_begin(p, "epilogue", p->stream);
     if (D == 2) {
         if ((e = set_smem<T>((const void *)k_epilogue<T, 2>, smem)) != cudaSuccess) return e;
         k_epilogue<T, 2><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0);
@@ -691,6 +704,7 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
         if ((e = set_smem<T>((const void *)k_epilogue<T, 3>, smem)) != cudaSuccess) return e;
         k_epilogue<T, 3><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0);
     }
+    prof_end(p, p->stream);
     (void)N2;
     return cudaGetLastError();
 }

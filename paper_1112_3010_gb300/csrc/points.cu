@@ -242,16 +242,24 @@ cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, con
         return e;
     const int tb = 256;
     const unsigned gk = (unsigned)((K + tb - 1) / tb);
+    prof_begin(p, "snap", st);
     k_snap<<<gk, tb, 0, st>>>(p->D, K, points, weights, p->h, (int)p->N[0], (int)p->N[1], (int)p->N[2],
                               (int)p->nb[0], (int)p->nb[1], p->pt_key, p->pt_lc, p->bin_count, p->dsc);
+    prof_end(p, st);
+    prof_begin(p, "scan", st);
     k_scan<<<1, 1024, 0, st>>>(p->bin_count, p->bin_start, p->nbins);
+    prof_end(p, st);
+    prof_begin(p, "fill", st);
     k_fill<<<gk, tb, 0, st>>>(K, p->pt_key, p->pt_lc, p->bin_start, p->bin_fill, p->pt_entry);
+    prof_end(p, st);
+    prof_begin(p, "dedupe", st);
     if (p->D == 2)
         k_dedupe<64><<<(unsigned)p->nbins, 64, 0, st>>>(p->D, K, weights, p->bin_start, p->pt_entry, p->bin_nuniq,
                                                        p->ucell, p->ucount, p->uw, p->dsc);
     else
         k_dedupe<512><<<(unsigned)p->nbins, 128, 0, st>>>(p->D, K, weights, p->bin_start, p->pt_entry,
                                                          p->bin_nuniq, p->ucell, p->ucount, p->uw, p->dsc);
+    prof_end(p, st);
     return cudaGetLastError();
 }
 
@@ -260,6 +268,7 @@ cudaError_t launch_cheb(sdf_plan_impl *p) {
     const int64_t nb0 = p->nb[0], nb1 = p->nb[1], nb2 = p->nb[2];
     const int64_t nrows = nb1 * nb2;
     unsigned char *tmp = p->cheb + p->nbins;  // second half of the allocation
+    prof_begin(p, "cheb", st);
     k_cheb_x<<<(unsigned)((nrows + 127) / 128), 128, 0, st>>>(p->bin_nuniq, tmp, (int)nb0, nrows);
     const unsigned g = (unsigned)((p->nbins + 255) / 256);
     if (p->D == 2) {
@@ -270,13 +279,16 @@ cudaError_t launch_cheb(sdf_plan_impl *p) {
         cudaError_t e = cudaMemcpyAsync(p->cheb, tmp, p->nbins, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
     }
+    prof_end(p, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags) {
+    prof_begin(p, "source_flags", p->stream);
     k_source_flags<<<(unsigned)p->nbins, 64, 0, p->stream>>>(p->nbins, p->bin_start, p->bin_nuniq, p->ucell,
                                                              (int)p->N[0], (int)p->N[1], (int)p->nb[0],
                                                              (int)p->nb[1], flags);
+    prof_end(p, p->stream);
     return cudaGetLastError();
 }
 

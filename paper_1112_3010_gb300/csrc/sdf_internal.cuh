@@ -30,7 +30,8 @@ enum KernelId {
 struct KernelSpec {
     int id;
     int parity;     // bit a set: kernel odd along axis a
-    double l1;      // sum over the padded grid of |k|
+    double l1;      // sum over the padded grid of |k| (unscaled)
+    double scale;   // stored spectrum = scale * spectrum of k (keeps packed pairs balanced)
     void *c;        // device, compressed real spectrum (plan precision)
 };
 
@@ -59,6 +60,12 @@ struct DevScalars {
     unsigned long long n_fixup_tiles, n_fixup_nodes, n_capped;
     int64_t n_unique;
     double dl_dtau_acc;         // adjoint partial sum (deterministic order not required)
+};
+
+// Kernel-level event timing (sdf_profile_enable) and the launch counter.
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
 };
 
 struct sdf_plan_impl {
@@ -107,7 +114,16 @@ struct sdf_plan_impl {
     size_t staging_bytes = 0;
     size_t workspace_bytes = 0;
     double last_theta64 = 0, last_theta32 = 0, last_scap = 0;
+    // profiling
+    bool prof_on = false;
+    int64_t nlaunch = 0;      // kernels launched by the current/last execute
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
 };
+
+// Bracket one kernel launch: prof_begin before, prof_end after.
+void prof_begin(sdf_plan_impl *p, const char *name, cudaStream_t st);
+void prof_end(sdf_plan_impl *p, cudaStream_t st);
 
 // ---- launchers (defined in the .cu files) ----
 cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, const double *weights);
@@ -121,6 +137,8 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool with_sign, void *S, void *dS, vo
 cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags);
 cudaError_t build_spectra(sdf_plan_impl *p);
 cudaError_t launch_adjoint(sdf_plan_impl *p, int64_t K, const double *points, double *dL_dY, double *dL_dtau);
+
+double hessian_scale(const sdf_plan_impl *p);
 
 // noise model: floor_p = C_p u_p sqrt(log2 n) ||k||_1 ||g||_2 / sqrt(n), theta = floor/eps
 constexpr double kTrustEps = 2.5e-4;

@@ -33,7 +33,7 @@ namespace sdf {
 template <typename T>
 cudaError_t fwd_T_launch(const typename cplx_t<T>::type *in, typename cplx_t<T>::type *out, int logL, int n_in,
                          int64_t n_lines, int nfield, int64_t in_fs, int64_t out_fs,
-                         const typename cplx_t<T>::type *tw, cudaStream_t st);
+                         const typename cplx_t<T>::type *tw, cudaStream_t st, sdf_plan_impl *p);
 
 struct SampleCfg {
     int D;
@@ -200,7 +200,7 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
         for (int a = 0; a < D; ++a) {
             const int64_t L = p->M[a];
             const int64_t n_lines = total / L;
-            if ((e = fwd_T_launch<double>(src, dst, p->logM[a], (int)L, n_lines, 1, 0, 0, tw64[a], st)) !=
+            if ((e = fwd_T_launch<double>(src, dst, p->logM[a], (int)L, n_lines, 1, 0, 0, tw64[a], st, nullptr)) !=
                 cudaSuccess)
                 break;
             std::swap(src, dst);
@@ -211,7 +211,7 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
             break;
         if ((e = cudaMemsetAsync(resid, 0, sizeof(double), st)) != cudaSuccess) break;
         const int nodd = __builtin_popcount((unsigned)ks.parity);
-        double scale = inv_n;
+        double scale = inv_n * ks.scale;
         if ((e = cudaMalloc(&ks.c, esz * ctotal)) != cudaSuccess) break;
         if (p->prec == SDF_FP64)
             k_compress<double><<<1024, 256, 0, st>>>(src, reinterpret_cast<double *>(ks.c), D, p->M[0], p->M[1],
