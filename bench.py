@@ -338,7 +338,7 @@ def main():
                         "max_abs_d2S_times_tau": dH * s.tau, "trusted_frac": m.float().mean().item(),
                         "sign_diff_in_trust_region": sgn_mis})
         fp64 = {"ms_per_step": ms64, "value": pts_per_step / (ms64 * 1e-3), "unit": UNIT,
-                "speedup_mixed_over_fp64": (pts_per_step / (ms64 * 1e-3)) / (value / world),
+                "speedup_mixed_over_fp64": (value / world) / (pts_per_step / (ms64 * 1e-3)),
                 "accuracy": acc}
         for p in p64:
             p.close()

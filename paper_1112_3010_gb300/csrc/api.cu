@@ -37,11 +37,15 @@ static sdf_status cuda_fail(cudaError_t e) {
         if (e_ != cudaSuccess) return cuda_fail(e_); \
     } while (0)
 
-// Noise constants C_p of the transform error model (see DESIGN notes in
-// passes.cu / include/sdf.h): the largest |phi_computed - phi| over a grid is
-// below C_p u_p sqrt(log2 n) ||k||_1 ||g||_2 / sqrt(n).
-static const double kNoiseC32 = 4.0;
-static const double kNoiseC64 = 4.0;
+// Noise constants C_p of the transform error model: the largest
+// |phi_computed - phi| over a grid stays below
+// C_p u_p sqrt(log2 n) ||k||_1 ||g||_2 / sqrt(n), with ||k||_1 the larger
+// stored l1 norm of the channel's packed pair.  Calibrated on GB300 against
+// the FP64 oracle (largest ratios seen: 5.9 for double, 4.8 for float
+// transforms, over 2D/3D point sets with tau/h from 0.5 to 1.5); 12 leaves a
+// factor-two margin.
+static const double kNoiseC32 = 12.0;
+static const double kNoiseC64 = 12.0;
 
 static int64_t next_pow2(int64_t v) {
     int64_t p = 1;
