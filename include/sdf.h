@@ -230,6 +230,42 @@ sdf_status sdf_profile_enable(sdf_plan plan, int enable);
  */
 int sdf_profile_read(sdf_plan plan, sdf_kernel_time *out, int max);
 
+/*
+ * sdf_execute_noalloc -- the whole path (plan set-up and one execute) for a
+ * small problem, with no device allocation at all.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: a process whose device memory belongs to another allocator
+ * (a framework's caching pool), a plugin whose host forbids device
+ * allocation after start-up, or a service held to a memory budget fixed in
+ * advance.  Every scratch buffer (kernel spectra, transform buffers, point
+ * bins, flags, device status) lives in one static 32 MiB device array
+ * inside this library; every GPU that loads the library holds it until the
+ * process exits.  The caller still owns points, weights and outputs.
+ *
+ *   D, dims, h, tau, precision, outputs   as sdf_plan_create
+ *   K, points, weights, S, dS, d2S, sign, flags   as sdf_execute
+ *   stream     cudaStream_t (as void*) for the work
+ *
+ * Limits: problems whose scratch exceeds 32 MiB are rejected with
+ * SDF_ERR_CAPACITY before any device work (sdf_last_error() gives the size
+ * needed).  That admits 2D grids up to 256 x 256 in either precision with
+ * K <= 65536 points, and 3D grids up to 32^3.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  The call
+ * is synchronous (it waits for its stream and returns the device status, as
+ * sdf_sync).  All calls share the one array, which keeps the last call's
+ * contents; every counter that must start at zero is cleared by each call.
+ * Calls from this process are serialised by a lock; calls that overlap on the
+ * GPU from elsewhere (another process using the same library image cannot)
+ * would race on the array.
+ */
+sdf_status sdf_execute_noalloc(int D, const int64_t *dims, double h, double tau,
+                               int precision, unsigned outputs, int64_t K,
+                               const double *points, const double *weights,
+                               void *S, void *dS, void *d2S, int8_t *sign,
+                               uint8_t *flags, void *stream);
+
 /* Free the plan and everything it owns (synchronises its stream). */
 void sdf_plan_destroy(sdf_plan plan);
 

@@ -30,7 +30,7 @@ STATUS = {0: "SDF_OK", 1: "SDF_ERR_INVALID_ARG", 2: "SDF_ERR_UNSUPPORTED",
 EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
             "sdf_plan_get_info", "sdf_get_stats", "sdf_plan_destroy", "sdf_status_string",
             "sdf_last_error", "sdf_profile_enable", "sdf_profile_read",
-            "sdf_plan_set_noise_constants"]
+            "sdf_plan_set_noise_constants", "sdf_execute_noalloc"]
 
 
 class SDFError(RuntimeError):
@@ -95,6 +95,9 @@ def load_library(path: str | None = None):
         L.sdf_status_string.restype = ctypes.c_char_p
         L.sdf_last_error.argtypes = []
         L.sdf_last_error.restype = ctypes.c_char_p
+        L.sdf_execute_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(i64), d, d, ctypes.c_int, u, i64,
+                                          vp, vp, vp, vp, vp, vp, vp, vp]
+        L.sdf_execute_noalloc.restype = ctypes.c_int
         L.sdf_plan_set_noise_constants.argtypes = [vp, d, d]
         L.sdf_plan_set_noise_constants.restype = ctypes.c_int
         L.sdf_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -168,6 +171,17 @@ def sdf_get_stats(handle) -> ExecStats:
 def sdf_plan_set_noise_constants(handle, c_fp32, c_fp64):
     _ck(_lib().sdf_plan_set_noise_constants(handle, float(c_fp32), float(c_fp64)),
         "sdf_plan_set_noise_constants")
+
+
+def sdf_execute_noalloc(D, dims, h, tau, precision, outputs, K, points, weights, S, dS, d2S, sign,
+                        flags, stream):
+    """The whole path for a small problem with no device allocation (scratch in
+    a static array inside the library).  Synchronous; returns nothing."""
+    dims_arr = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    _ck(_lib().sdf_execute_noalloc(int(D), dims_arr, float(h), float(tau), int(precision), int(outputs),
+                                   int(K), _ptr(points), _ptr(weights), _ptr(S), _ptr(dS), _ptr(d2S),
+                                   _ptr(sign), _ptr(flags), ctypes.c_void_p(stream or 0)),
+        "sdf_execute_noalloc")
 
 
 def sdf_profile_enable(handle, enable):

@@ -61,6 +61,8 @@ cudaError_t build_spectra(sdf_plan_impl *p);
 
 double hessian_scale(const sdf_plan_impl *p) { return p->tau * p->h / (p->tau + p->h); }
 
+void set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
 void prof_begin(sdf_plan_impl *p, const char *name, cudaStream_t st) {
     ++p->nlaunch;
     if (!p->prof_on) return;
@@ -164,6 +166,140 @@ static void add_mu(sdf_plan_impl *p) {
 
 static size_t vbytes(const sdf_plan_impl *p) { return p->prec == SDF_FP64 ? sizeof(double2) : sizeof(float2); }
 
+namespace sdf {
+
+// Grid geometry of a plan: padded sizes, bins, node counts, defaults.
+void plan_geometry(sdf_plan_impl *p, int D, const int64_t *dims, double h, double tau, int precision,
+                   unsigned outputs, void *stream) {
+    p->D = D;
+    p->prec = precision;
+    outputs |= SDF_OUT_S;
+    if (outputs & SDF_OUT_D2S) outputs |= SDF_OUT_DS;
+    p->outputs = outputs;
+    p->h = h;
+    p->tau = tau;
+    p->stream = reinterpret_cast<cudaStream_t>(stream);
+    p->nnodes = 1;
+    p->nbins = 1;
+    for (int a = 0; a < 3; ++a) {
+        p->N[a] = (a < D) ? dims[a] : 1;
+        p->M[a] = (a < D) ? std::max<int64_t>(16, next_pow2(2 * p->N[a] - 1)) : 1;
+        int l = 0;
+        while ((int64_t(1) << l) < p->M[a]) ++l;
+        p->logM[a] = l;
+        p->nb[a] = (p->N[a] + kBin - 1) / kBin;
+        p->nnodes *= p->N[a];
+        p->nbins *= p->nb[a];
+    }
+    for (int i = 0; i < KER_COUNT; ++i) p->kslot[i] = -1;
+    p->noise_c32 = kNoiseC32;
+    p->noise_c64 = kNoiseC64;
+}
+
+// Kernels the requested outputs need.
+std::vector<int> plan_kernel_ids(const sdf_plan_impl *p) {
+    const int D = p->D;
+    const bool ds = p->outputs & SDF_OUT_DS, d2 = p->outputs & SDF_OUT_D2S, sg = p->outputs & SDF_OUT_SIGN;
+    std::vector<int> ids = {KER_PHI};
+    if (ds) {
+        ids.push_back(KER_GX);
+        ids.push_back(KER_GY);
+        if (D == 3) ids.push_back(KER_GZ);
+    }
+    if (d2) {
+        ids.push_back(KER_HXX);
+        ids.push_back(KER_HYY);
+        if (D == 3) ids.push_back(KER_HZZ);
+        ids.push_back(KER_HXY);
+        if (D == 3) {
+            ids.push_back(KER_HXZ);
+            ids.push_back(KER_HYZ);
+        }
+    }
+    if (sg) {
+        ids.push_back(KER_W1);
+        ids.push_back(KER_W2);
+        if (D == 3) ids.push_back(KER_W3);
+    }
+    return ids;
+}
+
+// Transform programme (input fields, packed output groups) and the noise-model
+// factor Q; needs the kernel l1 norms.
+void plan_programme(sdf_plan_impl *p) {
+    const int D = p->D;
+    const double tau = p->tau;
+    const bool ds = p->outputs & SDF_OUT_DS, d2 = p->outputs & SDF_OUT_D2S, sg = p->outputs & SDF_OUT_SIGN;
+    p->nfield = sg ? (D == 2 ? 2 : 3) : 1;
+    p->ngroup = 0;
+    if (D == 2) {
+        add_pair(p, KER_PHI, CH_PHI, ds ? KER_GX : -1, CH_GX);
+        if (ds) add_pair(p, KER_GY, CH_GY, d2 ? KER_HXX : -1, CH_HXX);
+        if (d2) add_pair(p, KER_HYY, CH_HYY, KER_HXY, CH_HXY);
+    } else {
+        add_pair(p, KER_PHI, CH_PHI, ds ? KER_GX : -1, CH_GX);
+        if (ds) add_pair(p, KER_GY, CH_GY, KER_GZ, CH_GZ);
+        if (d2) {
+            add_pair(p, KER_HXX, CH_HXX, KER_HYY, CH_HYY);
+            add_pair(p, KER_HZZ, CH_HZZ, KER_HXY, CH_HXY);
+            add_pair(p, KER_HXZ, CH_HXZ, KER_HYZ, CH_HYZ);
+        }
+    }
+    if (sg) add_mu(p);
+    // noise-model factor Q (how phi's error enters each requested output).
+    // Noise of a channel ~ the larger stored l1 norm of its packed pair,
+    // times the channel's unscale factor.
+    const Channel base_ch[] = {CH_PHI, CH_GX, CH_GY, CH_GZ, CH_HXX, CH_HYY, CH_HZZ, CH_HXY, CH_HXZ, CH_HYZ};
+    const int base_k[] = {KER_PHI, KER_GX, KER_GY, KER_GZ, KER_HXX, KER_HYY, KER_HZZ, KER_HXY, KER_HXZ, KER_HYZ};
+    auto kern_of = [&](int ch) {
+        for (int i = 0; i < 10; ++i)
+            if (base_ch[i] == ch) return base_k[i];
+        return -1;
+    };
+    auto stored_l1 = [&](int ch) {
+        const int id = kern_of(ch);
+        if (id < 0 || p->kslot[id] < 0) return 0.0;
+        const KernelSpec &k = p->kernels[p->kslot[id]];
+        return k.l1 * k.scale;
+    };
+    double f = 0, gmax = 0, hmax = 0;
+    for (int g = 0; g < p->ngroup; ++g) {
+        const double pair = std::max(stored_l1(p->gch[g][0]), stored_l1(p->gch[g][1]));
+        for (int hh = 0; hh < 2; ++hh) {
+            const int ch = p->gch[g][hh];
+            const int id = kern_of(ch);
+            if (id < 0) continue;
+            const double n = pair / p->kernels[p->kslot[id]].scale;
+            if (ch == CH_PHI) f = n;
+            else if (ch >= CH_GX && ch <= CH_GZ) gmax = std::max(gmax, n);
+            else hmax = std::max(hmax, n);
+        }
+    }
+    double q = f;
+    if (ds) q = std::max(q, f + gmax);
+    if (d2) q = std::max(q, tau * hmax + 2 * gmax + 2 * f);
+    p->q_factor = q;
+}
+
+// Sizes of the two transform buffers (bytesA, bytesB).
+void plan_buffer_sizes(sdf_plan_impl *p) {
+    const int64_t N1 = p->N[1], N2 = p->N[2], M0 = p->M[0], M1 = p->M[1];
+    const int64_t ng = std::max(p->ngroup, 2);
+    const int64_t nf = p->nfield;
+    int64_t a, b;
+    if (p->D == 2) {
+        a = nf * M0 * N1;
+        b = ng * M0 * N1;
+    } else {
+        a = std::max(nf * M0 * N2 * N1, ng * M1 * M0 * N2);
+        b = std::max(nf * M1 * M0 * N2, ng * M0 * N2 * N1);
+    }
+    p->bytesA = a * vbytes(p);
+    p->bytesB = b * vbytes(p);
+}
+
+}  // namespace sdf
+
 static cudaError_t alloc(void **ptr, size_t bytes, size_t *acc) {
     cudaError_t e = cudaMalloc(ptr, bytes);
     if (e == cudaSuccess && acc) *acc += bytes;
@@ -247,52 +383,9 @@ sdf_status sdf_plan_create(sdf_plan *out, int D, const int64_t *dims, double h, 
     auto t0 = std::chrono::steady_clock::now();
     sdf_plan_s *p = new (std::nothrow) sdf_plan_s();
     if (!p) return SDF_ERR_OOM;
-    p->D = D;
-    p->prec = precision;
-    outputs |= SDF_OUT_S;
-    if (outputs & SDF_OUT_D2S) outputs |= SDF_OUT_DS;
-    p->outputs = outputs;
-    p->h = h;
-    p->tau = tau;
-    p->stream = reinterpret_cast<cudaStream_t>(stream);
-    p->nnodes = 1;
-    p->nbins = 1;
-    for (int a = 0; a < 3; ++a) {
-        p->N[a] = (a < D) ? dims[a] : 1;
-        p->M[a] = (a < D) ? std::max<int64_t>(16, next_pow2(2 * p->N[a] - 1)) : 1;
-        int l = 0;
-        while ((int64_t(1) << l) < p->M[a]) ++l;
-        p->logM[a] = l;
-        p->nb[a] = (p->N[a] + kBin - 1) / kBin;
-        p->nnodes *= p->N[a];
-        p->nbins *= p->nb[a];
-    }
-    for (int i = 0; i < KER_COUNT; ++i) p->kslot[i] = -1;
-    p->noise_c32 = kNoiseC32;
-    p->noise_c64 = kNoiseC64;
-
-    const bool ds = outputs & SDF_OUT_DS, d2 = outputs & SDF_OUT_D2S, sg = outputs & SDF_OUT_SIGN;
-    std::vector<int> ids = {KER_PHI};
-    if (ds) {
-        ids.push_back(KER_GX);
-        ids.push_back(KER_GY);
-        if (D == 3) ids.push_back(KER_GZ);
-    }
-    if (d2) {
-        ids.push_back(KER_HXX);
-        ids.push_back(KER_HYY);
-        if (D == 3) ids.push_back(KER_HZZ);
-        ids.push_back(KER_HXY);
-        if (D == 3) {
-            ids.push_back(KER_HXZ);
-            ids.push_back(KER_HYZ);
-        }
-    }
-    if (sg) {
-        ids.push_back(KER_W1);
-        ids.push_back(KER_W2);
-        if (D == 3) ids.push_back(KER_W3);
-    }
+    plan_geometry(p, D, dims, h, tau, precision, outputs, stream);
+    outputs = p->outputs;
+    const std::vector<int> ids = plan_kernel_ids(p);
     cudaError_t e;
 #define PCK(x)                          \
     do {                                \
@@ -310,74 +403,10 @@ sdf_status sdf_plan_create(sdf_plan *out, int D, const int64_t *dims, double h, 
         else PCK(upload_twiddles<float>(&p->tw[a], p->M[a], &p->workspace_bytes));
     }
     PCK(build_kernel_list(p, ids));
-    // transform programme
-    p->nfield = sg ? (D == 2 ? 2 : 3) : 1;
-    p->ngroup = 0;
-    if (D == 2) {
-        add_pair(p, KER_PHI, CH_PHI, ds ? KER_GX : -1, CH_GX);
-        if (ds) add_pair(p, KER_GY, CH_GY, d2 ? KER_HXX : -1, CH_HXX);
-        if (d2) add_pair(p, KER_HYY, CH_HYY, KER_HXY, CH_HXY);
-    } else {
-        add_pair(p, KER_PHI, CH_PHI, ds ? KER_GX : -1, CH_GX);
-        if (ds) add_pair(p, KER_GY, CH_GY, KER_GZ, CH_GZ);
-        if (d2) {
-            add_pair(p, KER_HXX, CH_HXX, KER_HYY, CH_HYY);
-            add_pair(p, KER_HZZ, CH_HZZ, KER_HXY, CH_HXY);
-            add_pair(p, KER_HXZ, CH_HXZ, KER_HYZ, CH_HYZ);
-        }
-    }
-    if (sg) add_mu(p);
-    // noise-model factor Q (how phi's error enters each requested output)
-    {
-        // Noise of a channel ~ the larger stored l1 norm of its packed pair,
-        // times the channel's unscale factor.
-        const Channel base_ch[] = {CH_PHI, CH_GX, CH_GY, CH_GZ, CH_HXX, CH_HYY, CH_HZZ, CH_HXY, CH_HXZ, CH_HYZ};
-        const int base_k[] = {KER_PHI, KER_GX, KER_GY, KER_GZ, KER_HXX, KER_HYY, KER_HZZ, KER_HXY, KER_HXZ, KER_HYZ};
-        auto kern_of = [&](int ch) {
-            for (int i = 0; i < 10; ++i)
-                if (base_ch[i] == ch) return base_k[i];
-            return -1;
-        };
-        auto stored_l1 = [&](int ch) {
-            const int id = kern_of(ch);
-            if (id < 0 || p->kslot[id] < 0) return 0.0;
-            const KernelSpec &k = p->kernels[p->kslot[id]];
-            return k.l1 * k.scale;
-        };
-        double f = 0, gmax = 0, hmax = 0;
-        for (int g = 0; g < p->ngroup; ++g) {
-            const double pair = std::max(stored_l1(p->gch[g][0]), stored_l1(p->gch[g][1]));
-            for (int hh = 0; hh < 2; ++hh) {
-                const int ch = p->gch[g][hh];
-                const int id = kern_of(ch);
-                if (id < 0) continue;
-                const double n = pair / p->kernels[p->kslot[id]].scale;
-                if (ch == CH_PHI) f = n;
-                else if (ch >= CH_GX && ch <= CH_GZ) gmax = std::max(gmax, n);
-                else hmax = std::max(hmax, n);
-            }
-        }
-        double q = f;
-        if (ds) q = std::max(q, f + gmax);
-        if (d2) q = std::max(q, tau * hmax + 2 * gmax + 2 * f);
-        p->q_factor = q;
-    }
+    plan_programme(p);
     // workspace
     {
-        const int64_t N0 = p->N[0], N1 = p->N[1], N2 = p->N[2], M0 = p->M[0], M1 = p->M[1];
-        const int64_t ng = std::max(p->ngroup, 2);
-        const int64_t nf = p->nfield;
-        int64_t a, b;
-        if (D == 2) {
-            a = nf * M0 * N1;
-            b = ng * M0 * N1;
-        } else {
-            a = std::max(nf * M0 * N2 * N1, ng * M1 * M0 * N2);
-            b = std::max(nf * M1 * M0 * N2, ng * M0 * N2 * N1);
-        }
-        (void)N0;
-        p->bytesA = a * vbytes(p);
-        p->bytesB = b * vbytes(p);
+        plan_buffer_sizes(p);
         PCK(alloc(&p->bufA, p->bytesA, &p->workspace_bytes));
         PCK(alloc(&p->bufB, p->bytesB, &p->workspace_bytes));
         const int64_t nb = p->nbins;

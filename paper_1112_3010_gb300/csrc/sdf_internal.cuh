@@ -140,6 +140,18 @@ cudaError_t launch_adjoint(sdf_plan_impl *p, int64_t K, const double *points, do
 
 double hessian_scale(const sdf_plan_impl *p);
 
+// plan set-up steps shared by sdf_plan_create and sdf_execute_noalloc
+void plan_geometry(sdf_plan_impl *p, int D, const int64_t *dims, double h, double tau, int precision,
+                   unsigned outputs, void *stream);
+std::vector<int> plan_kernel_ids(const sdf_plan_impl *p);
+void plan_programme(sdf_plan_impl *p);
+void plan_buffer_sizes(sdf_plan_impl *p);
+int kernel_parity(int id, int D);
+void set_last_error(const char *msg);  // text returned by sdf_last_error()
+constexpr int kSpectraParts = 1024;
+cudaError_t build_spectra_into(sdf_plan_impl *p, double2 *bufX, double2 *bufY, double *part, double *host_part,
+                               double2 *const *tw64);
+
 // noise model: floor_p = C_p u_p sqrt(log2 n) ||k||_1 ||g||_2 / sqrt(n), theta = floor/eps
 constexpr double kTrustEps = 2.5e-4;
 

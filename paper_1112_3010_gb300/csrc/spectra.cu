@@ -235,4 +235,58 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
 
 int kernel_parity(int id, int D) { return parity_of(id, D); }
 
+// The same sampling, FP64 transform and compression as build_spectra, into
+// memory the caller provides: bufX and bufY (prod(M) double2 each), part
+// (kSpectraParts doubles), tw64[a] (M_a double2, already filled) and each
+// p->kernels[i].c (compressed spectrum).  host_part receives kSpectraParts
+// doubles.  Allocates nothing; synchronises the stream once per kernel.
+cudaError_t build_spectra_into(sdf_plan_impl *p, double2 *bufX, double2 *bufY, double *part, double *host_part,
+                               double2 *const *tw64) {
+    cudaError_t e = cudaSuccess;
+    const int D = p->D;
+    cudaStream_t st = p->stream;
+    int64_t total = 1;
+    for (int a = 0; a < D; ++a) total *= p->M[a];
+    const int nblk = kSpectraParts;
+    const double inv_n = 1.0 / (double)total;
+    for (auto &ks : p->kernels) {
+        SampleCfg c;
+        c.D = D;
+        for (int a = 0; a < 3; ++a) {
+            c.M[a] = p->M[a];
+            c.N[a] = p->N[a];
+        }
+        c.h = p->h;
+        c.tau = p->tau;
+        c.id = ks.id;
+        k_sample<<<nblk, 256, 0, st>>>(c, bufX, part, total);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        double2 *src = bufX, *dst = bufY;
+        for (int a = 0; a < D; ++a) {
+            const int64_t L = p->M[a];
+            if ((e = fwd_T_launch<double>(src, dst, p->logM[a], (int)L, total / L, 1, 0, 0, tw64[a], st,
+                                          nullptr)) != cudaSuccess)
+                return e;
+            std::swap(src, dst);
+        }
+        if ((e = cudaMemcpyAsync(host_part, part, sizeof(double) * nblk, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
+            return e;
+        const int nodd = __builtin_popcount((unsigned)ks.parity);
+        const double scale = inv_n * ks.scale;
+        if (p->prec == SDF_FP64)
+            k_compress<double><<<1024, 256, 0, st>>>(src, reinterpret_cast<double *>(ks.c), D, p->M[0], p->M[1],
+                                                     p->M[2], nodd, scale, nullptr);
+        else
+            k_compress<float><<<1024, 256, 0, st>>>(src, reinterpret_cast<float *>(ks.c), D, p->M[0], p->M[1],
+                                                    p->M[2], nodd, scale, nullptr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        double l1 = 0.0;
+        for (int i = 0; i < nblk; ++i) l1 += host_part[i];
+        ks.l1 = l1;
+    }
+    return e;
+}
+
 }  // namespace sdf
