@@ -110,6 +110,7 @@ typedef struct {
     int64_t n_fixup_nodes;  /* nodes it recomputed                            */
     int64_t n_capped;    /* nodes returned as S_cap                            */
     int64_t n_launches;  /* kernels the last execute launched                  */
+    int64_t n_fixup_terms;  /* (node, occupied node) terms the fix-up summed   */
 } sdf_exec_stats;
 
 /* Per-kernel device time, filled by sdf_profile_read(). */

@@ -59,7 +59,8 @@ class ExecStats(ctypes.Structure):
     _fields_ = [("theta64", ctypes.c_double), ("theta32", ctypes.c_double), ("s_cap", ctypes.c_double),
                 ("g_norm2", ctypes.c_double), ("n_unique", ctypes.c_int64),
                 ("n_fixup_tiles", ctypes.c_int64), ("n_fixup_nodes", ctypes.c_int64),
-                ("n_capped", ctypes.c_int64), ("n_launches", ctypes.c_int64)]
+                ("n_capped", ctypes.c_int64), ("n_launches", ctypes.c_int64),
+                ("n_fixup_terms", ctypes.c_int64)]
 
 
 class KernelTime(ctypes.Structure):

@@ -579,6 +579,7 @@ sdf_status sdf_get_stats(sdf_plan p, sdf_exec_stats *st) {
     st->n_fixup_nodes = (int64_t)d.n_fixup_nodes;
     st->n_capped = (int64_t)d.n_capped;
     st->n_launches = p->nlaunch;
+    st->n_fixup_terms = (int64_t)d.n_fixup_terms;
     return SDF_OK;
 }
 

@@ -9,12 +9,14 @@
 // but gives no mechanism; this one is ours.
 //
 // One CTA per flagged 8^D tile (one thread per node).  Candidate bins are
-// visited in rings of Chebyshev distance k = 0, 1, 2, ... around the tile,
-// and the search stops once every node of the ring lies farther than
-// min_k r_k + c_cut from every flagged node (c_cut = tau ln(K/1e-7), so the
-// dropped terms weigh less than 1e-7 of the sum).  A tile whose nearest
-// occupied bin is so far that K exp(-d/tau) < theta_64 keeps the capped value.
-// Visiting order is fixed, so the sums are deterministic.
+// visited in rings of Chebyshev distance k = 0, 1, 2, ... around the tile;
+// after ring k every unvisited occupied node lies at least lb = (8k+1)h from
+// every node of the tile, so a node stops summing once K exp(-(lb - m)/tau)
+// is below 1e-5 of its sum, or once even its sum plus K exp(-lb/tau) is below
+// theta_64 (it stays capped).  Terms beyond m + tau ln(K 1e5) are skipped.  A
+// tile whose nearest occupied bin is so far that K exp(-d/tau) < theta_64
+// keeps the capped value.  Visiting order is fixed, so the sums are
+// deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -81,9 +83,8 @@ template <int D, typename TO>
 __global__ void __launch_bounds__(D == 2 ? 64 : 512) k_fixup(FixParams P) {
     constexpr int NT = (D == 2) ? 64 : 512;
     constexpr int NH = D * (D + 1) / 2;
-    __shared__ int cx[kFixCap], cy[kFixCap], cz[kFixCap], cc[kFixCap];
+    __shared__ int4 cell[kFixCap];  // (x, y, z, count) of staged occupied nodes
     __shared__ int soff[1];
-    __shared__ float red[NT];
     __shared__ int wtot[32];
     const int64_t b = blockIdx.x;
     if (!P.tile_flag[b]) return;
@@ -99,32 +100,24 @@ __global__ void __launch_bounds__(D == 2 ? 64 : 512) k_fixup(FixParams P) {
     const int x = bx * 8 + (tid & 7), y = by * 8 + ((tid >> 3) & 7), z = bz * 8 + (tid >> 6);
     const bool inb = x < P.N0 && y < P.N1 && (D == 2 || z < P.N2);
     const int64_t node = (int64_t)x + (int64_t)P.N0 * (y + (int64_t)P.N1 * z);
-    bool mine = false;
-    if (inb) mine = (P.flags[node] & SDF_FLAG_CAPPED) != 0;
-    const float h = (float)P.h, tau = (float)P.tau;
+    const bool mine = inb && (P.flags[node] & SDF_FLAG_CAPPED) != 0;
+    bool active = mine;      // still summing
+    bool early_cap = false;  // shown below theta_64 before the sum finished
+    const float h = (float)P.h, tau = (float)P.tau, itau = 1.f / tau, ih = 1.f / h;
     const float l2e_tau = 1.4426950408889634f / tau;
-    const float ccut = (float)(P.tau * (P.logK + 16.118095650958319));  // tau ln(K / 1e-7)
+    // terms beyond m + ccut weigh < 1e-5 of the sum in total (K of them at most)
+    const float lnK = (float)P.logK;
+    const float ccut = tau * (lnK + 11.512925f);
     float m = INFINITY, sE = 0.f, sG[D], sH[NH];
 #pragma unroll
     for (int a = 0; a < D; ++a) sG[a] = 0.f;
 #pragma unroll
     for (int a = 0; a < NH; ++a) sH[a] = 0.f;
+    unsigned long long nterm = 0;
 
     const int kmax = max(max(P.nb0, P.nb1), (D == 3) ? P.nb2 : 0);
     for (int k = 0; k <= kmax; ++k) {
-        // stop when the ring is beyond every flagged node's cut-off
-        if (k >= 2) {
-            red[tid] = mine ? m + ccut : -INFINITY;
-            __syncthreads();
-            for (int s = NT / 2; s > 0; s >>= 1) {
-                if (tid < s) red[tid] = fmaxf(red[tid], red[tid + s]);
-                __syncthreads();
-            }
-            const float need = red[0];
-            __syncthreads();
-            const float lb = (8.f * (k - 1) + 1.f) * h;
-            if (!(lb <= need)) break;
-        }
+        if (!__syncthreads_or(active)) break;
         const int nring = (k == 0) ? 1 : ((D == 2) ? 8 * k : (2 * k + 1) * (2 * k + 1) * (2 * k + 1) -
                                                                 (2 * k - 1) * (2 * k - 1) * (2 * k - 1));
         for (int i0 = 0; i0 < nring;) {
@@ -166,29 +159,27 @@ __global__ void __launch_bounds__(D == 2 ? 64 : 512) k_fixup(FixParams P) {
             const bool take = (i < nring) && (off + nb <= kFixCap);
             const int taken = __syncthreads_count(take);  // taken bins form a prefix
             if (tid == taken - 1) soff[0] = off + nb;
-            __syncthreads();
-            const int ncell = (taken > 0) ? soff[0] : 0;
-            // copy cells of taken bins
             if (take && nb > 0) {
                 const int s0 = P.bin_start[gb];
-                const int qb = gb;
-                const int qx = qb % P.nb0, qy = (qb / P.nb0) % P.nb1, qz = qb / (P.nb0 * P.nb1);
+                const int qx = gb % P.nb0, qy = (gb / P.nb0) % P.nb1, qz = gb / (P.nb0 * P.nb1);
                 for (int e = 0; e < nb; ++e) {
                     const int lc = P.ucell[s0 + e];
-                    cx[off + e] = qx * 8 + (lc & 7);
-                    cy[off + e] = qy * 8 + ((lc >> 3) & 7);
-                    cz[off + e] = qz * 8 + (lc >> 6);
-                    cc[off + e] = P.ucount[s0 + e];
+                    cell[off + e] = make_int4(qx * 8 + (lc & 7), qy * 8 + ((lc >> 3) & 7), qz * 8 + (lc >> 6),
+                                              P.ucount[s0 + e]);
                 }
             }
             __syncthreads();
-            if (mine) {
+            const int ncell = (taken > 0) ? soff[0] : 0;
+            if (active) {
                 for (int e = 0; e < ncell; ++e) {
-                    const int ddx = x - cx[e], ddy = y - cy[e], ddz = (D == 3) ? z - cz[e] : 0;
+                    const int4 q = cell[e];
+                    const int ddx = x - q.x, ddy = y - q.y, ddz = (D == 3) ? z - q.z : 0;
                     const int r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    const float rg = sqrtf((float)r2);
-                    const float r = rg * h;
+                    // r = h sqrt(r2) and 1/sqrt(r2) from one reciprocal square root
+                    const float ir = r2 > 0 ? rsqrtf((float)r2) : 0.f;
+                    const float r = (float)r2 * ir * h;
                     if (r - m > ccut) continue;
+                    ++nterm;
                     if (r < m) {
                         const float sc = exp2f((r - m) * l2e_tau);
                         sE *= sc;
@@ -198,28 +189,46 @@ __global__ void __launch_bounds__(D == 2 ? 64 : 512) k_fixup(FixParams P) {
                         for (int a = 0; a < NH; ++a) sH[a] *= sc;
                         m = r;
                     }
-                    const float E = (float)cc[e] * exp2f((m - r) * l2e_tau);
+                    const float E = (float)q.w * exp2f((m - r) * l2e_tau);
                     sE += E;
                     if (r2 > 0) {
-                        const float ir = 1.f / rg;
-                        const float n0 = ddx * ir, n1 = ddy * ir, n2 = ddz * ir;
-                        const float nn[3] = {n0, n1, n2};
-                        const float irw = 1.f / r, it = 1.f / tau;
+                        const float nn[3] = {ddx * ir, ddy * ir, ddz * ir};
+                        const float irw = ir * ih;  // 1/r in world units
 #pragma unroll
                         for (int a = 0; a < D; ++a) sG[a] += E * nn[a];
-                        int q = 0;
+                        int qh = 0;
 #pragma unroll
-                        for (int a = 0; a < D; ++a, ++q) sH[q] += E * ((1.f - nn[a] * nn[a]) * irw - nn[a] * nn[a] * it);
+                        for (int a = 0; a < D; ++a, ++qh)
+                            sH[qh] += E * ((1.f - nn[a] * nn[a]) * irw - nn[a] * nn[a] * itau);
 #pragma unroll
                         for (int a = 0; a < D; ++a)
 #pragma unroll
-                            for (int bb = a + 1; bb < D; ++bb, ++q) sH[q] += E * (-nn[a] * nn[bb] * (irw + it));
+                            for (int bb = a + 1; bb < D; ++bb, ++qh) sH[qh] -= E * nn[a] * nn[bb] * (irw + itau);
                     }
                 }
             }
             __syncthreads();
             i0 += max(taken, 1);
-            if (taken == 0) break;  // cannot happen: one bin never exceeds kFixCap
+        }
+        // after ring k every unvisited node lies at least lb from this tile
+        if (active) {
+            const float lb = (8.f * k + 1.f) * h;
+            const float tailA = -lb * itau + lnK;                 // log of K exp(-lb/tau)
+            if (m < INFINITY) {
+                const float lsE = logf(sE);
+                // the rest adds less than 1e-5 of the sum: final
+                if ((lb - m) * itau >= lnK - lsE + 11.512925f) active = false;
+                // phi < theta_64 whatever the rest adds: capped
+                const float A = -m * itau + lsE;
+                const float hi = fmaxf(A, tailA), lo = fminf(A, tailA);
+                if (hi + log1pf(expf(lo - hi)) < (float)lt - 1e-4f) {
+                    active = false;
+                    early_cap = true;
+                }
+            } else if (tailA < (float)lt - 1e-4f) {
+                active = false;
+                early_cap = true;
+            }
         }
     }
     int fixed = 0, capped = 0;
@@ -230,7 +239,7 @@ __global__ void __launch_bounds__(D == 2 ? 64 : 512) k_fixup(FixParams P) {
         TO *dS = reinterpret_cast<TO *>(P.dS);
         TO *d2S = reinterpret_cast<TO *>(P.d2S);
         const double sg = (P.sign && P.sign[node] < 0) ? -1.0 : 1.0;
-        if (!(S <= scap)) {
+        if (early_cap || !(S <= scap)) {
             capped = 1;
             P.flags[node] = SDF_FLAG_CAPPED | SDF_FLAG_FIXUP;
         } else {
@@ -245,23 +254,24 @@ __global__ void __launch_bounds__(D == 2 ? 64 : 512) k_fixup(FixParams P) {
             }
             if (d2S) {
                 int q = 0;
-                const float it = 1.f / tau;
 #pragma unroll
-                for (int a = 0; a < D; ++a, ++q) d2S[q * P.nnodes + node] = (TO)(sH[q] * inv + g[a] * g[a] * it);
+                for (int a = 0; a < D; ++a, ++q) d2S[q * P.nnodes + node] = (TO)(sH[q] * inv + g[a] * g[a] * itau);
 #pragma unroll
                 for (int a = 0; a < D; ++a)
 #pragma unroll
                     for (int bb = a + 1; bb < D; ++bb, ++q)
-                        d2S[q * P.nnodes + node] = (TO)(sH[q] * inv + g[a] * g[bb] * it);
+                        d2S[q * P.nnodes + node] = (TO)(sH[q] * inv + g[a] * g[bb] * itau);
             }
             P.flags[node] = SDF_FLAG_FIXUP;
         }
     }
     // statistics
     const unsigned fb = __ballot_sync(0xffffffffu, fixed), cb = __ballot_sync(0xffffffffu, capped);
+    for (int o = 16; o > 0; o >>= 1) nterm += __shfl_down_sync(0xffffffffu, nterm, o);
     if ((tid & 31) == 0) {
         if (fb) atomicAdd(&P.dsc_w->n_fixup_nodes, (unsigned long long)__popc(fb));
         if (cb) atomicAdd(&P.dsc_w->n_capped, (unsigned long long)__popc(cb));
+        if (nterm) atomicAdd(&P.dsc_w->n_fixup_terms, nterm);
     }
     if (tid == 0) atomicAdd(&P.dsc_w->n_fixup_tiles, 1ull);
 }

@@ -57,7 +57,7 @@ struct DevScalars {
     int pad0;
     unsigned long long wmax;    // bits of max |weight| (positive doubles order as integers)
     unsigned long long sum_c2;  // sum over nodes of count^2
-    unsigned long long n_fixup_tiles, n_fixup_nodes, n_capped;
+    unsigned long long n_fixup_tiles, n_fixup_nodes, n_capped, n_fixup_terms;
     int64_t n_unique;
     double dl_dtau_acc;         // adjoint partial sum (deterministic order not required)
 };
