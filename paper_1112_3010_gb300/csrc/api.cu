@@ -329,6 +329,8 @@ static void free_plan(sdf_plan_impl *p) {
     cudaFree(p->sign_int);
     cudaFree(p->dsc);
     cudaFree(p->staging);
+    cudaFree(p->adj_planes);
+    cudaFree(p->adj_part);
     if (p->hsc) cudaFreeHost(p->hsc);
     for (auto &r : p->prof_recs) {
         if (r.a) cudaEventDestroy(r.a);
@@ -634,7 +636,11 @@ sdf_status sdf_backward(sdf_plan p, int64_t K, const double *points, const void 
     if (!p || !points || !w || !S_saved || !dL_dY || !dL_dtau) return SDF_ERR_INVALID_ARG;
     if (!(p->outputs & SDF_OUT_DS)) return SDF_ERR_INVALID_ARG;
     if (K < 1 || K >= (int64_t(1) << 31) - 1) return SDF_ERR_INVALID_ARG;
-    return (sdf_status)SDF_ERR_UNSUPPORTED;  // filled in by adjoint.cu
+    CK(ensure_points(p, K));
+    p->last_K = K;
+    p->nlaunch = 0;
+    CK(launch_adjoint(p, K, points, w, S_saved, flags, dL_dY, dL_dtau));
+    return SDF_OK;
 }
 
 }  // extern "C"

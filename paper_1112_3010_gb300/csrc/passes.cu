@@ -496,17 +496,20 @@ template cudaError_t fwd_T_launch<double>(const double2 *, double2 *, int, int, 
 template cudaError_t fwd_T_launch<float>(const float2 *, float2 *, int, int, int64_t, int, int64_t, int64_t,
                                          const float2 *, cudaStream_t, sdf_plan_impl *);
 
-static FusedParams make_fused_params(const sdf_plan_impl *p) {
+// adj: the adjoint programme (transform of a = w/phi) instead of the forward one
+static FusedParams make_fused_params(const sdf_plan_impl *p, bool adj = false) {
     FusedParams F;
     memset(&F, 0, sizeof(F));
-    F.ngroup = p->ngroup;
-    for (int g = 0; g < p->ngroup; ++g) {
-        F.nterm[g] = p->group[g].nterm;
-        for (int k = 0; k < p->group[g].nterm; ++k) {
-            F.tk[g][k] = p->group[g].term[k].kslot;
-            F.tf[g][k] = p->group[g].term[k].field;
-            F.br[g][k] = p->group[g].term[k].br;
-            F.bi[g][k] = p->group[g].term[k].bi;
+    const int ng = adj ? p->adj_ngroup : p->ngroup;
+    const Group *grp = adj ? p->adj_group : p->group;
+    F.ngroup = ng;
+    for (int g = 0; g < ng; ++g) {
+        F.nterm[g] = grp[g].nterm;
+        for (int k = 0; k < grp[g].nterm; ++k) {
+            F.tk[g][k] = grp[g].term[k].kslot;
+            F.tf[g][k] = grp[g].term[k].field;
+            F.br[g][k] = grp[g].term[k].br;
+            F.bi[g][k] = grp[g].term[k].bi;
         }
     }
     for (size_t s = 0; s < p->kernels.size() && s < (size_t)kMaxKernels; ++s) {
@@ -584,7 +587,7 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         while (R * 2 * TPL <= 256) R *= 2;
         LineCfg c = line_cfg(logL, R);
         const size_t smem = (size_t)R * c.PL * sizeof(V);
-        FusedParams F = make_fused_params(p);
+        FusedParams F = make_fused_params(p, dense_in != nullptr);
         if (dense_in) F.nfield = 1;
         const int64_t n_out = (D == 2) ? N1 : N2;
         const int64_t out_fs = fused_lines * n_out;
@@ -713,6 +716,89 @@ cudaError_t launch_inverse_epilogue(sdf_plan_impl *p, bool with_weights, void *S
                                     uint8_t *flags) {
     if (p->prec == SDF_FP64) return inverse_epilogue_impl<double>(p, with_weights, S, dS, d2S, sign, flags);
     return inverse_epilogue_impl<float>(p, with_weights, S, dS, d2S, sign, flags);
+}
+
+// ---------------------------------------------------------------- adjoint epilogue
+// Last inverse pass of the adjoint: the real / imaginary part of each group
+// goes to dense plane plane[g][0|1] (-1: dropped), node order x fastest.
+struct DenseParams {
+    int ngroup;
+    int plane[2][2];
+    int64_t in_fs, nnodes;
+    int N0;
+};
+
+template <typename T>
+__global__ void SDF_LB(T) k_epi_dense(const cx<T> *__restrict__ in, int logL, int R, int64_t n_lines, DenseParams P,
+                                      T *planes, const cx<T> *__restrict__ tw) {
+    using V = cx<T>;
+    extern __shared__ unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int tid = threadIdx.x, lr = tid % R, t = tid / R;
+    const int64_t line = (int64_t)blockIdx.x * R + lr;
+    const bool valid = line < n_lines;
+    V *my = sm + lr * PL;
+    for (int g = 0; g < P.ngroup; ++g) {
+        V v[16];
+        const V *src = in + g * P.in_fs + line;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
+        __syncthreads();
+        fft_line<true>(v, my, t, logL, tw);
+        if (!valid) continue;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int x = t + m * TPL;
+            if (x >= P.N0) continue;
+            const int64_t node = line * P.N0 + x;
+            if (P.plane[g][0] >= 0) planes[P.plane[g][0] * P.nnodes + node] = v[m].x;
+            if (P.plane[g][1] >= 0) planes[P.plane[g][1] * P.nnodes + node] = v[m].y;
+        }
+    }
+}
+
+// Transform a = w/phi (dense x-pass, [y-pass], fused pass with the adjoint
+// programme, [inverse y-pass]) and write the D+1 convolution planes
+// (a * k_x, a * k_y[, a * k_z], a * (|X| f)) to p->adj_planes.
+template <typename T>
+static cudaError_t adjoint_transforms_impl(sdf_plan_impl *p, const void *w, const void *S_saved,
+                                           const uint8_t *flags) {
+    using V = cx<T>;
+    const void *pair[2] = {w, S_saved};
+    cudaError_t e = forward_impl<T>(p, false, pair, flags);
+    if (e != cudaSuccess) return e;
+    const V *lin = nullptr;
+    if ((e = inverse_mid<T>(p, p->adj_ngroup, &lin)) != cudaSuccess) return e;
+    const int D = p->D;
+    const int64_t N1 = p->N[1], N2 = p->N[2], M0 = p->M[0];
+    const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
+    DenseParams P;
+    memset(&P, 0, sizeof(P));
+    P.ngroup = p->adj_ngroup;
+    for (int g = 0; g < p->adj_ngroup; ++g)
+        for (int hh = 0; hh < 2; ++hh) {
+            const int ch = p->adj_gch[g][hh];
+            P.plane[g][hh] = ch == CH_AGX ? 0 : ch == CH_AGY ? 1 : ch == CH_AGZ ? 2 : ch == CH_ARF ? D : -1;
+        }
+    P.in_fs = M0 * n_lines;
+    P.nnodes = p->nnodes;
+    P.N0 = (int)p->N[0];
+    const int logL = p->logM[0];
+    const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
+    LineCfg c = line_cfg(logL, R);
+    const size_t smem = (size_t)R * c.PL * sizeof(V);
+    if ((e = set_smem<T>((const void *)k_epi_dense<T>, smem)) != cudaSuccess) return e;
+    prof_begin(p, "epi_dense", p->stream);
+    k_epi_dense<T><<<(unsigned)((n_lines + R - 1) / R), R * c.TPL, smem, p->stream>>>(
+        lin, logL, R, n_lines, P, reinterpret_cast<T *>(p->adj_planes), reinterpret_cast<const V *>(p->tw[0]));
+    prof_end(p, p->stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_transforms(sdf_plan_impl *p, const void *w, const void *S_saved, const uint8_t *flags) {
+    if (p->prec == SDF_FP64) return adjoint_transforms_impl<double>(p, w, S_saved, flags);
+    return adjoint_transforms_impl<float>(p, w, S_saved, flags);
 }
 
 }  // namespace sdf

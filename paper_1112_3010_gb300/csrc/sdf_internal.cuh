@@ -114,6 +114,12 @@ struct sdf_plan_impl {
     size_t staging_bytes = 0;
     size_t workspace_bytes = 0;
     double last_theta64 = 0, last_theta32 = 0, last_scap = 0;
+    // adjoint programme (built at the first sdf_backward) and its buffers
+    int adj_ngroup = 0;
+    Group adj_group[2];
+    int adj_gch[2][2];
+    void *adj_planes = nullptr;      // D+1 dense planes (plan precision)
+    double *adj_part = nullptr;      // reduction partials
     // profiling
     bool prof_on = false;
     int64_t nlaunch = 0;      // kernels launched by the current/last execute
@@ -136,7 +142,8 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool with_sign, void *S, void *dS, vo
                          uint8_t *flags);
 cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags);
 cudaError_t build_spectra(sdf_plan_impl *p);
-cudaError_t launch_adjoint(sdf_plan_impl *p, int64_t K, const double *points, double *dL_dY, double *dL_dtau);
+cudaError_t launch_adjoint(sdf_plan_impl *p, int64_t K, const double *points, const void *w, const void *S_saved,
+                           const uint8_t *flags, double *dL_dY, double *dL_dtau);
 
 double hessian_scale(const sdf_plan_impl *p);
 
