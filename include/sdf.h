@@ -232,6 +232,54 @@ sdf_status sdf_profile_enable(sdf_plan plan, int enable);
 int sdf_profile_read(sdf_plan plan, sdf_kernel_time *out, int max);
 
 /*
+ * Batches: many independent problems (uneven grid sizes and point counts)
+ * executed together.  Problems with identical (D, dims, h, tau, precision,
+ * outputs) share one set of kernel spectra.  Problems are spread over
+ * `n_streams` worker streams; the first sdf_batch_execute (and any call whose
+ * K or buffer pointers differ from the previous call's) runs every problem
+ * once, then captures the whole batch -- all problems, all passes, forked
+ * across the worker streams and joined back -- into one CUDA graph; every
+ * later call with the same arguments is one cudaGraphLaunch on `stream`.
+ * This is the paper's method applied per problem (Table 1, Secs. 4-5); the
+ * batching itself has no counterpart in the paper.
+ */
+typedef struct sdf_batch_s *sdf_batch;
+
+/*
+ * sdf_batch_create -- n problems of dimension D.
+ *   dims       host, n x D node counts (x first per problem).
+ *   h, tau     host, n values each.
+ *   precision, outputs   as sdf_plan_create, common to all problems.
+ *   n_streams  worker streams (1..32) the problems are spread over.
+ *   stream     cudaStream_t (as void*) the graph is launched on.
+ * Synchronous; allocates device memory.
+ */
+sdf_status sdf_batch_create(sdf_batch *out, int n, int D, const int64_t *dims,
+                            const double *h, const double *tau, int precision,
+                            unsigned outputs, int n_streams, void *stream);
+
+/*
+ * sdf_batch_execute -- every problem of the batch, as sdf_execute per problem.
+ * All arrays are host arrays of n entries; each pointer entry is a device
+ * buffer as in sdf_execute (NULL where sdf_execute allows NULL; the whole
+ * array may be NULL to mean all NULL).  Asynchronous on `stream`.
+ */
+sdf_status sdf_batch_execute(sdf_batch batch, const int64_t *K,
+                             const double *const *points,
+                             const double *const *weights, void *const *S,
+                             void *const *dS, void *const *d2S,
+                             int8_t *const *sign, uint8_t *const *flags);
+
+/* Wait for the batch; return the first device-side error of any problem. */
+sdf_status sdf_batch_sync(sdf_batch batch);
+
+/* Plan of problem i (owned by the batch), for sdf_get_stats and the like. */
+sdf_plan sdf_batch_plan(sdf_batch batch, int i);
+
+/* Free the batch, its plans, streams and graph. */
+void sdf_batch_destroy(sdf_batch batch);
+
+/*
  * sdf_execute_noalloc -- the whole path (plan set-up and one execute) for a
  * small problem, with no device allocation at all.  The paper has no
  * counterpart; this entry point exists for callers that cannot call

@@ -30,7 +30,8 @@ STATUS = {0: "SDF_OK", 1: "SDF_ERR_INVALID_ARG", 2: "SDF_ERR_UNSUPPORTED",
 EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
             "sdf_plan_get_info", "sdf_get_stats", "sdf_plan_destroy", "sdf_status_string",
             "sdf_last_error", "sdf_profile_enable", "sdf_profile_read",
-            "sdf_plan_set_noise_constants", "sdf_execute_noalloc"]
+            "sdf_plan_set_noise_constants", "sdf_execute_noalloc", "sdf_batch_create",
+            "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy"]
 
 
 class SDFError(RuntimeError):
@@ -99,6 +100,18 @@ def load_library(path: str | None = None):
         L.sdf_execute_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(i64), d, d, ctypes.c_int, u, i64,
                                           vp, vp, vp, vp, vp, vp, vp, vp]
         L.sdf_execute_noalloc.restype = ctypes.c_int
+        pp = ctypes.POINTER(vp)
+        L.sdf_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(i64),
+                                       ctypes.POINTER(d), ctypes.POINTER(d), ctypes.c_int, u, ctypes.c_int, vp]
+        L.sdf_batch_create.restype = ctypes.c_int
+        L.sdf_batch_execute.argtypes = [vp, ctypes.POINTER(i64), pp, pp, pp, pp, pp, pp, pp]
+        L.sdf_batch_execute.restype = ctypes.c_int
+        L.sdf_batch_sync.argtypes = [vp]
+        L.sdf_batch_sync.restype = ctypes.c_int
+        L.sdf_batch_plan.argtypes = [vp, ctypes.c_int]
+        L.sdf_batch_plan.restype = vp
+        L.sdf_batch_destroy.argtypes = [vp]
+        L.sdf_batch_destroy.restype = None
         L.sdf_plan_set_noise_constants.argtypes = [vp, d, d]
         L.sdf_plan_set_noise_constants.restype = ctypes.c_int
         L.sdf_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -183,6 +196,45 @@ def sdf_execute_noalloc(D, dims, h, tau, precision, outputs, K, points, weights,
                                    int(K), _ptr(points), _ptr(weights), _ptr(S), _ptr(dS), _ptr(d2S),
                                    _ptr(sign), _ptr(flags), ctypes.c_void_p(stream or 0)),
         "sdf_execute_noalloc")
+
+
+def _ptr_array(ts):
+    if ts is None:
+        return None
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+def sdf_batch_create(D, dims_list, h_list, tau_list, precision, outputs, n_streams, stream):
+    n = len(dims_list)
+    dims = (ctypes.c_int64 * (n * D))(*[int(x) for dd in dims_list for x in dd])
+    hs = (ctypes.c_double * n)(*[float(x) for x in h_list])
+    ts = (ctypes.c_double * n)(*[float(x) for x in tau_list])
+    handle = ctypes.c_void_p()
+    _ck(_lib().sdf_batch_create(ctypes.byref(handle), n, int(D), dims, hs, ts, int(precision), int(outputs),
+                                int(n_streams), ctypes.c_void_p(stream or 0)), "sdf_batch_create")
+    return handle
+
+
+def sdf_batch_execute(handle, K, points, weights, S, dS, d2S, sign, flags):
+    Ks = (ctypes.c_int64 * len(K))(*[int(k) for k in K])
+    _ck(_lib().sdf_batch_execute(handle, Ks, _ptr_array(points), _ptr_array(weights), _ptr_array(S),
+                                 _ptr_array(dS), _ptr_array(d2S), _ptr_array(sign), _ptr_array(flags)),
+        "sdf_batch_execute")
+
+
+def sdf_batch_sync(handle):
+    return int(_lib().sdf_batch_sync(handle))
+
+
+def sdf_batch_plan(handle, i):
+    return ctypes.c_void_p(_lib().sdf_batch_plan(handle, int(i)))
+
+
+def sdf_batch_destroy(handle):
+    _lib().sdf_batch_destroy(handle)
 
 
 def sdf_profile_enable(handle, enable):
@@ -313,3 +365,57 @@ class Plan:
                      None if flags is None else flags.contiguous(), dY, dtau)
         self.sync()
         return dY, dtau
+
+
+class Batch:
+    """Independent problems of one dimension D executed as one graph launch."""
+
+    def __init__(self, D, dims_list, h_list, tau_list, precision="fp32", outputs=("S", "sign"),
+                 n_streams=8, stream=None):
+        import torch
+        self.torch = torch
+        self.D = int(D)
+        self.dims = [tuple(int(x) for x in d) for d in dims_list]
+        self.precision = SDF_FP64 if precision in ("fp64", SDF_FP64) else SDF_FP32
+        mask = 0
+        for o in outputs:
+            mask |= _OUTS[o]
+        self.outputs = mask | SDF_OUT_S
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = sdf_batch_create(self.D, self.dims, h_list, tau_list, self.precision, self.outputs,
+                                       n_streams, self.stream.cuda_stream)
+        self.dtype = torch.float64 if self.precision == SDF_FP64 else torch.float32
+
+    def alloc_outputs(self, signed=True, flags=True):
+        t = self.torch
+        outs = []
+        for d in self.dims:
+            shp = tuple(reversed(d))
+            o = {"S": t.empty(shp, dtype=self.dtype, device="cuda")}
+            if self.outputs & SDF_OUT_SIGN and signed:
+                o["sign"] = t.empty(shp, dtype=t.int8, device="cuda")
+            if flags:
+                o["flags"] = t.empty(shp, dtype=t.uint8, device="cuda")
+            outs.append(o)
+        return outs
+
+    def execute(self, points, weights, outs):
+        """points/weights: lists of device float64 tensors; outs from alloc_outputs."""
+        K = [int(p.shape[0]) for p in points]
+        col = lambda k: [o.get(k) for o in outs] if any(k in o for o in outs) else None
+        sdf_batch_execute(self.handle, K, points, weights, col("S"), col("dS"), col("d2S"), col("sign"),
+                          col("flags"))
+
+    def sync(self):
+        _ck(sdf_batch_sync(self.handle), "sdf_batch_sync")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            sdf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

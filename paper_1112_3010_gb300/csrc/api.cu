@@ -309,7 +309,8 @@ static cudaError_t alloc(void **ptr, size_t bytes, size_t *acc) {
 static void free_plan(sdf_plan_impl *p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
-    for (auto &k : p->kernels) cudaFree(k.c);
+    if (!p->shares_spectra)
+        for (auto &k : p->kernels) cudaFree(k.c);
     for (int a = 0; a < 3; ++a) cudaFree(p->tw[a]);
     cudaFree(p->bufA);
     cudaFree(p->bufB);
@@ -373,6 +374,15 @@ const char *sdf_last_error(void) { return g_last_error; }
 
 sdf_status sdf_plan_create(sdf_plan *out, int D, const int64_t *dims, double h, double tau, int precision,
                            unsigned outputs, void *stream) {
+    return sdf::plan_create_shared(out, D, dims, h, tau, precision, outputs, stream, nullptr);
+}
+
+}  // extern "C"
+
+// A plan; with share_from, the kernel spectra of that plan (same D, dims, h,
+// tau, precision and outputs) are used instead of building new ones.
+sdf_status sdf::plan_create_shared(sdf_plan *out, int D, const int64_t *dims, double h, double tau, int precision,
+                                   unsigned outputs, void *stream, const sdf_plan_impl *share_from) {
     if (!out) return SDF_ERR_INVALID_ARG;
     *out = nullptr;
     if (D != 2 && D != 3) return SDF_ERR_UNSUPPORTED;
@@ -404,7 +414,13 @@ sdf_status sdf_plan_create(sdf_plan *out, int D, const int64_t *dims, double h, 
         if (precision == SDF_FP64) PCK(upload_twiddles<double>(&p->tw[a], p->M[a], &p->workspace_bytes));
         else PCK(upload_twiddles<float>(&p->tw[a], p->M[a], &p->workspace_bytes));
     }
-    PCK(build_kernel_list(p, ids));
+    if (share_from) {
+        p->kernels = share_from->kernels;
+        for (int i = 0; i < KER_COUNT; ++i) p->kslot[i] = share_from->kslot[i];
+        p->shares_spectra = true;
+    } else {
+        PCK(build_kernel_list(p, ids));
+    }
     plan_programme(p);
     // workspace
     {
@@ -432,6 +448,8 @@ sdf_status sdf_plan_create(sdf_plan *out, int D, const int64_t *dims, double h, 
     *out = p;
     return SDF_OK;
 }
+
+extern "C" {
 
 static cudaError_t ensure_points(sdf_plan_impl *p, int64_t K) {
     if (K <= p->Kcap) return cudaSuccess;

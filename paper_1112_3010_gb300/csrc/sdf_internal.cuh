@@ -120,6 +120,8 @@ struct sdf_plan_impl {
     int adj_gch[2][2];
     void *adj_planes = nullptr;      // D+1 dense planes (plan precision)
     double *adj_part = nullptr;      // reduction partials
+    // kernel spectra owned by another plan of the same shape (batches)
+    bool shares_spectra = false;
     // profiling
     bool prof_on = false;
     int64_t nlaunch = 0;      // kernels launched by the current/last execute
@@ -146,6 +148,9 @@ cudaError_t launch_adjoint(sdf_plan_impl *p, int64_t K, const double *points, co
                            const uint8_t *flags, double *dL_dY, double *dL_dtau);
 
 double hessian_scale(const sdf_plan_impl *p);
+
+sdf_status plan_create_shared(sdf_plan *out, int D, const int64_t *dims, double h, double tau, int precision,
+                              unsigned outputs, void *stream, const sdf_plan_impl *share_from);
 
 // plan set-up steps shared by sdf_plan_create and sdf_execute_noalloc
 void plan_geometry(sdf_plan_impl *p, int D, const int64_t *dims, double h, double tau, int precision,
