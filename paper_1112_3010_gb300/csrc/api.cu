@@ -28,6 +28,7 @@ static sdf_status cuda_fail(cudaError_t e) {
         return SDF_ERR_OOM;
     }
     snprintf(g_last_error, sizeof g_last_error, "%s", cudaGetErrorString(e));
+    cudaGetLastError();  // a later call must not pick this error up again
     return SDF_ERR_CUDA;
 }
 

@@ -21,8 +21,9 @@ struct sdf_batch_s {
     std::vector<sdf_plan> plans;
     std::vector<cudaStream_t> workers;
     std::vector<cudaEvent_t> join;
-    cudaEvent_t fork = nullptr;
-    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    cudaStream_t stream = nullptr;   // the caller's stream (may be the legacy stream)
+    cudaStream_t origin = nullptr;   // internal stream the graph is captured on
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     // arguments the graph was captured with
@@ -46,10 +47,13 @@ static void batch_free(sdf_batch_s *b) {
     for (auto s : b->workers) cudaStreamDestroy(s);
     for (auto e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->origin) cudaStreamDestroy(b->origin);
 }
 
 static sdf_status fail(cudaError_t e) {
     set_last_error(cudaGetErrorString(e));
+    cudaGetLastError();  // do not leave the error for the next call to find
     return e == cudaErrorMemoryAllocation ? SDF_ERR_OOM : SDF_ERR_CUDA;
 }
 
@@ -83,7 +87,9 @@ sdf_status sdf_batch_create(sdf_batch *out, int n, int D, const int64_t *dims, c
         }
         b->join.push_back(ev);
     }
-    if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) {
+    if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking)) != cudaSuccess) {
         batch_free(b);
         delete b;
         return fail(e);
@@ -154,8 +160,8 @@ sdf_status sdf_batch_execute(sdf_batch b, const int64_t *K, const double *const 
         if (s != SDF_OK) return s;
         for (auto st : b->workers)
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
-        if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
-        if ((e = cudaEventRecord(b->fork, b->stream)) == cudaSuccess) {
+        if ((e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
+        if ((e = cudaEventRecord(b->fork, b->origin)) == cudaSuccess) {
             for (auto st : b->workers)
                 if ((e = cudaStreamWaitEvent(st, b->fork, 0)) != cudaSuccess) break;
         }
@@ -163,11 +169,11 @@ sdf_status sdf_batch_execute(sdf_batch b, const int64_t *K, const double *const 
         if (e == cudaSuccess && s == SDF_OK) {
             for (size_t w = 0; w < b->workers.size(); ++w) {
                 if ((e = cudaEventRecord(b->join[w], b->workers[w])) != cudaSuccess) break;
-                if ((e = cudaStreamWaitEvent(b->stream, b->join[w], 0)) != cudaSuccess) break;
+                if ((e = cudaStreamWaitEvent(b->origin, b->join[w], 0)) != cudaSuccess) break;
             }
         }
         cudaGraph_t g = nullptr;
-        cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+        cudaError_t ee = cudaStreamEndCapture(b->origin, &g);
         if (e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             return fail(e);
