@@ -241,8 +241,11 @@ def main():
     pts_per_step = sum(s.n_nodes for s in shapes)
     value = world * pts_per_step * args.steps / (total_ms * 1e-3)
     prof = {}
+    per_plan = []
     for p in plans:
-        for name, (n, t) in p.profile_read().items():
+        pp = p.profile_read()
+        per_plan.append(pp)
+        for name, (n, t) in pp.items():
             a = prof.setdefault(name, [0, 0.0])
             a[0] += n
             a[1] += t
@@ -358,8 +361,12 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "kernels": per_kernel, "fp64_path": fp64,
             "fixup": [{"tau": s.tau, "tiles": st.n_fixup_tiles, "nodes": st.n_fixup_nodes,
-                       "capped_in_fixup": st.n_capped, "theta32": st.theta32, "theta64": st.theta64}
-                      for s, st in zip(shapes, stats)]}
+                       "capped_in_fixup": st.n_capped, "terms": st.n_fixup_terms, "theta32": st.theta32,
+                       "theta64": st.theta64,
+                       "ms": pp.get("fixup", (1, 0.0))[1] / max(1, pp.get("fixup", (1, 0.0))[0]),
+                       "terms_per_s": st.n_fixup_terms / max(1e-12, 1e-3 * pp.get("fixup", (1, 0.0))[1]
+                                                             / max(1, pp.get("fixup", (1, 0.0))[0]))}
+                      for s, st, pp in zip(shapes, stats, per_plan)]}
     if rank == 0:
         print(json.dumps(line))
     for p in plans:

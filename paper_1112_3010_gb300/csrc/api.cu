@@ -64,6 +64,13 @@ double hessian_scale(const sdf_plan_impl *p) { return p->tau * p->h / (p->tau + 
 
 void set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
 
+// theta_p = theta_coef(p, precision) * ||g||_2 (see include/sdf.h, trust region)
+double theta_coef(const sdf_plan_impl *p, int prec) {
+    const double n = (double)p->M[0] * (double)p->M[1] * (p->D == 3 ? (double)p->M[2] : 1.0);
+    const double base = sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
+    return prec == SDF_FP64 ? p->noise_c64 * ldexp(1.0, -53) * base : p->noise_c32 * ldexp(1.0, -24) * base;
+}
+
 void prof_begin(sdf_plan_impl *p, const char *name, cudaStream_t st) {
     ++p->nlaunch;
     if (!p->prof_on) return;

@@ -57,30 +57,6 @@ __global__ void k_snap(int D, int64_t K, const double *__restrict__ P, const dou
     }
 }
 
-// Exclusive scan of n counts into start[0..n] by one CTA of 1024 threads.
-__global__ void __launch_bounds__(1024) k_scan(const int *__restrict__ count, int *start, int64_t n) {
-    __shared__ long long part[1024];
-    const int tid = threadIdx.x;
-    const int64_t chunk = (n + 1023) / 1024;
-    const int64_t lo = tid * chunk, hi = min(n, lo + chunk);
-    long long s = 0;
-    for (int64_t i = lo; i < hi; ++i) s += count[i];
-    part[tid] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        long long v = (tid >= off) ? part[tid - off] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
-    }
-    long long run = part[tid] - s;
-    for (int64_t i = lo; i < hi; ++i) {
-        start[i] = (int)run;
-        run += count[i];
-    }
-    if (tid == 1023) start[n] = (int)part[1023];
-}
-
 __global__ void k_fill(int64_t K, const int *__restrict__ pt_bin, const int *__restrict__ pt_lc,
                        const int *__restrict__ bin_start, int *bin_fill, long long *entry) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,22 +161,31 @@ __global__ void k_dedupe(int D, int64_t K, const double *__restrict__ W, const i
     }
 }
 
-// Chebyshev distance (in bins, capped at 255) to the nearest occupied bin:
-// separable, one axis at a time.
-__global__ void k_cheb_x(const int *__restrict__ nuniq, unsigned char *out, int nb0, int64_t nrows) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const int64_t base = r * nb0;
-    int d = 255;
-    for (int x = 0; x < nb0; ++x) {
-        d = nuniq[base + x] > 0 ? 0 : min(255, d + 1);
-        out[base + x] = (unsigned char)d;
+// Chebyshev distance (in bins) to the nearest occupied bin, separable, one
+// axis at a time.  Only distances below `cap` matter to the fix-up (a tile at
+// cap or beyond is provably below theta_64), so each search stops there and
+// larger distances are stored as cap.
+__device__ __forceinline__ int cheb_cap(const DevScalars *dsc, double coef64, double logK, double tau_over_h) {
+    const double lt = log(coef64 * sqrt((double)dsc->sum_c2));
+    const double c = floor(((logK - lt) * tau_over_h - 1.0) / 8.0) + 2.0;
+    return (int)fmin(255.0, fmax(1.0, c));
+}
+
+__global__ void k_cheb_x(const int *__restrict__ nuniq, unsigned char *out, int nb0, int64_t nbins,
+                         const DevScalars *dsc, double coef64, double logK, double tau_over_h) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int cap = cheb_cap(dsc, coef64, logK, tau_over_h);
+    const int x = (int)(b % nb0);
+    const int64_t row = b - x;
+    int best = cap;
+    for (int d = 0; d < best; ++d) {
+        if ((x - d >= 0 && nuniq[row + x - d] > 0) || (x + d < nb0 && nuniq[row + x + d] > 0)) {
+            best = d;
+            break;
+        }
     }
-    d = 255;
-    for (int x = nb0 - 1; x >= 0; --x) {
-        d = nuniq[base + x] > 0 ? 0 : min(255, d + 1);
-        if (d < out[base + x]) out[base + x] = (unsigned char)d;
-    }
+    out[b] = (unsigned char)best;
 }
 
 // pass along an axis with stride `st` and length `n`: d(b) = min_j max(|i-j|, in(b_j))
@@ -217,18 +202,92 @@ __global__ void k_cheb_axis(const unsigned char *__restrict__ in, unsigned char 
     out[b] = (unsigned char)best;
 }
 
+// One warp per occupied bin (grid-stride over bins).
 __global__ void k_source_flags(int64_t nb_total, const int *__restrict__ bin_start, const int *__restrict__ nuniq,
                                const int *__restrict__ ucell, int N0, int N1, int nb0, int nb1, uint8_t *flags) {
-    const int64_t b = blockIdx.x;
-    if (b >= nb_total) return;
-    const int n = nuniq[b], s = bin_start[b];
-    const int bx = (int)(b % nb0), by = (int)((b / nb0) % nb1), bz = (int)(b / ((int64_t)nb0 * nb1));
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int lc = ucell[s + i];
-        const int x = bx * 8 + (lc & 7), y = by * 8 + ((lc >> 3) & 7), z = bz * 8 + (lc >> 6);
-        const int64_t node = x + (int64_t)N0 * (y + (int64_t)N1 * z);
-        flags[node] |= SDF_FLAG_SOURCE;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = warp; b < nb_total; b += nwarp) {
+        const int n = nuniq[b];
+        if (n == 0) continue;
+        const int s = bin_start[b];
+        const int bx = (int)(b % nb0), by = (int)((b / nb0) % nb1), bz = (int)(b / ((int64_t)nb0 * nb1));
+        for (int i = lane; i < n; i += 32) {
+            const int lc = ucell[s + i];
+            const int x = bx * 8 + (lc & 7), y = by * 8 + ((lc >> 3) & 7), z = bz * 8 + (lc >> 6);
+            const int64_t node = x + (int64_t)N0 * (y + (int64_t)N1 * z);
+            flags[node] |= SDF_FLAG_SOURCE;
+        }
     }
+}
+
+// Exclusive scan of n counts in three phases: per 4096-element tile (local
+// scan + tile total), tile totals (one block), tile offsets added.
+constexpr int kScanTile = 4096;
+
+__device__ __forceinline__ int block_excl_scan_1024(int v, int *wsum, int *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = wsum[lane];
+        int i2 = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, i2, o);
+            if (lane >= o) i2 += u;
+        }
+        wsum[lane] = i2 - w;
+        if (lane == 31) *total = i2;
+    }
+    __syncthreads();
+    return wsum[wid] + incl - v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int *__restrict__ count, int *start, int *tile_sum,
+                                                     int64_t n) {
+    __shared__ int wsum[32];
+    __shared__ int total;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * threadIdx.x;
+    int v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = (base + j < n) ? count[base + j] : 0;
+    const int off = block_excl_scan_1024(v[0] + v[1] + v[2] + v[3], wsum, &total);
+    int run = off;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (base + j < n) start[base + j] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(int *tile_sum, int ntiles, int *start, int64_t n) {
+    __shared__ int wsum[32];
+    __shared__ int total;
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < ntiles; t0 += 1024) {
+        const int i = t0 + threadIdx.x;
+        const int v = i < ntiles ? tile_sum[i] : 0;
+        const int off = block_excl_scan_1024(v, wsum, &total);
+        if (i < ntiles) tile_sum[i] = carry + off;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) start[n] = carry;
+}
+
+__global__ void k_scan_add(int *start, const int *__restrict__ tile_sum, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && i >= kScanTile) start[i] += tile_sum[i / kScanTile];
 }
 
 cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, const double *weights) {
@@ -246,8 +305,13 @@ cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, con
     k_snap<<<gk, tb, 0, st>>>(p->D, K, points, weights, p->h, (int)p->N[0], (int)p->N[1], (int)p->N[2],
                               (int)p->nb[0], (int)p->nb[1], p->pt_key, p->pt_lc, p->bin_count, p->dsc);
     prof_end(p, st);
+    // tile totals go to bin_nuniq, which k_dedupe overwrites for every bin
+    const int64_t ntiles = (p->nbins + kScanTile - 1) / kScanTile;
     prof_begin(p, "scan", st);
-    k_scan<<<1, 1024, 0, st>>>(p->bin_count, p->bin_start, p->nbins);
+    k_scan_tiles<<<(unsigned)ntiles, 1024, 0, st>>>(p->bin_count, p->bin_start, p->bin_nuniq, p->nbins);
+    k_scan_sums<<<1, 1024, 0, st>>>(p->bin_nuniq, (int)ntiles, p->bin_start, p->nbins);
+    if (ntiles > 1)
+        k_scan_add<<<(unsigned)((p->nbins + 255) / 256), 256, 0, st>>>(p->bin_start, p->bin_nuniq, p->nbins);
     prof_end(p, st);
     prof_begin(p, "fill", st);
     k_fill<<<gk, tb, 0, st>>>(K, p->pt_key, p->pt_lc, p->bin_start, p->bin_fill, p->pt_entry);
@@ -266,11 +330,11 @@ cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, con
 cudaError_t launch_cheb(sdf_plan_impl *p) {
     cudaStream_t st = p->stream;
     const int64_t nb0 = p->nb[0], nb1 = p->nb[1], nb2 = p->nb[2];
-    const int64_t nrows = nb1 * nb2;
     unsigned char *tmp = p->cheb + p->nbins;  // second half of the allocation
-    prof_begin(p, "cheb", st);
-    k_cheb_x<<<(unsigned)((nrows + 127) / 128), 128, 0, st>>>(p->bin_nuniq, tmp, (int)nb0, nrows);
     const unsigned g = (unsigned)((p->nbins + 255) / 256);
+    prof_begin(p, "cheb", st);
+    k_cheb_x<<<g, 256, 0, st>>>(p->bin_nuniq, tmp, (int)nb0, p->nbins, p->dsc, theta_coef(p, SDF_FP64),
+                                log((double)p->last_K), p->tau / p->h);
     if (p->D == 2) {
         k_cheb_axis<<<g, 256, 0, st>>>(tmp, p->cheb, p->nbins, nb0, (int)nb1);
     } else {
@@ -285,9 +349,8 @@ cudaError_t launch_cheb(sdf_plan_impl *p) {
 
 cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags) {
     prof_begin(p, "source_flags", p->stream);
-    k_source_flags<<<(unsigned)p->nbins, 64, 0, p->stream>>>(p->nbins, p->bin_start, p->bin_nuniq, p->ucell,
-                                                             (int)p->N[0], (int)p->N[1], (int)p->nb[0],
-                                                             (int)p->nb[1], flags);
+    k_source_flags<<<152 * 8, 256, 0, p->stream>>>(p->nbins, p->bin_start, p->bin_nuniq, p->ucell, (int)p->N[0],
+                                                  (int)p->N[1], (int)p->nb[0], (int)p->nb[1], flags);
     prof_end(p, p->stream);
     return cudaGetLastError();
 }

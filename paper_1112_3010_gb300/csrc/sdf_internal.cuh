@@ -160,6 +160,7 @@ void plan_programme(sdf_plan_impl *p);
 void plan_buffer_sizes(sdf_plan_impl *p);
 int kernel_parity(int id, int D);
 void set_last_error(const char *msg);  // text returned by sdf_last_error()
+double theta_coef(const sdf_plan_impl *p, int prec);
 constexpr int kSpectraParts = 1024;
 cudaError_t build_spectra_into(sdf_plan_impl *p, double2 *bufX, double2 *bufY, double *part, double *host_part,
                                double2 *const *tw64);
