@@ -41,7 +41,8 @@ struct FixParams {
     int fp64_out;
 };
 
-constexpr int kFixCap = 2048;  // cells staged in shared memory at once
+constexpr int kFixCap = 1024;  // cells staged in shared memory at once
+constexpr int kTB2 = 2;       // 2D tile: kTB2 x kTB2 bins (16 x 16 nodes)
 
 // Bin offset of ring element i (ring k > 0) in 2D: walk the square's border.
 __device__ __forceinline__ void ring2(int k, int i, int &dx, int &dy) {
@@ -79,25 +80,51 @@ __device__ __forceinline__ void ring3(int k, int i, int &dx, int &dy, int &dz) {
     dy = i / w - k;
 }
 
+// Border of a square of side s (s >= 2): element i of 4(s-1), as offsets
+// from its corner.
+__device__ __forceinline__ void square_border(int s, int i, int &dx, int &dy) {
+    const int side = i / (s - 1), o = i % (s - 1);
+    switch (side) {
+        case 0: dx = o; dy = 0; break;
+        case 1: dx = s - 1; dy = o; break;
+        case 2: dx = s - 1 - o; dy = s - 1; break;
+        default: dx = 0; dy = s - 1 - o; break;
+    }
+}
+
 template <int D, typename TO>
-__global__ void __launch_bounds__(D == 2 ? 64 : 512) k_fixup(FixParams P) {
-    constexpr int NT = (D == 2) ? 64 : 512;
+__global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
+    constexpr int TB = (D == 2) ? kTB2 : 1;  // tile edge in bins
+    constexpr int NT = (D == 2) ? 64 * kTB2 * kTB2 : 512;
     constexpr int NH = D * (D + 1) / 2;
     __shared__ int4 cell[kFixCap];  // (x, y, z, count) of staged occupied nodes
     __shared__ int soff[1];
     __shared__ int wtot[32];
-    const int64_t b = blockIdx.x;
-    if (!P.tile_flag[b]) return;
     const int tid = threadIdx.x;
-    const int bx = (int)(b % P.nb0), by = (int)((b / P.nb0) % P.nb1), bz = (int)(b / ((int64_t)P.nb0 * P.nb1));
+    const int nt0 = (P.nb0 + TB - 1) / TB, nt1 = (P.nb1 + TB - 1) / TB;
+    const int64_t tile = blockIdx.x;
+    const int bx = (int)(tile % nt0) * TB, by = (int)((tile / nt0) % nt1) * TB,
+              bz = (int)(tile / ((int64_t)nt0 * nt1)) * TB;
+    // the tile's bins: any flagged?  nearest occupied bin over all of them
+    int c = 255;
+    bool flagged = false;
+    for (int j = 0; j < TB * TB; ++j) {
+        const int qx = bx + (j % TB), qy = by + (j / TB);
+        if (qx >= P.nb0 || qy >= P.nb1) continue;
+        const int64_t q = qx + (int64_t)P.nb0 * (qy + (int64_t)P.nb1 * bz);
+        flagged |= P.tile_flag[q] != 0;
+        c = min(c, (int)P.cheb[q]);
+    }
+    if (!flagged) return;
     const double theta64 = P.coef64 * sqrt((double)P.dsc->sum_c2);
     const double lt = log(theta64);
-    const int c = P.cheb[b];
     const double dlo = (c >= 1) ? (8.0 * (c - 1) + 1.0) * P.h : 0.0;
     // every node of the tile: phi <= K exp(-dlo/tau) < theta64 -> stays capped
     if (c >= 255 || P.logK - dlo / P.tau < lt) return;
 
-    const int x = bx * 8 + (tid & 7), y = by * 8 + ((tid >> 3) & 7), z = bz * 8 + (tid >> 6);
+    const int x = (D == 2) ? bx * 8 + (tid % (8 * TB)) : bx * 8 + (tid & 7);
+    const int y = (D == 2) ? by * 8 + (tid / (8 * TB)) : by * 8 + ((tid >> 3) & 7);
+    const int z = (D == 2) ? 0 : bz * 8 + (tid >> 6);
     const bool inb = x < P.N0 && y < P.N1 && (D == 2 || z < P.N2);
     const int64_t node = (int64_t)x + (int64_t)P.N0 * (y + (int64_t)P.N1 * z);
     const bool mine = inb && (P.flags[node] & SDF_FLAG_CAPPED) != 0;
@@ -118,17 +145,22 @@ __global__ void __launch_bounds__(D == 2 ? 64 : 512) k_fixup(FixParams P) {
     const int kmax = max(max(P.nb0, P.nb1), (D == 3) ? P.nb2 : 0);
     for (int k = 0; k <= kmax; ++k) {
         if (!__syncthreads_or(active)) break;
-        const int nring = (k == 0) ? 1 : ((D == 2) ? 8 * k : (2 * k + 1) * (2 * k + 1) * (2 * k + 1) -
-                                                                (2 * k - 1) * (2 * k - 1) * (2 * k - 1));
+        // ring k: bins at Chebyshev distance k from the tile's block of bins
+        const int nring = (D == 2) ? 4 * (TB + 2 * k - 1)
+                                   : ((k == 0) ? 1 : (2 * k + 1) * (2 * k + 1) * (2 * k + 1) -
+                                                         (2 * k - 1) * (2 * k - 1) * (2 * k - 1));
         for (int i0 = 0; i0 < nring;) {
             // one candidate bin per thread
             const int i = i0 + tid;
             int nb = 0, gb = -1;
             if (i < nring) {
                 int dx = 0, dy = 0, dz = 0;
-                if (k > 0) {
-                    if (D == 2) ring2(k, i, dx, dy);
-                    else ring3(k, i, dx, dy, dz);
+                if (D == 2) {
+                    square_border(TB + 2 * k, i, dx, dy);
+                    dx -= k;
+                    dy -= k;
+                } else if (k > 0) {
+                    ring3(k, i, dx, dy, dz);
                 }
                 const int qx = bx + dx, qy = by + dy, qz = bz + dz;
                 if (qx >= 0 && qx < P.nb0 && qy >= 0 && qy < P.nb1 && (D == 2 || (qz >= 0 && qz < P.nb2))) {
@@ -307,8 +339,12 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS
     F.logK = log((double)p->last_K);
     F.fp64_out = 0;
     prof_begin(p, "fixup", p->stream);
-    if (D == 2) k_fixup<2, float><<<(unsigned)p->nbins, 64, 0, p->stream>>>(F);
-    else k_fixup<3, float><<<(unsigned)p->nbins, 512, 0, p->stream>>>(F);
+    if (D == 2) {
+        const int64_t nt = ((p->nb[0] + kTB2 - 1) / kTB2) * ((p->nb[1] + kTB2 - 1) / kTB2);
+        k_fixup<2, float><<<(unsigned)nt, 64 * kTB2 * kTB2, 0, p->stream>>>(F);
+    } else {
+        k_fixup<3, float><<<(unsigned)p->nbins, 512, 0, p->stream>>>(F);
+    }
     prof_end(p, p->stream);
     return cudaGetLastError();
 }
