@@ -170,6 +170,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -196,6 +197,11 @@ def main():
         pts = [torch.from_numpy(s.points).cuda() for s in shapes]
         wts = [torch.from_numpy(s.weights).cuda() for s in shapes]
         outs = [p.alloc_outputs(["S", "dS", "d2S", "sign", "flags"]) for p in plans]
+    # tile schedule chosen by the library's autotuner (plan-time work, untimed)
+    tuning = []
+    if not args.no_tune:
+        for p, x, w in zip(plans, pts, wts):
+            tuning.append(pkg.sdf_plan_autotune(p.handle, x.shape[0], x, w, 2))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
@@ -357,7 +363,8 @@ def main():
             "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "padded": [info.padded[0], info.padded[1]],
                        "K": K_PTS, "taus": list(TAUS), "outputs": "S,dS,d2S,sign,flags",
                        "precision": "mixed (fp32 FFT + shifted direct-sum fix-up)",
-                       "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "tile_schedule": [{"lines_T": a, "lines_F": b, "fused_variant": c} for a, b, c in tuning]},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "kernels": per_kernel, "fp64_path": fp64,
             "fixup": [{"tau": s.tau, "tiles": st.n_fixup_tiles, "nodes": st.n_fixup_nodes,

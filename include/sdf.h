@@ -216,6 +216,26 @@ sdf_status sdf_get_stats(sdf_plan plan, sdf_exec_stats *stats);
 sdf_status sdf_plan_set_noise_constants(sdf_plan plan, double c_fp32, double c_fp64);
 
 /*
+ * Tile schedule.  lines_T: lines of the transforms each CTA of the transposed
+ * passes (x-pass, 3D y-passes, epilogue) handles; lines_F: lines per CTA of the
+ * fused pass; fused_variant: 0 = up to 128 registers per thread, 1 = at most
+ * 256 threads and three CTAs per SM.  0 (or an invalid value, rounded down to
+ * a valid one) keeps the built-in rule.  Results do not depend on these.
+ */
+sdf_status sdf_plan_set_tuning(sdf_plan plan, int lines_T, int lines_F, int fused_variant);
+
+/*
+ * sdf_plan_autotune -- time candidate tile schedules on the plan's stream with
+ * the given inputs (as sdf_execute; outputs are not written), keep the
+ * fastest, and report it in *lines_T, *lines_F, *fused_variant (host, may be
+ * NULL).  Each candidate runs `reps` executes after one warm-up; the passes
+ * each knob affects are timed with CUDA events.  Synchronous.
+ */
+sdf_status sdf_plan_autotune(sdf_plan plan, int64_t K, const double *points,
+                             const double *weights, int reps, int *lines_T,
+                             int *lines_F, int *fused_variant);
+
+/*
  * sdf_profile_enable -- when enable != 0, every kernel the plan launches is
  * bracketed by a pair of CUDA events recorded on the plan's stream (the
  * stream the kernel runs on), so the durations are device times of that

@@ -31,7 +31,8 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_plan_get_info", "sdf_get_stats", "sdf_plan_destroy", "sdf_status_string",
             "sdf_last_error", "sdf_profile_enable", "sdf_profile_read",
             "sdf_plan_set_noise_constants", "sdf_execute_noalloc", "sdf_batch_create",
-            "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy"]
+            "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy",
+            "sdf_plan_set_tuning", "sdf_plan_autotune"]
 
 
 class SDFError(RuntimeError):
@@ -112,6 +113,11 @@ def load_library(path: str | None = None):
         L.sdf_batch_plan.restype = vp
         L.sdf_batch_destroy.argtypes = [vp]
         L.sdf_batch_destroy.restype = None
+        L.sdf_plan_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.sdf_plan_set_tuning.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.sdf_plan_autotune.argtypes = [vp, i64, vp, vp, ctypes.c_int, ip, ip, ip]
+        L.sdf_plan_autotune.restype = ctypes.c_int
         L.sdf_plan_set_noise_constants.argtypes = [vp, d, d]
         L.sdf_plan_set_noise_constants.restype = ctypes.c_int
         L.sdf_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -196,6 +202,19 @@ def sdf_execute_noalloc(D, dims, h, tau, precision, outputs, K, points, weights,
                                    int(K), _ptr(points), _ptr(weights), _ptr(S), _ptr(dS), _ptr(d2S),
                                    _ptr(sign), _ptr(flags), ctypes.c_void_p(stream or 0)),
         "sdf_execute_noalloc")
+
+
+def sdf_plan_set_tuning(handle, lines_T, lines_F, fused_variant):
+    _ck(_lib().sdf_plan_set_tuning(handle, int(lines_T), int(lines_F), int(fused_variant)),
+        "sdf_plan_set_tuning")
+
+
+def sdf_plan_autotune(handle, K, points, weights, reps):
+    """Returns (lines_T, lines_F, fused_variant) chosen by the library."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _ck(_lib().sdf_plan_autotune(handle, int(K), _ptr(points), _ptr(weights), int(reps), ctypes.byref(a),
+                                 ctypes.byref(b), ctypes.byref(c)), "sdf_plan_autotune")
+    return a.value, b.value, c.value
 
 
 def _ptr_array(ts):

@@ -618,6 +618,79 @@ sdf_status sdf_plan_set_noise_constants(sdf_plan p, double c32, double c64) {
     return SDF_OK;
 }
 
+sdf_status sdf_plan_set_tuning(sdf_plan p, int lines_T, int lines_F, int fused_variant) {
+    if (!p) return SDF_ERR_INVALID_ARG;
+    p->tune_RT = lines_T > 0 ? lines_T : 0;
+    p->tune_RF = lines_F > 0 ? lines_F : 0;
+    p->tune_FV = fused_variant == 1 ? 1 : 0;
+    return SDF_OK;
+}
+
+// Device time of the named kernels over `reps` executes (after one warm-up).
+static sdf_status time_kernels(sdf_plan p, int64_t K, const double *points, const double *weights, int reps,
+                               const char *const *names, int nnames, double *ms) {
+    sdf_status s = sdf_execute(p, K, points, weights, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (s != SDF_OK) return s;
+    const bool was = p->prof_on;
+    p->prof_on = true;
+    sdf_kernel_time kt[32];
+    sdf_profile_read(p, kt, 32);  // drop older records
+    for (int r = 0; r < reps; ++r) {
+        s = sdf_execute(p, K, points, weights, nullptr, nullptr, nullptr, nullptr, nullptr);
+        if (s != SDF_OK) break;
+    }
+    const int n = sdf_profile_read(p, kt, 32);
+    p->prof_on = was;
+    if (s != SDF_OK) return s;
+    if (n < 0) return SDF_ERR_CUDA;
+    *ms = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < nnames; ++j)
+            if (strcmp(kt[i].name, names[j]) == 0) *ms += kt[i].total_ms;
+    return SDF_OK;
+}
+
+sdf_status sdf_plan_autotune(sdf_plan p, int64_t K, const double *points, const double *weights, int reps,
+                             int *lines_T, int *lines_F, int *fused_variant) {
+    if (!p || !points || reps < 1) return SDF_ERR_INVALID_ARG;
+    const char *tnames[] = {"xpass", "fwd_y", "inv_y", "epilogue"};
+    const char *fnames[] = {"fused"};
+    double best = 1e300;
+    int bestT = p->tune_RT, bestF = p->tune_RF, bestV = p->tune_FV;
+    for (int RT : {0, 1, 2, 4, 8, 16}) {
+        p->tune_RT = RT;
+        double ms;
+        sdf_status s = time_kernels(p, K, points, weights, reps, tnames, 4, &ms);
+        if (s != SDF_OK) return s;
+        if (ms < best) {
+            best = ms;
+            bestT = RT;
+        }
+    }
+    p->tune_RT = bestT;
+    best = 1e300;
+    for (int RF : {0, 1, 2, 4}) {
+        for (int FV : {0, 1}) {
+            p->tune_RF = RF;
+            p->tune_FV = FV;
+            double ms;
+            sdf_status s = time_kernels(p, K, points, weights, reps, fnames, 1, &ms);
+            if (s != SDF_OK) return s;
+            if (ms < best) {
+                best = ms;
+                bestF = RF;
+                bestV = FV;
+            }
+        }
+    }
+    p->tune_RF = bestF;
+    p->tune_FV = bestV;
+    if (lines_T) *lines_T = bestT;
+    if (lines_F) *lines_F = bestF;
+    if (fused_variant) *fused_variant = bestV;
+    return SDF_OK;
+}
+
 sdf_status sdf_profile_enable(sdf_plan p, int enable) {
     if (!p) return SDF_ERR_INVALID_ARG;
     p->prof_on = enable != 0;

@@ -27,6 +27,8 @@ template <typename T> using cx = typename cplx_t<T>::type;
 
 // Thread bound per precision: a double line needs twice the registers.
 #define SDF_LB(T) __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
+// Larger block variant: double lines never exceed 512 threads.
+template <typename T> constexpr int big_mt() { return sizeof(T) == 8 ? 512 : 1024; }
 template <typename T> constexpr int max_threads() { return sizeof(T) == 8 ? 512 : 1024; }
 
 struct LineCfg {
@@ -56,8 +58,8 @@ static inline int pick_R(int logL, size_t vbytes, int max_threads, int r_cap, si
 // Builds each line of the point fields from the deduplicated node list
 // (bin-grouped), transforms it along x and writes it transposed.
 // Field 0: (count, 0); field 1: (w_0, w_1); field 2: (w_2, 0).
-template <typename T>
-__global__ void SDF_LB(T) k_xpass_cells(const int *__restrict__ bin_start, const int *__restrict__ bin_nuniq,
+template <typename T, int MT>
+__global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_start, const int *__restrict__ bin_nuniq,
                                                       const int *__restrict__ ucell, const int *__restrict__ ucount,
                                                       const double *__restrict__ uw, int N1, int nb0, int nb1,
                                                       int logL, int R, int nfield, int64_t n_lines, cx<T> *out,
@@ -152,8 +154,8 @@ __global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__rest
 // Contiguous lines of n_in stored values (the rest of the L inputs are zero),
 // forward transform, transposed output.  Used for the 3D y-pass and for the
 // plan-time kernel transforms (n_in = L).
-template <typename T>
-__global__ void SDF_LB(T) k_fwd_T(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int R,
+template <typename T, int MT>
+__global__ void __launch_bounds__(MT) k_fwd_T(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int R,
                                                 int64_t n_lines, int nfield, int64_t in_fs, int64_t out_fs,
                                                 const cx<T> *__restrict__ tw) {
     using V = cx<T>;
@@ -196,6 +198,12 @@ struct FusedParams {
     int nfield;
 };
 
+// Bijection of [0, M) (M even): 2j -> j, 1 -> M/2, 2j+1 -> M-j.
+__device__ __forceinline__ int pair_index(int i, int M) {
+    const int j = i >> 1;
+    return (i & 1) ? (j == 0 ? M / 2 : M - j) : j;
+}
+
 template <typename T, int D>
 __device__ __forceinline__ void line_fold(int64_t line, const FusedParams &P, int64_t &cbase, int &flips) {
     // flips bit a: frequency on axis a is above M_a/2
@@ -215,8 +223,8 @@ __device__ __forceinline__ void line_fold(int64_t line, const FusedParams &P, in
 
 // Forward along the last axis, multiply by the kernel spectra, inverse along the
 // same axis, keep the first n_out outputs.  Field spectra stay in registers.
-template <typename T, int D>
-__global__ void __launch_bounds__(512) k_fused(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int n_out,
+template <typename T, int D, int FV>
+__global__ void __launch_bounds__(FV ? 256 : 512, FV ? 3 : 1) k_fused(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int n_out,
                                                int R, int64_t n_lines, int64_t in_fs, int64_t out_fs, FusedParams P,
                                                const cx<T> *__restrict__ tw) {
     using V = cx<T>;
@@ -224,12 +232,22 @@ __global__ void __launch_bounds__(512) k_fused(const cx<T> *__restrict__ in, cx<
     V *sm = reinterpret_cast<V *>(smraw);
     const int L = 1 << logL, TPL = L >> 4, PL = pad16(L), half = L >> 1;
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
-    const int64_t line = (int64_t)blockIdx.x * R + lr;
-    const bool valid = line < n_lines;
+    // consecutive line ids visit frequency pairs (k, M-k), which read the same
+    // folded spectrum row: the second read hits L2
+    const int64_t lid = (int64_t)blockIdx.x * R + lr;
+    const bool valid = lid < n_lines;
+    int64_t line = 0;
+    if (valid) {
+        if (D == 2) {
+            line = pair_index((int)lid, P.M0);
+        } else {
+            line = (int64_t)pair_index((int)(lid / P.M0), P.M1) * P.M0 + pair_index((int)(lid % P.M0), P.M0);
+        }
+    }
     V *my = sm + lr * PL;
     int64_t cb;
     int flips;
-    line_fold<T, D>(valid ? line : 0, P, cb, flips);
+    line_fold<T, D>(line, P, cb, flips);
     cb *= (half + 1);
     const int waxis = D - 1;
 
@@ -304,8 +322,8 @@ __global__ void __launch_bounds__(512) k_fused(const cx<T> *__restrict__ in, cx<
 // ---------------------------------------------------------------- inverse (3D y)
 // Transposed input (all L elements), inverse transform, contiguous output of
 // the first n_out elements.
-template <typename T>
-__global__ void SDF_LB(T) k_inv_T(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_out, int R,
+template <typename T, int MT>
+__global__ void __launch_bounds__(MT) k_inv_T(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_out, int R,
                                                 int64_t n_lines, int nfield, int64_t in_fs, int64_t out_fs,
                                                 const cx<T> *__restrict__ tw) {
     using V = cx<T>;
@@ -354,8 +372,8 @@ struct EpiParams {
     double hs_inv;  // 1 / scale of the stored Hessian kernels
 };
 
-template <typename T, int D>
-__global__ void SDF_LB(T) k_epilogue(const cx<T> *__restrict__ in, int logL, int R, int64_t n_lines,
+template <typename T, int D, int MT>
+__global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, int logL, int R, int64_t n_lines,
                                                    EpiParams P, const cx<T> *__restrict__ tw) {
     using V = cx<T>;
     extern __shared__ unsigned char smraw[];
@@ -477,17 +495,41 @@ static cudaError_t set_smem(const void *fn, size_t bytes) {
 
 constexpr size_t kSmemBudget = 200 * 1024;
 
+// Lines per CTA of a transposed pass: the plan's tuning when set and valid,
+// else pick_R.
+template <typename T>
+static int tuned_R(const sdf_plan_impl *p, int logL) {
+    const int def = pick_R(logL, sizeof(cx<T>), max_threads<T>(), 16, kSmemBudget);
+    if (!p || p->tune_RT <= 0) return def;
+    const int TPL = (1 << logL) >> 4, PL = pad16(1 << logL);
+    int R = p->tune_RT;
+    while (R > 1 && (R * TPL > max_threads<T>() || (size_t)R * PL * sizeof(cx<T>) > kSmemBudget)) R >>= 1;
+    return R;
+}
+
+// Launch kern<T, MT> with MT = 1024 only when the block needs it (more
+// registers per thread otherwise).  Needs `cudaError_t e` in scope.
+#define SDF_LAUNCH_MT(kern, T, nthr, grid, smem, st, ...)                                               \
+    do {                                                                                              \
+        if ((nthr) > 512) {                                                                           \
+            if ((e = set_smem<T>((const void *)kern<T, big_mt<T>()>, smem)) != cudaSuccess) return e; \
+            kern<T, big_mt<T>()><<<(unsigned)(grid), (nthr), (smem), (st)>>>(__VA_ARGS__);             \
+        } else {                                                                                      \
+            if ((e = set_smem<T>((const void *)kern<T, 512>, smem)) != cudaSuccess) return e;         \
+            kern<T, 512><<<(unsigned)(grid), (nthr), (smem), (st)>>>(__VA_ARGS__);                     \
+        }                                                                                             \
+    } while (0)
+
 template <typename T>
 cudaError_t fwd_T_launch(const cx<T> *in, cx<T> *out, int logL, int n_in, int64_t n_lines, int nfield, int64_t in_fs,
                          int64_t out_fs, const cx<T> *tw, cudaStream_t st, sdf_plan_impl *p) {
-    const int R = pick_R(logL, sizeof(cx<T>), max_threads<T>(), 16, kSmemBudget);
+    const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
     const size_t smem = (size_t)R * c.PL * sizeof(cx<T>);
-    cudaError_t e = set_smem<T>((const void *)k_fwd_T<T>, smem);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     const int64_t grid = (n_lines + R - 1) / R;
     if (p) prof_begin(p, "fwd_y", st);
-    k_fwd_T<T><<<(unsigned)grid, R * c.TPL, smem, st>>>(in, out, logL, n_in, R, n_lines, nfield, in_fs, out_fs, tw);
+    SDF_LAUNCH_MT(k_fwd_T, T, R * c.TPL, grid, smem, st, in, out, logL, n_in, R, n_lines, nfield, in_fs, out_fs, tw);
     if (p) prof_end(p, st);
     return cudaGetLastError();
 }
@@ -537,7 +579,7 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
     // ---- x-pass
     {
         const int logL = p->logM[0];
-        const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
+        const int R = dense_in ? pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget) : tuned_R<T>(p, logL);
         LineCfg c = line_cfg(logL, R);
         const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
         const size_t smem = (size_t)R * c.PL * sizeof(V);
@@ -551,11 +593,10 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
                                                                      (int)N0, logL, R, n_lines, A, tw0);
             prof_end(p, st);
         } else {
-            if ((e = set_smem<T>((const void *)k_xpass_cells<T>, smem)) != cudaSuccess) return e;
             prof_begin(p, "xpass", st);
-            k_xpass_cells<T><<<(unsigned)grid, R * c.TPL, smem, st>>>(
-                p->bin_start, p->bin_nuniq, p->ucell, p->ucount, p->uw, (int)N1, (int)p->nb[0], (int)p->nb[1], logL,
-                R, nfield, n_lines, A, M0 * n_lines, tw0);
+            SDF_LAUNCH_MT(k_xpass_cells, T, R * c.TPL, grid, smem, st, p->bin_start, p->bin_nuniq, p->ucell,
+                          p->ucount, p->uw, (int)N1, (int)p->nb[0], (int)p->nb[1], logL, R, nfield, n_lines, A,
+                          M0 * n_lines, tw0);
             prof_end(p, st);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -585,6 +626,12 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         const int TPL = (1 << logL) >> 4;
         int R = 1;
         while (R * 2 * TPL <= 256) R *= 2;
+        if (p->tune_RF > 0) {
+            R = p->tune_RF;
+            while (R > 1 && R * TPL > 512) R >>= 1;
+        }
+        // the 3-blocks-per-SM register variant needs <= 256 threads
+        const bool fv = p->tune_FV == 1 && R * TPL <= 256;
         LineCfg c = line_cfg(logL, R);
         const size_t smem = (size_t)R * c.PL * sizeof(V);
         FusedParams F = make_fused_params(p, dense_in != nullptr);
@@ -594,15 +641,20 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         const int64_t grid = (fused_lines + R - 1) / R;
         const V *twl = reinterpret_cast<const V *>(p->tw[D - 1]);
         prof_begin(p, "fused", st);
+#define SDF_FUSED(DD, FVV)                                                                                 \
+    do {                                                                                                   \
+        if ((e = set_smem<T>((const void *)k_fused<T, DD, FVV>, smem)) != cudaSuccess) return e;          \
+        k_fused<T, DD, FVV><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, fused_nin, (int)n_out, R, \
+                                                                  fused_lines, in_fs, out_fs, F, twl);     \
+    } while (0)
         if (D == 2) {
-            if ((e = set_smem<T>((const void *)k_fused<T, 2>, smem)) != cudaSuccess) return e;
-            k_fused<T, 2><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, fused_nin, (int)n_out, R,
-                                                                  fused_lines, in_fs, out_fs, F, twl);
+            if (fv) SDF_FUSED(2, 1);
+            else SDF_FUSED(2, 0);
         } else {
-            if ((e = set_smem<T>((const void *)k_fused<T, 3>, smem)) != cudaSuccess) return e;
-            k_fused<T, 3><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, fused_nin, (int)n_out, R,
-                                                                  fused_lines, in_fs, out_fs, F, twl);
+            if (fv) SDF_FUSED(3, 1);
+            else SDF_FUSED(3, 0);
         }
+#undef SDF_FUSED
         prof_end(p, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -627,17 +679,16 @@ static cudaError_t inverse_mid(sdf_plan_impl *p, int ngroup, const cx<T> **last_
     }
     const int64_t N1 = p->N[1], N2 = p->N[2], M0 = p->M[0], M1 = p->M[1];
     const int logL = p->logM[1];
-    const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
+    const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
     const size_t smem = (size_t)R * c.PL * sizeof(V);
-    cudaError_t e = set_smem<T>((const void *)k_inv_T<T>, smem);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     const int64_t n_lines = M0 * N2;  // lines (u, z')
     const int64_t grid = (n_lines + R - 1) / R;
     prof_begin(p, "inv_y", p->stream);
-    k_inv_T<T><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(
-        reinterpret_cast<const V *>(p->bufA), reinterpret_cast<V *>(p->bufB), logL, (int)N1, R, n_lines, ngroup,
-        M1 * n_lines, n_lines * N1, reinterpret_cast<const V *>(p->tw[1]));
+    SDF_LAUNCH_MT(k_inv_T, T, R * c.TPL, grid, smem, p->stream, reinterpret_cast<const V *>(p->bufA),
+                  reinterpret_cast<V *>(p->bufB), logL, (int)N1, R, n_lines, ngroup, M1 * n_lines, n_lines * N1,
+                  reinterpret_cast<const V *>(p->tw[1]));
     prof_end(p, p->stream);
     *last_in = reinterpret_cast<const V *>(p->bufB);
     return cudaGetLastError();
@@ -694,19 +745,26 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
     E.fixup = (p->prec == SDF_FP32) ? 1 : 0;
     E.hs_inv = 1.0 / hessian_scale(p);
     const int logL = p->logM[0];
-    const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
+    const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
     const size_t smem = (size_t)R * c.PL * sizeof(V);
     const int64_t grid = (n_lines + R - 1) / R;
     const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
+    const bool big = R * c.TPL > 512;
+#define SDF_EPI(DD, MTT)                                                                                    \
+    do {                                                                                                    \
+        if ((e = set_smem<T>((const void *)k_epilogue<T, DD, MTT>, smem)) != cudaSuccess) return e;        \
+        k_epilogue<T, DD, MTT><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0); \
+    } while (0)
     prof_begin(p, "epilogue", p->stream);
     if (D == 2) {
-        if ((e = set_smem<T>((const void *)k_epilogue<T, 2>, smem)) != cudaSuccess) return e;
-        k_epilogue<T, 2><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0);
+        if (big) SDF_EPI(2, big_mt<T>());
+        else SDF_EPI(2, 512);
     } else {
-        if ((e = set_smem<T>((const void *)k_epilogue<T, 3>, smem)) != cudaSuccess) return e;
-        k_epilogue<T, 3><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0);
+        if (big) SDF_EPI(3, big_mt<T>());
+        else SDF_EPI(3, 512);
     }
+#undef SDF_EPI
     prof_end(p, p->stream);
     (void)N2;
     return cudaGetLastError();

@@ -122,6 +122,9 @@ struct sdf_plan_impl {
     double *adj_part = nullptr;      // reduction partials
     // kernel spectra owned by another plan of the same shape (batches)
     bool shares_spectra = false;
+    // tile schedule (0: built-in rule): lines per CTA of the transposed passes
+    // and of the fused pass, and the fused pass's register variant
+    int tune_RT = 0, tune_RF = 0, tune_FV = 0;
     // profiling
     bool prof_on = false;
     int64_t nlaunch = 0;      // kernels launched by the current/last execute
