@@ -218,9 +218,12 @@ sdf_status sdf_plan_set_noise_constants(sdf_plan plan, double c_fp32, double c_f
 /*
  * Tile schedule.  lines_T: lines of the transforms each CTA of the transposed
  * passes (x-pass, 3D y-passes, epilogue) handles; lines_F: lines per CTA of the
- * fused pass; fused_variant: 0 = up to 128 registers per thread, 1 = at most
- * 256 threads and three CTAs per SM.  0 (or an invalid value, rounded down to
- * a valid one) keeps the built-in rule.  Results do not depend on these.
+ * fused pass; fused_variant: 1 = at most 256 threads and three CTAs per SM,
+ * 2 = up to 128 registers per thread, 3 = 2D float plans: one CTA per pair of
+ * mirror columns with the spectrum rows staged in shared memory (falls back to
+ * 2 when it does not fit).  0 (or an invalid value, rounded down to a valid
+ * one) keeps the built-in rule (3 where it fits, else 2).  Results do not
+ * depend on these.
  */
 sdf_status sdf_plan_set_tuning(sdf_plan plan, int lines_T, int lines_F, int fused_variant);
 

@@ -622,7 +622,7 @@ sdf_status sdf_plan_set_tuning(sdf_plan p, int lines_T, int lines_F, int fused_v
     if (!p) return SDF_ERR_INVALID_ARG;
     p->tune_RT = lines_T > 0 ? lines_T : 0;
     p->tune_RF = lines_F > 0 ? lines_F : 0;
-    p->tune_FV = fused_variant == 1 ? 1 : 0;
+    p->tune_FV = (fused_variant >= 1 && fused_variant <= 3) ? fused_variant : 0;
     return SDF_OK;
 }
 
@@ -670,7 +670,7 @@ sdf_status sdf_plan_autotune(sdf_plan p, int64_t K, const double *points, const 
     p->tune_RT = bestT;
     best = 1e300;
     for (int RF : {0, 1, 2, 4}) {
-        for (int FV : {0, 1}) {
+        for (int FV : {1, 2, 3}) {
             p->tune_RF = RF;
             p->tune_FV = FV;
             double ms;

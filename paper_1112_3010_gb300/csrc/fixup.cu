@@ -142,25 +142,38 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
     for (int a = 0; a < NH; ++a) sH[a] = 0.f;
     unsigned long long nterm = 0;
 
+    // ring k: bins at Chebyshev distance k from the tile's block of bins
+    auto nring_of = [&](int k) {
+        return (D == 2) ? 4 * (TB + 2 * k - 1)
+                        : ((k == 0) ? 1 : (2 * k + 1) * (2 * k + 1) * (2 * k + 1) - (2 * k - 1) * (2 * k - 1) * (2 * k - 1));
+    };
+    // (m + ccut)^2 in grid units: terms beyond it are skipped before any MUFU work
+    float rc2 = INFINITY;
     const int kmax = max(max(P.nb0, P.nb1), (D == 3) ? P.nb2 : 0);
-    for (int k = 0; k <= kmax; ++k) {
+    // rings are visited in batches {0,1,2}, {3,4}, then one at a time: most
+    // tiles finish in the first batch, one staging round
+    for (int k0 = 0; k0 <= kmax;) {
         if (!__syncthreads_or(active)) break;
-        // ring k: bins at Chebyshev distance k from the tile's block of bins
-        const int nring = (D == 2) ? 4 * (TB + 2 * k - 1)
-                                   : ((k == 0) ? 1 : (2 * k + 1) * (2 * k + 1) * (2 * k + 1) -
-                                                         (2 * k - 1) * (2 * k - 1) * (2 * k - 1));
+        const int k1 = min(kmax, (k0 == 0) ? 2 : (k0 == 3 ? 4 : k0));
+        int nring = 0;
+        for (int k = k0; k <= k1; ++k) nring += nring_of(k);
         for (int i0 = 0; i0 < nring;) {
             // one candidate bin per thread
             const int i = i0 + tid;
             int nb = 0, gb = -1;
             if (i < nring) {
+                int k = k0, ii = i;
+                while (ii >= nring_of(k)) {
+                    ii -= nring_of(k);
+                    ++k;
+                }
                 int dx = 0, dy = 0, dz = 0;
                 if (D == 2) {
-                    square_border(TB + 2 * k, i, dx, dy);
+                    square_border(TB + 2 * k, ii, dx, dy);
                     dx -= k;
                     dy -= k;
                 } else if (k > 0) {
-                    ring3(k, i, dx, dy, dz);
+                    ring3(k, ii, dx, dy, dz);
                 }
                 const int qx = bx + dx, qy = by + dy, qz = bz + dz;
                 if (qx >= 0 && qx < P.nb0 && qy >= 0 && qy < P.nb1 && (D == 2 || (qz >= 0 && qz < P.nb2))) {
@@ -207,6 +220,7 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
                     const int4 q = cell[e];
                     const int ddx = x - q.x, ddy = y - q.y, ddz = (D == 3) ? z - q.z : 0;
                     const int r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    if ((float)r2 > rc2) continue;
                     // r = h sqrt(r2) and 1/sqrt(r2) from one reciprocal square root
                     const float ir = r2 > 0 ? rsqrtf((float)r2) : 0.f;
                     const float r = (float)r2 * ir * h;
@@ -220,6 +234,8 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
 #pragma unroll
                         for (int a = 0; a < NH; ++a) sH[a] *= sc;
                         m = r;
+                        const float rc = (m + ccut) * ih * 1.0001f;
+                        rc2 = rc * rc;
                     }
                     const float E = (float)q.w * exp2f((m - r) * l2e_tau);
                     sE += E;
@@ -242,9 +258,9 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
             __syncthreads();
             i0 += max(taken, 1);
         }
-        // after ring k every unvisited node lies at least lb from this tile
+        // after ring k1 every unvisited node lies at least lb from this tile
         if (active) {
-            const float lb = (8.f * k + 1.f) * h;
+            const float lb = (8.f * k1 + 1.f) * h;
             const float tailA = -lb * itau + lnK;                 // log of K exp(-lb/tau)
             if (m < INFINITY) {
                 const float lsE = logf(sE);
@@ -262,6 +278,7 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
                 early_cap = true;
             }
         }
+        k0 = k1 + 1;
     }
     int fixed = 0, capped = 0;
     if (mine) {

@@ -93,7 +93,7 @@ size_t layout(sdf_plan_impl *p, int64_t K, unsigned char *base, double2 **tw64, 
         c.take(&tw64[a], sizeof(double2) * p->M[a]);
     }
     c.take(part, sizeof(double) * kSpectraParts);
-    const int64_t H = (p->M[0] / 2 + 1) * (p->M[1] / 2 + 1) * (D == 3 ? p->M[2] / 2 + 1 : 1);
+    const int64_t H = spec_rows(p) * spec_row_len(p);
     for (auto &k : p->kernels) c.take(&k.c, esz * H);
     const int64_t nb = p->nbins;
     c.take(&p->bin_count, sizeof(int) * (nb + 1));

@@ -196,6 +196,7 @@ struct FusedParams {
     int D;
     int M0, M1;                   // padded sizes of the line axes (3D: M0 = axis0, M1 = axis1)
     int nfield;
+    int64_t Hp;                   // compressed spectrum row length
 };
 
 // Bijection of [0, M) (M even): 2j -> j, 1 -> M/2, 2j+1 -> M-j.
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 3 : 1) k_fused(const cx<T
     int64_t cb;
     int flips;
     line_fold<T, D>(line, P, cb, flips);
-    cb *= (half + 1);
+    cb *= P.Hp;
     const int waxis = D - 1;
 
     V F0[16], F1[16], F2[16];
@@ -317,6 +318,117 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 3 : 1) k_fused(const cx<T
         // no sign-group term reads field 0, so F0 is dead here
         for (; g < P.ngroup; ++g) run_group(g, F1, F1, F2);
     }
+}
+
+// ---------------------------------------------------------------- fused, paired columns (2D)
+// One CTA, two halves of TPL threads: columns u = j and u = M0 - j, whose
+// folded spectrum rows are the same row j.  All the plan's rows for j are
+// copied to shared memory with 16-byte cp.async while the forward transform
+// of field 0 runs, then every multiply reads shared memory.  j = 0 and
+// j = M0/2 have no partner (the second half idles).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in,
+                                                    int n_out, int64_t in_fs, int64_t out_fs, FusedParams P, int nker,
+                                                    const cx<T> *__restrict__ tw) {
+    using V = cx<T>;
+    extern __shared__ __align__(16) unsigned char smraw_p[];
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L), half = L >> 1;
+    const int64_t Hp = P.Hp;
+    T *crow = reinterpret_cast<T *>(smraw_p);                      // nker rows of Hp
+    V *sm = reinterpret_cast<V *>(smraw_p + sizeof(T) * nker * Hp);  // two exchange lines
+    const int tid = threadIdx.x, hh = tid / TPL, t = tid % TPL;
+    const int j = blockIdx.x;
+    const int M0 = P.M0;
+    const bool valid = (hh == 0) || (j > 0 && j < M0 / 2);
+    const int u = hh == 0 ? j : M0 - j;
+    const int flips = (u > M0 / 2) ? 1 : 0;
+    V *my = sm + hh * PL;
+    // stage the spectrum rows of j
+    {
+        const int per_row = (int)(Hp * sizeof(T) / 16);
+        const int total = nker * per_row;
+        for (int i = tid; i < total; i += blockDim.x) {
+            const int k = i / per_row, o = i % per_row;
+            const T *src = reinterpret_cast<const T *>(P.kc[k]) + (int64_t)j * Hp;
+            cp_async16(reinterpret_cast<unsigned char *>(crow + (int64_t)k * Hp) + 16 * o,
+                       reinterpret_cast<const unsigned char *>(src) + 16 * o);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    V F0[16], F1[16];
+    auto load_fwd = [&](int f, V (&v)[16]) {
+        const V *src = in + f * in_fs + (int64_t)u * n_in;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int e = t + m * TPL;
+            v[m] = (valid && m < 8 && e < n_in) ? src[e] : mk<V>(T(0), T(0));
+        }
+        __syncthreads();
+        fft_line<false>(v, my, t, logL, tw);
+    };
+    auto run_group = [&](int g, const V (&A)[16], const V (&B)[16]) {
+        V v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = mk<V>(T(0), T(0));
+        for (int k = 0; k < P.nterm[g]; ++k) {
+            const int slot = P.tk[g][k];
+            const T *c = crow + (int64_t)slot * Hp;
+            const int par = P.kpar[slot];
+            const T br = T(P.br[g][k]), bi = T(P.bi[g][k]);
+            const bool useB = P.tf[g][k] != 0;
+            const bool lflip = (par & flips & 1) != 0;
+            const bool wodd = (par >> 1) & 1;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                const int w = t + m * TPL;
+                const int fw = w <= half ? w : L - w;
+                T val = c[fw];
+                if (lflip ^ (wodd && w > half)) val = -val;
+                const V s = useB ? B[m] : A[m];
+                const T pr = br * val, pi = bi * val;
+                v[m].x += pr * s.x - pi * s.y;
+                v[m].y += pr * s.y + pi * s.x;
+            }
+        }
+        __syncthreads();
+        fft_line<true>(v, my, t, logL, tw);
+        if (valid) {
+            V *o = out + g * out_fs + (int64_t)u * n_out;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                const int e = t + m * TPL;
+                if (m < 8 && e < n_out) o[e] = v[m];
+            }
+        }
+    };
+    load_fwd(0, F0);
+    cp_async_wait_all();
+    __syncthreads();
+    int g = 0;
+    for (; g < P.ngroup; ++g) {
+        bool only0 = true;
+        for (int k = 0; k < P.nterm[g]; ++k) only0 &= (P.tf[g][k] == 0);
+        if (!only0) break;
+        run_group(g, F0, F0);
+    }
+    if (g < P.ngroup) {
+        load_fwd(1, F1);
+        for (; g < P.ngroup; ++g) run_group(g, F1, F1);
+    }
+}
+
+// Shared memory of k_fused2p (0 when the 2D float plan does not fit).
+static size_t fused2p_smem(const sdf_plan_impl *p) {
+    if (p->D != 2 || p->prec != SDF_FP32 || p->nfield > 2) return 0;
+    const size_t b = sizeof(float) * p->kernels.size() * spec_row_len(p) + 2 * sizeof(float2) * pad16((int)p->M[1]);
+    const int TPL = (int)(p->M[1] >> 4);
+    return (b <= 220 * 1024 && 2 * TPL <= 512) ? b : 0;
 }
 
 // ---------------------------------------------------------------- inverse (3D y)
@@ -562,6 +674,7 @@ static FusedParams make_fused_params(const sdf_plan_impl *p, bool adj = false) {
     F.M0 = (int)p->M[0];
     F.M1 = (int)p->M[1];
     F.nfield = p->nfield;
+    F.Hp = spec_row_len(p);
     return F;
 }
 
@@ -641,6 +754,16 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         const int64_t grid = (fused_lines + R - 1) / R;
         const V *twl = reinterpret_cast<const V *>(p->tw[D - 1]);
         prof_begin(p, "fused", st);
+        // paired-column variant: the built-in choice for 2D float plans that fit
+        const size_t smem2p = (!dense_in && sizeof(T) == 4) ? fused2p_smem(p) : 0;
+        if (smem2p && (p->tune_FV == 0 || p->tune_FV == 3)) {
+            if ((e = set_smem<T>((const void *)k_fused2p<T>, smem2p)) != cudaSuccess) return e;
+            k_fused2p<T><<<(unsigned)(M0 / 2 + 1), 2 * TPL, smem2p, st>>>(fin, fout, logL, fused_nin, (int)n_out,
+                                                                          in_fs, out_fs, F, (int)p->kernels.size(),
+                                                                          twl);
+            prof_end(p, st);
+            return cudaGetLastError();
+        }
 #define SDF_FUSED(DD, FVV)                                                                                 \
     do {                                                                                                   \
         if ((e = set_smem<T>((const void *)k_fused<T, DD, FVV>, smem)) != cudaSuccess) return e;          \

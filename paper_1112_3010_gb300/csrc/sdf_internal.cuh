@@ -152,6 +152,14 @@ cudaError_t launch_adjoint(sdf_plan_impl *p, int64_t K, const double *points, co
 
 double hessian_scale(const sdf_plan_impl *p);
 
+// Compressed spectrum of one kernel: one row per folded line-axis frequency
+// (2D: f0; 3D: (f1, f0)), each row the folded last-axis frequencies padded to
+// a multiple of 4 values (16-byte aligned rows).
+inline int64_t spec_row_len(const sdf_plan_impl *p) { return ((p->M[p->D - 1] / 2 + 1) + 3) & ~int64_t(3); }
+inline int64_t spec_rows(const sdf_plan_impl *p) {
+    return p->D == 2 ? p->M[0] / 2 + 1 : (p->M[0] / 2 + 1) * (p->M[1] / 2 + 1);
+}
+
 sdf_status plan_create_shared(sdf_plan *out, int D, const int64_t *dims, double h, double tau, int precision,
                               unsigned outputs, void *stream, const sdf_plan_impl *share_from);
 

@@ -103,7 +103,7 @@ __global__ void k_sample(SampleCfg c, double2 *out, double *part, int64_t total)
 // Compress: c(fold) = Re(Khat(fold) * conj(zeta)) * scale, zeta = (-i)^nodd.
 template <typename T>
 __global__ void k_compress(const double2 *__restrict__ K, T *c, int D, int64_t M0, int64_t M1, int64_t M2, int nodd,
-                           double scale, double *resid) {
+                           double scale, double *resid, int64_t Hp) {
     const int64_t H0 = M0 / 2 + 1, H1 = M1 / 2 + 1, H2 = (D == 3) ? M2 / 2 + 1 : 1;
     const int64_t total = H0 * H1 * H2;
     double worst = 0.0;
@@ -112,12 +112,12 @@ __global__ void k_compress(const double2 *__restrict__ K, T *c, int D, int64_t M
         if (D == 2) {
             f1 = i % H1;
             f0 = i / H1;
-            dst = f0 * H1 + f1;
+            dst = f0 * Hp + f1;
         } else {
             f2 = i % H2;
             f0 = (i / H2) % H0;
             f1 = i / (H2 * H0);
-            dst = (f1 * H0 + f0) * H2 + f2;
+            dst = (f1 * H0 + f0) * Hp + f2;
         }
         const double2 k = K[f0 + M0 * (f1 + M1 * f2)];
         // conj(zeta) for zeta = (-i)^nodd: (+i)^nodd
@@ -181,7 +181,10 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
     std::vector<double> hpart(nblk);
     double inv_n = 1.0 / (double)total;
     const int64_t H0 = p->M[0] / 2 + 1, H1 = p->M[1] / 2 + 1, H2 = (D == 3) ? p->M[2] / 2 + 1 : 1;
-    const int64_t ctotal = H0 * H1 * H2;
+    const int64_t ctotal = spec_rows(p) * spec_row_len(p);
+    (void)H0;
+    (void)H1;
+    (void)H2;
     const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
     for (auto &ks : p->kernels) {
         SampleCfg c;
@@ -213,12 +216,13 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
         const int nodd = __builtin_popcount((unsigned)ks.parity);
         double scale = inv_n * ks.scale;
         if ((e = cudaMalloc(&ks.c, esz * ctotal)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(ks.c, 0, esz * ctotal, st)) != cudaSuccess) break;
         if (p->prec == SDF_FP64)
             k_compress<double><<<1024, 256, 0, st>>>(src, reinterpret_cast<double *>(ks.c), D, p->M[0], p->M[1],
-                                                     p->M[2], nodd, scale, resid);
+                                                     p->M[2], nodd, scale, resid, spec_row_len(p));
         else
             k_compress<float><<<1024, 256, 0, st>>>(src, reinterpret_cast<float *>(ks.c), D, p->M[0], p->M[1],
-                                                    p->M[2], nodd, scale, resid);
+                                                    p->M[2], nodd, scale, resid, spec_row_len(p));
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
         double l1 = 0.0;
@@ -276,10 +280,10 @@ cudaError_t build_spectra_into(sdf_plan_impl *p, double2 *bufX, double2 *bufY, d
         const double scale = inv_n * ks.scale;
         if (p->prec == SDF_FP64)
             k_compress<double><<<1024, 256, 0, st>>>(src, reinterpret_cast<double *>(ks.c), D, p->M[0], p->M[1],
-                                                     p->M[2], nodd, scale, nullptr);
+                                                     p->M[2], nodd, scale, nullptr, spec_row_len(p));
         else
             k_compress<float><<<1024, 256, 0, st>>>(src, reinterpret_cast<float *>(ks.c), D, p->M[0], p->M[1],
-                                                    p->M[2], nodd, scale, nullptr);
+                                                    p->M[2], nodd, scale, nullptr, spec_row_len(p));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
         double l1 = 0.0;
