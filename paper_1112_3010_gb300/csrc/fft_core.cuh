@@ -45,6 +45,16 @@ template <bool INV, typename V> __device__ __forceinline__ V mul_mi(V a) {
 
 __host__ __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
 
+// Shared-memory stride between the R lines of a CTA.  Threads of a warp
+// interleave lines (line = tid % R), and pad16(L) is a multiple of 16, so
+// without an offset all R lines would hit the same banks; an offset of
+// (elements per 128 bytes)/R staggers them across the banks.
+__host__ __device__ __forceinline__ int line_stride(int PL, int R, int vbytes) {
+    if (R <= 1) return PL;
+    const int per = 128 / vbytes;
+    return PL + (per / R > 0 ? per / R : 1);
+}
+
 // Multiply by w16^K = exp(-+2 pi i K/16) for a compile-time K in [0, 16).
 template <int K, bool INV, typename V> __device__ __forceinline__ V mul_w16(V a) {
     using T = decltype(V::x);

@@ -8,12 +8,15 @@
 // motivates the problem (Sec. 3.3, double precision fails far from the points)
 // but gives no mechanism; this one is ours.
 //
-// One CTA per flagged 8^D tile (one thread per node).  Candidate bins are
-// visited in rings of Chebyshev distance k = 0, 1, 2, ... around the tile;
-// after ring k every unvisited occupied node lies at least lb = (8k+1)h from
-// every node of the tile, so a node stops summing once K exp(-(lb - m)/tau)
-// is below 1e-5 of its sum, or once even its sum plus K exp(-lb/tau) is below
-// theta_64 (it stays capped).  Terms beyond m + tau ln(K 1e5) are skipped.  A
+// One CTA per flagged tile (2x2 bins of 8x8 nodes in 2D, one 8^3 bin in 3D),
+// two nodes per thread so that each staged point feeds two sums.  Candidate
+// bins are visited in rings of Chebyshev distance k = 0, 1, 2, ... around the
+// tile; after ring k every unvisited occupied node lies at least
+// lb = (8k+1)h from every node of the tile, so a node stops summing once
+// K exp(-(lb - m)/tau) is below 1e-5 of its sum, or once even its sum plus
+// K exp(-lb/tau) is below theta_64 (it stays capped).  Each staged batch of
+// points first gets a cheap pass for the nearest one (skipped when the batch
+// lies beyond the current m), so the summing loop itself has no branch.  A
 // tile whose nearest occupied bin is so far that K exp(-d/tau) < theta_64
 // keeps the capped value.  Visiting order is fixed, so the sums are
 // deterministic.
@@ -92,13 +95,35 @@ __device__ __forceinline__ void square_border(int s, int i, int &dx, int &dy) {
     }
 }
 
+// Hardware approximations (PTX ex2.approx / rsqrt.approx, relative error
+// about 2^-22): arguments here are never denormal (exponents lie in
+// [-40, 0], squared distances are integers >= 1).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// Index of the pair (a, b), a <= b, in the row-by-row upper triangle.
+template <int D> __device__ __forceinline__ constexpr int sym_index(int a, int b) {
+    return a * D - a * (a - 1) / 2 + (b - a);
+}
+
 template <int D, typename TO>
-__global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
+__global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 2) k_fixup(FixParams P) {
     constexpr int TB = (D == 2) ? kTB2 : 1;  // tile edge in bins
-    constexpr int NT = (D == 2) ? 64 * kTB2 * kTB2 : 512;
+    constexpr int NT = (D == 2) ? 32 * kTB2 * kTB2 : 256;
     constexpr int NH = D * (D + 1) / 2;
-    __shared__ int4 cell[kFixCap];  // (x, y, z, count) of staged occupied nodes
-    __shared__ int soff[1];
+    constexpr int NPT = 2;                    // nodes per thread
+    constexpr float kOff = (D == 2) ? 8.f : 4.f;  // second node: +kOff along the last axis
+    __shared__ float4 cell[kFixCap];  // (x, y, z, count) of staged occupied nodes
+    __shared__ int soff[NT + 1];      // first staged cell of each taken bin, then the total
+    __shared__ int ssrc[NT];          // the bin's first entry in ucell / ucount
+    __shared__ int sbin[NT];          // the bin's index
     __shared__ int wtot[32];
     const int tid = threadIdx.x;
     const int nt0 = (P.nb0 + TB - 1) / TB, nt1 = (P.nb1 + TB - 1) / TB;
@@ -122,45 +147,67 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
     // every node of the tile: phi <= K exp(-dlo/tau) < theta64 -> stays capped
     if (c >= 255 || P.logK - dlo / P.tau < lt) return;
 
+    // this thread's nodes: (x, y, z) and the same plus kOff along y (2D) or z (3D)
     const int x = (D == 2) ? bx * 8 + (tid % (8 * TB)) : bx * 8 + (tid & 7);
     const int y = (D == 2) ? by * 8 + (tid / (8 * TB)) : by * 8 + ((tid >> 3) & 7);
     const int z = (D == 2) ? 0 : bz * 8 + (tid >> 6);
-    const bool inb = x < P.N0 && y < P.N1 && (D == 2 || z < P.N2);
-    const int64_t node = (int64_t)x + (int64_t)P.N0 * (y + (int64_t)P.N1 * z);
-    const bool mine = inb && (P.flags[node] & SDF_FLAG_CAPPED) != 0;
-    bool active = mine;      // still summing
-    bool early_cap = false;  // shown below theta_64 before the sum finished
+    int64_t node[NPT];
+    bool mine[NPT], active[NPT], early_cap[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int yj = (D == 2) ? y + 8 * j : y, zj = (D == 2) ? 0 : z + 4 * j;
+        const bool inb = x < P.N0 && yj < P.N1 && (D == 2 || zj < P.N2);
+        node[j] = (int64_t)x + (int64_t)P.N0 * (yj + (int64_t)P.N1 * zj);
+        mine[j] = inb && (P.flags[node[j]] & SDF_FLAG_CAPPED) != 0;
+        active[j] = mine[j];   // still summing
+        early_cap[j] = false;  // shown below theta_64 before the sum finished
+    }
     const float h = (float)P.h, tau = (float)P.tau, itau = 1.f / tau, ih = 1.f / h;
-    const float l2e_tau = 1.4426950408889634f / tau;
-    // terms beyond m + ccut weigh < 1e-5 of the sum in total (K of them at most)
+    // distances are kept in grid units (node spacing 1); exp(-(r - m)/tau) =
+    // 2^((m - r) * l2e_th) with l2e_th = h log2(e)/tau
+    const float l2e_th = (float)(P.h * 1.4426950408889634 / P.tau);
     const float lnK = (float)P.logK;
-    const float ccut = tau * (lnK + 11.512925f);
-    float m = INFINITY, sE = 0.f, sG[D], sH[NH];
+    // node and cell coordinates are integers below 2^13, so the squared
+    // distances that matter (below 2^24) are exact in float
+    const float xf = (float)x, yf = (float)y, zf = (float)z;
+    // running sums per node, relative to exp(-m/tau), m the nearest occupied
+    // node seen so far: sE = sum c e, sA = sum c e/r, sG_a = sum c e d_a/r,
+    // sB_ab = sum c e d_a d_b (1/r_w + 1/tau)/r^2 (r in grid units, r_w = h r
+    // the distance, d = node - point); then H_ab = (delta_ab sA/h - sB_ab)/sE
+    // + g_a g_b/tau (eqs. Sxx, Syy, Sxy) and grad S = sG/sE (eq. SxSy)
+    float mg[NPT], mk[NPT], sE[NPT], sA[NPT], sG[NPT][D], sB[NPT][NH];
 #pragma unroll
-    for (int a = 0; a < D; ++a) sG[a] = 0.f;
+    for (int j = 0; j < NPT; ++j) {
+        mg[j] = INFINITY;
+        mk[j] = INFINITY;
+        sE[j] = 0.f;
+        sA[j] = 0.f;
 #pragma unroll
-    for (int a = 0; a < NH; ++a) sH[a] = 0.f;
-    unsigned long long nterm = 0;
+        for (int a = 0; a < D; ++a) sG[j][a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < NH; ++a) sB[j][a] = 0.f;
+    }
+    unsigned nterm = 0;
 
     // ring k: bins at Chebyshev distance k from the tile's block of bins
     auto nring_of = [&](int k) {
         return (D == 2) ? 4 * (TB + 2 * k - 1)
                         : ((k == 0) ? 1 : (2 * k + 1) * (2 * k + 1) * (2 * k + 1) - (2 * k - 1) * (2 * k - 1) * (2 * k - 1));
     };
-    // (m + ccut)^2 in grid units: terms beyond it are skipped before any MUFU work
-    float rc2 = INFINITY;
     const int kmax = max(max(P.nb0, P.nb1), (D == 3) ? P.nb2 : 0);
     // rings are visited in batches {0,1,2}, {3,4}, then one at a time: most
     // tiles finish in the first batch, one staging round
     for (int k0 = 0; k0 <= kmax;) {
-        if (!__syncthreads_or(active)) break;
+        if (!__syncthreads_or(active[0] || active[1])) break;
         const int k1 = min(kmax, (k0 == 0) ? 2 : (k0 == 3 ? 4 : k0));
+        // every node of ring k0 or beyond lies at least 8(k0-1)+1 from the tile
+        const float lb_in = (k0 == 0) ? 0.f : 8.f * (k0 - 1) + 1.f;
         int nring = 0;
         for (int k = k0; k <= k1; ++k) nring += nring_of(k);
         for (int i0 = 0; i0 < nring;) {
             // one candidate bin per thread
             const int i = i0 + tid;
-            int nb = 0, gb = -1;
+            int nb = 0, gb = -1, s0 = 0;
             if (i < nring) {
                 int k = k0, ii = i;
                 while (ii >= nring_of(k)) {
@@ -179,6 +226,7 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
                 if (qx >= 0 && qx < P.nb0 && qy >= 0 && qy < P.nb1 && (D == 2 || (qz >= 0 && qz < P.nb2))) {
                     gb = qx + P.nb0 * (qy + P.nb1 * qz);
                     nb = P.bin_nuniq[gb];
+                    s0 = P.bin_start[gb];
                 }
             }
             // block exclusive scan of nb
@@ -203,55 +251,94 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
             const int off = wtot[wid] + incl - nb;
             const bool take = (i < nring) && (off + nb <= kFixCap);
             const int taken = __syncthreads_count(take);  // taken bins form a prefix
-            if (tid == taken - 1) soff[0] = off + nb;
-            if (take && nb > 0) {
-                const int s0 = P.bin_start[gb];
-                const int qx = gb % P.nb0, qy = (gb / P.nb0) % P.nb1, qz = gb / (P.nb0 * P.nb1);
-                for (int e = 0; e < nb; ++e) {
-                    const int lc = P.ucell[s0 + e];
-                    cell[off + e] = make_int4(qx * 8 + (lc & 7), qy * 8 + ((lc >> 3) & 7), qz * 8 + (lc >> 6),
-                                              P.ucount[s0 + e]);
+            if (take) {
+                soff[tid] = off;
+                ssrc[tid] = s0;
+                sbin[tid] = gb;
+            }
+            if (tid == taken - 1) soff[taken] = off + nb;
+            __syncthreads();
+            const int ncell = (taken > 0) ? soff[taken] : 0;
+            // all threads copy: staged cell j belongs to the last taken bin
+            // whose first cell is <= j (empty bins share their successor's)
+            for (int j = tid; j < ncell; j += NT) {
+                int lo = 0, hi = taken - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (soff[mid] <= j) lo = mid;
+                    else hi = mid - 1;
                 }
+                const int g = sbin[lo], src = ssrc[lo] + (j - soff[lo]);
+                const int qx = g % P.nb0, qy = (g / P.nb0) % P.nb1, qz = g / (P.nb0 * P.nb1);
+                const int lc = P.ucell[src];
+                cell[j] = make_float4((float)(qx * 8 + (lc & 7)), (float)(qy * 8 + ((lc >> 3) & 7)),
+                                      (float)(qz * 8 + (lc >> 6)), (float)P.ucount[src]);
             }
             __syncthreads();
-            const int ncell = (taken > 0) ? soff[0] : 0;
-            if (active) {
-                for (int e = 0; e < ncell; ++e) {
-                    const int4 q = cell[e];
-                    const int ddx = x - q.x, ddy = y - q.y, ddz = (D == 3) ? z - q.z : 0;
-                    const int r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if ((float)r2 > rc2) continue;
-                    // r = h sqrt(r2) and 1/sqrt(r2) from one reciprocal square root
-                    const float ir = r2 > 0 ? rsqrtf((float)r2) : 0.f;
-                    const float r = (float)r2 * ir * h;
-                    if (r - m > ccut) continue;
-                    ++nterm;
-                    if (r < m) {
-                        const float sc = exp2f((r - m) * l2e_tau);
-                        sE *= sc;
+            if ((active[0] || active[1]) && ncell > 0) {
+                // a new nearest node is possible only while some node's m
+                // exceeds the ring's lower bound: find it first and move the
+                // shift there, so that the sum below never rescales
+                if (mg[0] > lb_in || mg[1] > lb_in) {
+                    float mn[NPT] = {INFINITY, INFINITY};
+                    for (int e = 0; e < ncell; ++e) {
+                        const float4 q = cell[e];
+                        const float d0 = xf - q.x, d1 = yf - q.y;
+                        const float cl = (D == 2) ? d1 : zf - q.z;
+                        const float base = (D == 2) ? d0 * d0 : fmaf(d0, d0, d1 * d1);
 #pragma unroll
-                        for (int a = 0; a < D; ++a) sG[a] *= sc;
-#pragma unroll
-                        for (int a = 0; a < NH; ++a) sH[a] *= sc;
-                        m = r;
-                        const float rc = (m + ccut) * ih * 1.0001f;
-                        rc2 = rc * rc;
+                        for (int j = 0; j < NPT; ++j) {
+                            const float cj = cl + kOff * j;
+                            mn[j] = fminf(mn[j], fmaf(cj, cj, base));
+                        }
                     }
-                    const float E = (float)q.w * exp2f((m - r) * l2e_tau);
-                    sE += E;
-                    if (r2 > 0) {
-                        const float nn[3] = {ddx * ir, ddy * ir, ddz * ir};
-                        const float irw = ir * ih;  // 1/r in world units
 #pragma unroll
-                        for (int a = 0; a < D; ++a) sG[a] += E * nn[a];
+                    for (int j = 0; j < NPT; ++j) {
+                        const float r = sqrtf(mn[j]);
+                        if (r < mg[j]) {
+                            const float sc = (mg[j] < INFINITY) ? ex2_approx((r - mg[j]) * l2e_th) : 0.f;
+                            sE[j] *= sc;
+                            sA[j] *= sc;
+#pragma unroll
+                            for (int a = 0; a < D; ++a) sG[j][a] *= sc;
+#pragma unroll
+                            for (int a = 0; a < NH; ++a) sB[j][a] *= sc;
+                            mg[j] = r;
+                            mk[j] = r * l2e_th;
+                        }
+                    }
+                }
+                nterm += (unsigned)ncell * ((mine[0] ? 1u : 0u) + (mine[1] ? 1u : 0u));
+#pragma unroll 2
+                for (int e = 0; e < ncell; ++e) {
+                    const float4 q = cell[e];
+                    const float d0 = xf - q.x, d1 = yf - q.y;
+                    const float cl = (D == 2) ? d1 : zf - q.z;
+                    const float base = (D == 2) ? d0 * d0 : fmaf(d0, d0, d1 * d1);
+#pragma unroll
+                    for (int j = 0; j < NPT; ++j) {
+                        const float cj = cl + kOff * j;
+                        const float d[3] = {d0, (D == 2) ? cj : d1, cj};
+                        const float r2 = fmaf(cj, cj, base);
+                        // 1/r from one reciprocal square root; r2 is an integer,
+                        // and the point under the node itself (r2 = 0) gets
+                        // 1/r = 0: it adds to the sum only
+                        const float ir = fminf(rsqrt_approx(r2), r2);
+                        const float rg = r2 * ir;
+                        const float E = q.w * ex2_approx(fmaf(-rg, l2e_th, mk[j]));
+                        const float Eir = E * ir;
+                        const float F = Eir * ir * fmaf(ir, ih, itau);
+                        sE[j] += E;
+                        sA[j] += Eir;
+#pragma unroll
+                        for (int a = 0; a < D; ++a) sG[j][a] = fmaf(Eir, d[a], sG[j][a]);
                         int qh = 0;
 #pragma unroll
-                        for (int a = 0; a < D; ++a, ++qh)
-                            sH[qh] += E * ((1.f - nn[a] * nn[a]) * irw - nn[a] * nn[a] * itau);
+                        for (int a = 0; a < D; ++a) {
+                            const float Fd = F * d[a];
 #pragma unroll
-                        for (int a = 0; a < D; ++a)
-#pragma unroll
-                            for (int bb = a + 1; bb < D; ++bb, ++qh) sH[qh] -= E * nn[a] * nn[bb] * (irw + itau);
+                            for (int bb = a; bb < D; ++bb, ++qh) sB[j][qh] = fmaf(Fd, d[bb], sB[j][qh]);
+                        }
                     }
                 }
             }
@@ -259,68 +346,83 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_fixup(FixParams P) {
             i0 += max(taken, 1);
         }
         // after ring k1 every unvisited node lies at least lb from this tile
-        if (active) {
-            const float lb = (8.f * k1 + 1.f) * h;
-            const float tailA = -lb * itau + lnK;                 // log of K exp(-lb/tau)
-            if (m < INFINITY) {
-                const float lsE = logf(sE);
+        const float lb = (8.f * k1 + 1.f) * h;
+        const float tailA = -lb * itau + lnK;  // log of K exp(-lb/tau)
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            if (!active[j]) continue;
+            if (mg[j] < INFINITY) {
+                const float m = mg[j] * h;
+                const float lsE = logf(sE[j]);
                 // the rest adds less than 1e-5 of the sum: final
-                if ((lb - m) * itau >= lnK - lsE + 11.512925f) active = false;
+                if ((lb - m) * itau >= lnK - lsE + 11.512925f) active[j] = false;
                 // phi < theta_64 whatever the rest adds: capped
                 const float A = -m * itau + lsE;
                 const float hi = fmaxf(A, tailA), lo = fminf(A, tailA);
                 if (hi + log1pf(expf(lo - hi)) < (float)lt - 1e-4f) {
-                    active = false;
-                    early_cap = true;
+                    active[j] = false;
+                    early_cap[j] = true;
                 }
             } else if (tailA < (float)lt - 1e-4f) {
-                active = false;
-                early_cap = true;
+                active[j] = false;
+                early_cap[j] = true;
             }
         }
         k0 = k1 + 1;
     }
     int fixed = 0, capped = 0;
-    if (mine) {
-        const double S = (double)m - P.tau * log((double)sE);
-        const double scap = -P.tau * lt;
-        TO *So = reinterpret_cast<TO *>(P.S);
-        TO *dS = reinterpret_cast<TO *>(P.dS);
-        TO *d2S = reinterpret_cast<TO *>(P.d2S);
-        const double sg = (P.sign && P.sign[node] < 0) ? -1.0 : 1.0;
-        if (early_cap || !(S <= scap)) {
-            capped = 1;
-            P.flags[node] = SDF_FLAG_CAPPED | SDF_FLAG_FIXUP;
-        } else {
-            fixed = 1;
-            if (So) So[node] = (TO)(sg * S);
-            const float inv = 1.f / sE;
-            float g[D];
+    TO *So = reinterpret_cast<TO *>(P.S);
+    TO *dS = reinterpret_cast<TO *>(P.dS);
+    TO *d2S = reinterpret_cast<TO *>(P.d2S);
+    const double scap = -P.tau * lt;
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                g[a] = sG[a] * inv;
-                if (dS) dS[a * P.nnodes + node] = (TO)g[a];
-            }
-            if (d2S) {
-                int q = 0;
-#pragma unroll
-                for (int a = 0; a < D; ++a, ++q) d2S[q * P.nnodes + node] = (TO)(sH[q] * inv + g[a] * g[a] * itau);
-#pragma unroll
-                for (int a = 0; a < D; ++a)
-#pragma unroll
-                    for (int bb = a + 1; bb < D; ++bb, ++q)
-                        d2S[q * P.nnodes + node] = (TO)(sH[q] * inv + g[a] * g[bb] * itau);
-            }
-            P.flags[node] = SDF_FLAG_FIXUP;
+    for (int j = 0; j < NPT; ++j) {
+        if (!mine[j]) continue;
+        const int64_t nd = node[j];
+        const double S = (double)mg[j] * P.h - P.tau * log((double)sE[j]);
+        const double sg = (P.sign && P.sign[nd] < 0) ? -1.0 : 1.0;
+        if (early_cap[j] || !(S <= scap)) {
+            ++capped;
+            P.flags[nd] = SDF_FLAG_CAPPED | SDF_FLAG_FIXUP;
+            continue;
         }
+        ++fixed;
+        if (So) So[nd] = (TO)(sg * S);
+        const float inv = 1.f / sE[j];
+        float g[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            g[a] = sG[j][a] * inv;
+            if (dS) dS[a * P.nnodes + nd] = (TO)g[a];
+        }
+        if (d2S) {
+            // sB is stored row by row (xx, xy, [xz,] yy, ...); d2S is
+            // diagonal first, then the pairs a < b
+            const float Ad = sA[j] * ih * inv;
+            int q = 0;
+#pragma unroll
+            for (int a = 0; a < D; ++a, ++q)
+                d2S[q * P.nnodes + nd] = (TO)(Ad - sB[j][sym_index<D>(a, a)] * inv + g[a] * g[a] * itau);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int bb = a + 1; bb < D; ++bb, ++q)
+                    d2S[q * P.nnodes + nd] = (TO)(-sB[j][sym_index<D>(a, bb)] * inv + g[a] * g[bb] * itau);
+        }
+        P.flags[nd] = SDF_FLAG_FIXUP;
     }
     // statistics
-    const unsigned fb = __ballot_sync(0xffffffffu, fixed), cb = __ballot_sync(0xffffffffu, capped);
-    for (int o = 16; o > 0; o >>= 1) nterm += __shfl_down_sync(0xffffffffu, nterm, o);
+    unsigned fx = fixed, cp = capped;
+    unsigned long long nt64 = nterm;
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_down_sync(0xffffffffu, fx, o);
+        cp += __shfl_down_sync(0xffffffffu, cp, o);
+        nt64 += __shfl_down_sync(0xffffffffu, nt64, o);
+    }
     if ((tid & 31) == 0) {
-        if (fb) atomicAdd(&P.dsc_w->n_fixup_nodes, (unsigned long long)__popc(fb));
-        if (cb) atomicAdd(&P.dsc_w->n_capped, (unsigned long long)__popc(cb));
-        if (nterm) atomicAdd(&P.dsc_w->n_fixup_terms, nterm);
+        if (fx) atomicAdd(&P.dsc_w->n_fixup_nodes, (unsigned long long)fx);
+        if (cp) atomicAdd(&P.dsc_w->n_capped, (unsigned long long)cp);
+        if (nt64) atomicAdd(&P.dsc_w->n_fixup_terms, nt64);
     }
     if (tid == 0) atomicAdd(&P.dsc_w->n_fixup_tiles, 1ull);
 }
@@ -358,9 +460,9 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS
     prof_begin(p, "fixup", p->stream);
     if (D == 2) {
         const int64_t nt = ((p->nb[0] + kTB2 - 1) / kTB2) * ((p->nb[1] + kTB2 - 1) / kTB2);
-        k_fixup<2, float><<<(unsigned)nt, 64 * kTB2 * kTB2, 0, p->stream>>>(F);
+        k_fixup<2, float><<<(unsigned)nt, 32 * kTB2 * kTB2, 0, p->stream>>>(F);
     } else {
-        k_fixup<3, float><<<(unsigned)p->nbins, 512, 0, p->stream>>>(F);
+        k_fixup<3, float><<<(unsigned)p->nbins, 256, 0, p->stream>>>(F);
     }
     prof_end(p, p->stream);
     return cudaGetLastError();

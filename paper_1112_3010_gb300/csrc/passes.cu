@@ -50,7 +50,7 @@ static inline LineCfg line_cfg(int logL, int R) {
 static inline int pick_R(int logL, size_t vbytes, int max_threads, int r_cap, size_t smem_budget) {
     int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
     int R = 1;
-    while (R * 2 <= r_cap && (R * 2) * TPL <= max_threads && (size_t)(R * 2) * PL * vbytes <= smem_budget) R *= 2;
+    while (R * 2 <= r_cap && (R * 2) * TPL <= max_threads && (size_t)(R * 2) * line_stride(PL, R * 2, (int)vbytes) * vbytes <= smem_budget) R *= 2;
     return R;
 }
 
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_
     const int z = valid ? (int)(line / N1) : 0;
     const int by = y >> 3, bz = z >> 3, ly = y & 7, lz = z & 7;
     const int64_t brow = (int64_t)nb0 * (by + (int64_t)nb1 * bz);
-    V *my = sm + lr * PL;
+    V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
     for (int f = 0; f < nfield; ++f) {
         if (f > 0) __syncthreads();
 #pragma unroll
@@ -127,7 +127,7 @@ __global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__rest
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
-    V *my = sm + lr * PL;
+    V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
     V v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(MT) k_fwd_T(const cx<T> *__restrict__ in, cx<T
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
-    V *my = sm + lr * PL;
+    V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
     for (int f = 0; f < nfield; ++f) {
         V v[16];
         const V *src = in + f * in_fs + line * n_in;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 3 : 1) k_fused(const cx<T
             line = (int64_t)pair_index((int)(lid / P.M0), P.M1) * P.M0 + pair_index((int)(lid % P.M0), P.M0);
         }
     }
-    V *my = sm + lr * PL;
+    V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
     int64_t cb;
     int flips;
     line_fold<T, D>(line, P, cb, flips);
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(MT) k_inv_T(const cx<T> *__restrict__ in, cx<T
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
-    V *my = sm + lr * PL;
+    V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
     for (int f = 0; f < nfield; ++f) {
         V v[16];
         const V *src = in + f * in_fs + line;
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
-    V *my = sm + lr * PL;
+    V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
     const int N0 = P.N0;
     const double c2 = (double)P.dsc->sum_c2;
     const double gn = sqrt(c2);
@@ -615,7 +615,7 @@ static int tuned_R(const sdf_plan_impl *p, int logL) {
     if (!p || p->tune_RT <= 0) return def;
     const int TPL = (1 << logL) >> 4, PL = pad16(1 << logL);
     int R = p->tune_RT;
-    while (R > 1 && (R * TPL > max_threads<T>() || (size_t)R * PL * sizeof(cx<T>) > kSmemBudget)) R >>= 1;
+    while (R > 1 && (R * TPL > max_threads<T>() || (size_t)R * line_stride(PL, R, (int)sizeof(cx<T>)) * sizeof(cx<T>) > kSmemBudget)) R >>= 1;
     return R;
 }
 
@@ -637,7 +637,7 @@ cudaError_t fwd_T_launch(const cx<T> *in, cx<T> *out, int logL, int n_in, int64_
                          int64_t out_fs, const cx<T> *tw, cudaStream_t st, sdf_plan_impl *p) {
     const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
-    const size_t smem = (size_t)R * c.PL * sizeof(cx<T>);
+    const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(cx<T>)) * sizeof(cx<T>);
     cudaError_t e;
     const int64_t grid = (n_lines + R - 1) / R;
     if (p) prof_begin(p, "fwd_y", st);
@@ -695,7 +695,7 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         const int R = dense_in ? pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget) : tuned_R<T>(p, logL);
         LineCfg c = line_cfg(logL, R);
         const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
-        const size_t smem = (size_t)R * c.PL * sizeof(V);
+        const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
         const int64_t grid = (n_lines + R - 1) / R;
         const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
         if (dense_in) {
@@ -746,7 +746,7 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         // the 3-blocks-per-SM register variant needs <= 256 threads
         const bool fv = p->tune_FV == 1 && R * TPL <= 256;
         LineCfg c = line_cfg(logL, R);
-        const size_t smem = (size_t)R * c.PL * sizeof(V);
+        const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
         FusedParams F = make_fused_params(p, dense_in != nullptr);
         if (dense_in) F.nfield = 1;
         const int64_t n_out = (D == 2) ? N1 : N2;
@@ -804,7 +804,7 @@ static cudaError_t inverse_mid(sdf_plan_impl *p, int ngroup, const cx<T> **last_
     const int logL = p->logM[1];
     const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
-    const size_t smem = (size_t)R * c.PL * sizeof(V);
+    const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
     cudaError_t e;
     const int64_t n_lines = M0 * N2;  // lines (u, z')
     const int64_t grid = (n_lines + R - 1) / R;
@@ -870,7 +870,7 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
     const int logL = p->logM[0];
     const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
-    const size_t smem = (size_t)R * c.PL * sizeof(V);
+    const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
     const int64_t grid = (n_lines + R - 1) / R;
     const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
     const bool big = R * c.TPL > 512;
@@ -919,7 +919,7 @@ __global__ void SDF_LB(T) k_epi_dense(const cx<T> *__restrict__ in, int logL, in
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
-    V *my = sm + lr * PL;
+    V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
     for (int g = 0; g < P.ngroup; ++g) {
         V v[16];
         const V *src = in + g * P.in_fs + line;
@@ -968,7 +968,7 @@ static cudaError_t adjoint_transforms_impl(sdf_plan_impl *p, const void *w, cons
     const int logL = p->logM[0];
     const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
     LineCfg c = line_cfg(logL, R);
-    const size_t smem = (size_t)R * c.PL * sizeof(V);
+    const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
     if ((e = set_smem<T>((const void *)k_epi_dense<T>, smem)) != cudaSuccess) return e;
     prof_begin(p, "epi_dense", p->stream);
     k_epi_dense<T><<<(unsigned)((n_lines + R - 1) / R), R * c.TPL, smem, p->stream>>>(
