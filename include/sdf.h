@@ -218,7 +218,7 @@ sdf_status sdf_plan_set_noise_constants(sdf_plan plan, double c_fp32, double c_f
 /*
  * Tile schedule.  lines_T: lines of the transforms each CTA of the transposed
  * passes (x-pass, 3D y-passes, epilogue) handles; lines_F: lines per CTA of the
- * fused pass; fused_variant: 1 = at most 256 threads and three CTAs per SM,
+ * fused pass; fused_variant: 1 = at most 256 threads and two CTAs per SM,
  * 2 = up to 128 registers per thread, 3 = 2D float plans: one CTA per pair of
  * mirror columns with the spectrum rows staged in shared memory (falls back to
  * 2 when it does not fit).  0 (or an invalid value, rounded down to a valid

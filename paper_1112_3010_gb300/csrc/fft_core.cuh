@@ -13,10 +13,16 @@
 // last stage has radix 2, 4 or 8 and each thread runs 16/radix butterflies.
 // Between stages data goes through shared memory with one pad element per 16
 // (index e -> e + e/16), which makes the stride-16 writes of the first stage
-// conflict-free.  Twiddles come from a per-length table tw[i] = exp(-2 pi i i/L)
-// computed in FP64 on the host (conjugated for the inverse).
+// conflict-free.  Twiddles come from a per-length table computed in long
+// double on the host (conjugated for the inverse): radix-16 stage s >= 1
+// (span Ns = 16^s) keeps w_{16 Ns}^{r k} at entry r*Ns + k - 16 (r = 1..15,
+// k < Ns), and a final radix-P stage (span Ns = L/P) keeps w_L^{r j} at
+// r*Ns + j - 16 (r < P, j < Ns).  Neighbouring k sit side by side, so the
+// lanes of a warp read neighbouring entries (no bank conflicts when the table
+// is in shared memory); L - 16 entries in all.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace sdf {
@@ -45,6 +51,37 @@ template <bool INV, typename V> __device__ __forceinline__ V mul_mi(V a) {
 
 __host__ __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
 
+// log2 of a power of two.
+__host__ __device__ __forceinline__ int ilog2(int64_t L) {
+    int k = 0;
+    while (((int64_t)1 << k) < L) ++k;
+    return k;
+}
+
+// Host: the twiddle table of an L = 2^logL line, in the layout above
+// (h holds L entries; the last 16 stay zero).
+template <typename V> inline void fill_twiddle_table(int logL, V *h) {
+    using T = decltype(V::x);
+    const int64_t L = (int64_t)1 << logL;
+    const int nst = logL >> 2, rem = logL & 3;
+    for (int64_t e = 0; e < L; ++e) h[e].x = h[e].y = T(0);
+    auto put = [&](int64_t e, int64_t i) {  // w_L^i
+        const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)i / (long double)L;
+        h[e].x = (T)cosl(ang);
+        h[e].y = (T)sinl(ang);
+    };
+    for (int s = 1; s < nst; ++s) {
+        const int64_t Ns = (int64_t)1 << (4 * s);
+        for (int64_t r = 1; r < 16; ++r)
+            for (int64_t k = 0; k < Ns; ++k) put(r * Ns + k - 16, r * k * (L / (16 * Ns)));
+    }
+    if (rem) {
+        const int64_t Ns = (int64_t)1 << (4 * nst), P = (int64_t)1 << rem;
+        for (int64_t r = 1; r < P; ++r)
+            for (int64_t j = 0; j < Ns; ++j) put(r * Ns + j - 16, r * j);
+    }
+}
+
 // Shared-memory stride between the R lines of a CTA.  Threads of a warp
 // interleave lines (line = tid % R), and pad16(L) is a multiple of 16, so
 // without an offset all R lines would hit the same banks; an offset of
@@ -53,6 +90,31 @@ __host__ __device__ __forceinline__ int line_stride(int PL, int R, int vbytes) {
     if (R <= 1) return PL;
     const int per = 128 / vbytes;
     return PL + (per / R > 0 ? per / R : 1);
+}
+
+// Float lines keep their L-entry twiddle table in shared memory, after the
+// line buffers; double lines (whose table would not fit beside an 8192-point
+// line) read it from global memory.
+__host__ __device__ __forceinline__ constexpr bool twiddles_in_smem(int vbytes) { return vbytes == 8; }
+
+// Shared memory of a CTA of R lines: the R staggered line buffers, then the
+// twiddle table when it is staged.
+__host__ __device__ __forceinline__ size_t line_smem(int R, int L, int vbytes) {
+    return ((size_t)R * line_stride(pad16(L), R, vbytes) + (twiddles_in_smem(vbytes) ? (size_t)L : 0)) *
+           (size_t)vbytes;
+}
+
+// The twiddle table fft_line reads: for float, copied to dst (shared memory
+// following the line buffers) -- fft_line reads twiddles only after its first
+// barrier, so no barrier is needed here; for double, the global table.
+template <typename V>
+__device__ __forceinline__ const V *stage_twiddles(V *dst, const V *__restrict__ tw, int L) {
+    if constexpr (!twiddles_in_smem((int)sizeof(V))) {
+        return tw;
+    } else {
+        for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = tw[i];
+        return dst;
+    }
 }
 
 // Multiply by w16^K = exp(-+2 pi i K/16) for a compile-time K in [0, 16).
@@ -145,19 +207,19 @@ template <bool INV, int S, typename V> __device__ __forceinline__ void dft8s(V *
     for (int q = 0; q < 8; ++q) a[q * S] = b[q];
 }
 
-template <typename V> __device__ __forceinline__ V ldtw(const V *__restrict__ tw, int i) { return __ldg(tw + i); }
+template <typename V> __device__ __forceinline__ V ldtw(const V *tw, int i) { return tw[i]; }
 
 // Final stage of radix P (2, 4 or 8): Ns = L/P, thread t runs butterflies
 // j = t + b*TPL (b < 16/P) on registers v[b + r*(16/P)].
 template <int P, bool INV, typename V>
-__device__ __forceinline__ void final_stage(V (&v)[16], int t, int TPL, const V *__restrict__ tw) {
+__device__ __forceinline__ void final_stage(V (&v)[16], int t, int TPL, int Ns, const V *__restrict__ tw) {
     constexpr int B = 16 / P;
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int j = t + b * TPL;  // < Ns, so k = j
 #pragma unroll
         for (int r = 1; r < P; ++r) {
-            V w = ldtw(tw, r * j);
+            V w = ldtw(tw, r * Ns + j - 16);
             v[b + r * B] = INV ? cmulc(v[b + r * B], w) : cmul(v[b + r * B], w);
         }
         if constexpr (P == 2) {
@@ -174,6 +236,7 @@ __device__ __forceinline__ void final_stage(V (&v)[16], int t, int TPL, const V 
 // normalised) of one line.  On entry v[m] = x[t + m*TPL]; on exit
 // v[m] = X[t + m*TPL].  `sm` is this line's shared buffer of pad16(L) elements.
 // Every thread of the CTA must call this with the same logL (it synchronises).
+// `tw` is the table of L twiddles (shared memory for float, global for double).
 template <bool INV, typename V>
 __device__ __forceinline__ void fft_line(V (&v)[16], V *sm, int t, int logL, const V *__restrict__ tw) {
     const int L = 1 << logL;
@@ -185,10 +248,10 @@ __device__ __forceinline__ void fft_line(V (&v)[16], V *sm, int t, int logL, con
         const int Ns = 1 << logNs;
         const int k = t & (Ns - 1);
         if (s > 0) {
-            const int step = k << (logL - 4 - logNs);  // k * L/(16 Ns)
+            const V *ts = tw + (k - 16);  // w_{16 Ns}^{r k} at ts[r * Ns]
 #pragma unroll
             for (int r = 1; r < 16; ++r) {
-                V w = ldtw(tw, r * step);
+                V w = ldtw(ts, r * Ns);
                 v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
             }
         }
@@ -203,9 +266,10 @@ __device__ __forceinline__ void fft_line(V (&v)[16], V *sm, int t, int logL, con
         for (int m = 0; m < 16; ++m) v[m] = sm[pad16(t + m * TPL)];
         logNs += 4;
     }
-    if (rem == 1) final_stage<2, INV>(v, t, TPL, tw);
-    else if (rem == 2) final_stage<4, INV>(v, t, TPL, tw);
-    else if (rem == 3) final_stage<8, INV>(v, t, TPL, tw);
+    const int Ns = 1 << logNs;
+    if (rem == 1) final_stage<2, INV>(v, t, TPL, Ns, tw);
+    else if (rem == 2) final_stage<4, INV>(v, t, TPL, Ns, tw);
+    else if (rem == 3) final_stage<8, INV>(v, t, TPL, Ns, tw);
 }
 
 }  // namespace sdf

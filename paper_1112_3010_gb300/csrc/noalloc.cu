@@ -72,11 +72,7 @@ template <typename T>
 cudaError_t fill_twiddles(void *dst, int64_t L) {
     using V = typename cplx_t<T>::type;
     std::vector<V> h(L);
-    for (int64_t i = 0; i < L; ++i) {
-        long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)i / (long double)L;
-        h[i].x = (T)cosl(ang);
-        h[i].y = (T)sinl(ang);
-    }
+    fill_twiddle_table(ilog2(L), h.data());
     return cudaMemcpy(dst, h.data(), sizeof(V) * L, cudaMemcpyHostToDevice);
 }
 

@@ -25,11 +25,10 @@ namespace sdf {
 
 template <typename T> using cx = typename cplx_t<T>::type;
 
-// Thread bound per precision: a double line needs twice the registers.
-#define SDF_LB(T) __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
-// Larger block variant: double lines never exceed 512 threads.
-template <typename T> constexpr int big_mt() { return sizeof(T) == 8 ? 512 : 1024; }
-template <typename T> constexpr int max_threads() { return sizeof(T) == 8 ? 512 : 1024; }
+// Line kernels run at most 512 threads per CTA: each thread holds 16 complex
+// values plus transform state, and 1024-thread CTAs (64 registers) spill.
+#define SDF_LB(T) __launch_bounds__(512)
+template <typename T> constexpr int max_threads() { return 512; }
 
 struct LineCfg {
     int logL, L, TPL, PL, R;
@@ -46,11 +45,11 @@ static inline LineCfg line_cfg(int logL, int R) {
 }
 
 // Lines per CTA: the largest power of two with R*TPL <= max_threads,
-// R*padded*sizeof(V) <= smem budget and R <= r_cap.
+// line_smem(R, L) <= smem budget and R <= r_cap.
 static inline int pick_R(int logL, size_t vbytes, int max_threads, int r_cap, size_t smem_budget) {
-    int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int L = 1 << logL, TPL = L >> 4;
     int R = 1;
-    while (R * 2 <= r_cap && (R * 2) * TPL <= max_threads && (size_t)(R * 2) * line_stride(PL, R * 2, (int)vbytes) * vbytes <= smem_budget) R *= 2;
+    while (R * 2 <= r_cap && (R * 2) * TPL <= max_threads && line_smem(R * 2, L, (int)vbytes) <= smem_budget) R *= 2;
     return R;
 }
 
@@ -76,6 +75,7 @@ __global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_
     const int by = y >> 3, bz = z >> 3, ly = y & 7, lz = z & 7;
     const int64_t brow = (int64_t)nb0 * (by + (int64_t)nb1 * bz);
     V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
+    const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
     for (int f = 0; f < nfield; ++f) {
         if (f > 0) __syncthreads();
 #pragma unroll
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_
         for (int m = 0; m < 8; ++m) v[m] = my[pad16(t + m * TPL)];
 #pragma unroll
         for (int m = 8; m < 16; ++m) v[m] = mk<V>(T(0), T(0));
-        fft_line<false>(v, my, t, logL, tw);
+        fft_line<false>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + f * out_fs + line;
 #pragma unroll
@@ -128,6 +128,7 @@ __global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__rest
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
     V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
+    const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
     V v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -143,7 +144,7 @@ __global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__rest
         v[m] = mk<V>(a, T(0));
     }
     __syncthreads();
-    fft_line<false>(v, my, t, logL, tw);
+    fft_line<false>(v, my, t, logL, tws);
     if (valid) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) out[(int64_t)(t + m * TPL) * n_lines + line] = v[m];
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(MT) k_fwd_T(const cx<T> *__restrict__ in, cx<T
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
     V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
+    const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
     for (int f = 0; f < nfield; ++f) {
         V v[16];
         const V *src = in + f * in_fs + line * n_in;
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(MT) k_fwd_T(const cx<T> *__restrict__ in, cx<T
             v[m] = (valid && e < n_in) ? src[e] : mk<V>(T(0), T(0));
         }
         __syncthreads();
-        fft_line<false>(v, my, t, logL, tw);
+        fft_line<false>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + f * out_fs + line;
 #pragma unroll
@@ -225,7 +227,7 @@ __device__ __forceinline__ void line_fold(int64_t line, const FusedParams &P, in
 // Forward along the last axis, multiply by the kernel spectra, inverse along the
 // same axis, keep the first n_out outputs.  Field spectra stay in registers.
 template <typename T, int D, int FV>
-__global__ void __launch_bounds__(FV ? 256 : 512, FV ? 3 : 1) k_fused(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int n_out,
+__global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int n_out,
                                                int R, int64_t n_lines, int64_t in_fs, int64_t out_fs, FusedParams P,
                                                const cx<T> *__restrict__ tw) {
     using V = cx<T>;
@@ -246,6 +248,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 3 : 1) k_fused(const cx<T
         }
     }
     V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
+    const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
     int64_t cb;
     int flips;
     line_fold<T, D>(line, P, cb, flips);
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 3 : 1) k_fused(const cx<T
             v[m] = (valid && m < 8 && e < n_in) ? src[e] : mk<V>(T(0), T(0));
         }
         __syncthreads();
-        fft_line<false>(v, my, t, logL, tw);
+        fft_line<false>(v, my, t, logL, tws);
     };
     auto run_group = [&](int g, const V (&A)[16], const V (&B)[16], const V (&C)[16]) {
         V v[16];
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 3 : 1) k_fused(const cx<T
             }
         }
         __syncthreads();
-        fft_line<true>(v, my, t, logL, tw);
+        fft_line<true>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + g * out_fs + line * n_out;
 #pragma unroll
@@ -349,6 +352,7 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
     const int u = hh == 0 ? j : M0 - j;
     const int flips = (u > M0 / 2) ? 1 : 0;
     V *my = sm + hh * PL;
+    const V *tws = stage_twiddles(sm + 2 * PL, tw, L);
     // stage the spectrum rows of j
     {
         const int per_row = (int)(Hp * sizeof(T) / 16);
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
             v[m] = (valid && m < 8 && e < n_in) ? src[e] : mk<V>(T(0), T(0));
         }
         __syncthreads();
-        fft_line<false>(v, my, t, logL, tw);
+        fft_line<false>(v, my, t, logL, tws);
     };
     auto run_group = [&](int g, const V (&A)[16], const V (&B)[16]) {
         V v[16];
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
             }
         }
         __syncthreads();
-        fft_line<true>(v, my, t, logL, tw);
+        fft_line<true>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + g * out_fs + (int64_t)u * n_out;
 #pragma unroll
@@ -426,7 +430,8 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
 // Shared memory of k_fused2p (0 when the 2D float plan does not fit).
 static size_t fused2p_smem(const sdf_plan_impl *p) {
     if (p->D != 2 || p->prec != SDF_FP32 || p->nfield > 2) return 0;
-    const size_t b = sizeof(float) * p->kernels.size() * spec_row_len(p) + 2 * sizeof(float2) * pad16((int)p->M[1]);
+    const size_t b = sizeof(float) * p->kernels.size() * spec_row_len(p) +
+                     sizeof(float2) * (2 * pad16((int)p->M[1]) + p->M[1]);  // rows, two lines, twiddles
     const int TPL = (int)(p->M[1] >> 4);
     return (b <= 220 * 1024 && 2 * TPL <= 512) ? b : 0;
 }
@@ -446,13 +451,14 @@ __global__ void __launch_bounds__(MT) k_inv_T(const cx<T> *__restrict__ in, cx<T
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
     V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
+    const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
     for (int f = 0; f < nfield; ++f) {
         V v[16];
         const V *src = in + f * in_fs + line;
 #pragma unroll
         for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
         __syncthreads();
-        fft_line<true>(v, my, t, logL, tw);
+        fft_line<true>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + f * out_fs + line * n_out;
 #pragma unroll
@@ -495,6 +501,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
     V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
+    const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
     const int N0 = P.N0;
     const double c2 = (double)P.dsc->sum_c2;
     const double gn = sqrt(c2);
@@ -526,7 +533,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
 #pragma unroll
         for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
         __syncthreads();
-        fft_line<true>(v, my, t, logL, tw);
+        fft_line<true>(v, my, t, logL, tws);
         if (!valid) continue;
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
@@ -613,23 +620,17 @@ template <typename T>
 static int tuned_R(const sdf_plan_impl *p, int logL) {
     const int def = pick_R(logL, sizeof(cx<T>), max_threads<T>(), 16, kSmemBudget);
     if (!p || p->tune_RT <= 0) return def;
-    const int TPL = (1 << logL) >> 4, PL = pad16(1 << logL);
+    const int TPL = (1 << logL) >> 4;
     int R = p->tune_RT;
-    while (R > 1 && (R * TPL > max_threads<T>() || (size_t)R * line_stride(PL, R, (int)sizeof(cx<T>)) * sizeof(cx<T>) > kSmemBudget)) R >>= 1;
+    while (R > 1 && (R * TPL > max_threads<T>() || line_smem(R, 1 << logL, (int)sizeof(cx<T>)) > kSmemBudget)) R >>= 1;
     return R;
 }
 
-// Launch kern<T, MT> with MT = 1024 only when the block needs it (more
-// registers per thread otherwise).  Needs `cudaError_t e` in scope.
-#define SDF_LAUNCH_MT(kern, T, nthr, grid, smem, st, ...)                                               \
-    do {                                                                                              \
-        if ((nthr) > 512) {                                                                           \
-            if ((e = set_smem<T>((const void *)kern<T, big_mt<T>()>, smem)) != cudaSuccess) return e; \
-            kern<T, big_mt<T>()><<<(unsigned)(grid), (nthr), (smem), (st)>>>(__VA_ARGS__);             \
-        } else {                                                                                      \
-            if ((e = set_smem<T>((const void *)kern<T, 512>, smem)) != cudaSuccess) return e;         \
-            kern<T, 512><<<(unsigned)(grid), (nthr), (smem), (st)>>>(__VA_ARGS__);                     \
-        }                                                                                             \
+// Launch kern<T, 512> (nthr <= 512).  Needs `cudaError_t e` in scope.
+#define SDF_LAUNCH_MT(kern, T, nthr, grid, smem, st, ...)                                     \
+    do {                                                                                    \
+        if ((e = set_smem<T>((const void *)kern<T, 512>, smem)) != cudaSuccess) return e;   \
+        kern<T, 512><<<(unsigned)(grid), (nthr), (smem), (st)>>>(__VA_ARGS__);               \
     } while (0)
 
 template <typename T>
@@ -637,7 +638,7 @@ cudaError_t fwd_T_launch(const cx<T> *in, cx<T> *out, int logL, int n_in, int64_
                          int64_t out_fs, const cx<T> *tw, cudaStream_t st, sdf_plan_impl *p) {
     const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
-    const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(cx<T>)) * sizeof(cx<T>);
+    const size_t smem = line_smem(R, c.L, (int)sizeof(cx<T>));
     cudaError_t e;
     const int64_t grid = (n_lines + R - 1) / R;
     if (p) prof_begin(p, "fwd_y", st);
@@ -695,7 +696,7 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         const int R = dense_in ? pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget) : tuned_R<T>(p, logL);
         LineCfg c = line_cfg(logL, R);
         const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
-        const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
+        const size_t smem = line_smem(R, c.L, (int)sizeof(V));
         const int64_t grid = (n_lines + R - 1) / R;
         const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
         if (dense_in) {
@@ -743,10 +744,10 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
             R = p->tune_RF;
             while (R > 1 && R * TPL > 512) R >>= 1;
         }
-        // the 3-blocks-per-SM register variant needs <= 256 threads
+        // the two-CTAs-per-SM variant needs <= 256 threads
         const bool fv = p->tune_FV == 1 && R * TPL <= 256;
         LineCfg c = line_cfg(logL, R);
-        const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
+        const size_t smem = line_smem(R, c.L, (int)sizeof(V));
         FusedParams F = make_fused_params(p, dense_in != nullptr);
         if (dense_in) F.nfield = 1;
         const int64_t n_out = (D == 2) ? N1 : N2;
@@ -804,7 +805,7 @@ static cudaError_t inverse_mid(sdf_plan_impl *p, int ngroup, const cx<T> **last_
     const int logL = p->logM[1];
     const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
-    const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
+    const size_t smem = line_smem(R, c.L, (int)sizeof(V));
     cudaError_t e;
     const int64_t n_lines = M0 * N2;  // lines (u, z')
     const int64_t grid = (n_lines + R - 1) / R;
@@ -870,23 +871,17 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
     const int logL = p->logM[0];
     const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
-    const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
+    const size_t smem = line_smem(R, c.L, (int)sizeof(V));
     const int64_t grid = (n_lines + R - 1) / R;
     const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
-    const bool big = R * c.TPL > 512;
 #define SDF_EPI(DD, MTT)                                                                                    \
     do {                                                                                                    \
         if ((e = set_smem<T>((const void *)k_epilogue<T, DD, MTT>, smem)) != cudaSuccess) return e;        \
         k_epilogue<T, DD, MTT><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0); \
     } while (0)
     prof_begin(p, "epilogue", p->stream);
-    if (D == 2) {
-        if (big) SDF_EPI(2, big_mt<T>());
-        else SDF_EPI(2, 512);
-    } else {
-        if (big) SDF_EPI(3, big_mt<T>());
-        else SDF_EPI(3, 512);
-    }
+    if (D == 2) SDF_EPI(2, 512);
+    else SDF_EPI(3, 512);
 #undef SDF_EPI
     prof_end(p, p->stream);
     (void)N2;
@@ -920,13 +915,14 @@ __global__ void SDF_LB(T) k_epi_dense(const cx<T> *__restrict__ in, int logL, in
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
     V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
+    const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
     for (int g = 0; g < P.ngroup; ++g) {
         V v[16];
         const V *src = in + g * P.in_fs + line;
 #pragma unroll
         for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
         __syncthreads();
-        fft_line<true>(v, my, t, logL, tw);
+        fft_line<true>(v, my, t, logL, tws);
         if (!valid) continue;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -968,7 +964,7 @@ static cudaError_t adjoint_transforms_impl(sdf_plan_impl *p, const void *w, cons
     const int logL = p->logM[0];
     const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
     LineCfg c = line_cfg(logL, R);
-    const size_t smem = (size_t)R * line_stride(c.PL, R, (int)sizeof(V)) * sizeof(V);
+    const size_t smem = line_smem(R, c.L, (int)sizeof(V));
     if ((e = set_smem<T>((const void *)k_epi_dense<T>, smem)) != cudaSuccess) return e;
     prof_begin(p, "epi_dense", p->stream);
     k_epi_dense<T><<<(unsigned)((n_lines + R - 1) / R), R * c.TPL, smem, p->stream>>>(

@@ -164,10 +164,7 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
     for (int a = 0; a < D; ++a) {
         const int64_t L = p->M[a];
         std::vector<double2> h(L);
-        for (int64_t i = 0; i < L; ++i) {
-            long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)i / (long double)L;
-            h[i] = make_double2((double)cosl(ang), (double)sinl(ang));
-        }
+        fill_twiddle_table(ilog2(L), h.data());
         if ((e = cudaMalloc(&tw64[a], sizeof(double2) * L)) != cudaSuccess) return e;
         if ((e = cudaMemcpy(tw64[a], h.data(), sizeof(double2) * L, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     }
