@@ -224,6 +224,52 @@ __device__ __forceinline__ void line_fold(int64_t line, const FusedParams &P, in
     }
 }
 
+// v[m] += beta * khat(w) * s[m] over a thread's 16 elements w = t + m*TPL of
+// a line of length L, where khat is the folded (real) kernel spectrum row c:
+// khat(w) = sg(w) c[w] for w <= L/2 and sg(w) c[L - w] above, the sign being
+// alo below the fold and ahi above it (odd kernels change sign across it;
+// w = L/2 takes alo).  beta is real (imag = false) or imaginary: every term
+// coefficient of the programme is a real multiple of 1 or i, and alo, ahi
+// carry that multiple.
+template <bool LDG, typename T, typename V>
+__device__ __forceinline__ void mac_term(V (&v)[16], const V (&s)[16], const T *c, int t, int TPL, int L, T alo, T ahi,
+                                         bool imag) {
+    const T *cp = c + t, *cn = c + (L - t);
+    auto coef = [&](int m) {
+        const T *q = (m < 8) ? cp + m * TPL : cn - m * TPL;
+        T val;
+        if constexpr (LDG) val = __ldg(q);
+        else val = *q;
+        return ((m < 8 || (m == 8 && t == 0)) ? alo : ahi) * val;
+    };
+    if (!imag) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const T a = coef(m);
+            v[m].x = fma(a, s[m].x, v[m].x);
+            v[m].y = fma(a, s[m].y, v[m].y);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const T a = coef(m);
+            v[m].x = fma(-a, s[m].y, v[m].x);
+            v[m].y = fma(a, s[m].x, v[m].y);
+        }
+    }
+}
+
+// The signs below and above the fold of a term's spectrum row, with its
+// coefficient folded in: lflip = the row's own fold flips an odd axis,
+// wodd = the kernel is odd along the line axis.
+template <typename T>
+__device__ __forceinline__ void term_coef(double br, double bi, bool lflip, bool wodd, T &alo, T &ahi, bool &imag) {
+    imag = (br == 0.0);
+    const T cf = T(imag ? bi : br);
+    alo = lflip ? -cf : cf;
+    ahi = (lflip != wodd) ? -cf : cf;
+}
+
 // Forward along the last axis, multiply by the kernel spectra, inverse along the
 // same axis, keep the first n_out outputs.  Field spectra stay in registers.
 template <typename T, int D, int FV>
@@ -233,7 +279,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
     using V = cx<T>;
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L), half = L >> 1;
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     // consecutive line ids visit frequency pairs (k, M-k), which read the same
     // folded spectrum row: the second read hits L2
@@ -274,22 +320,15 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
             const int slot = P.tk[g][k];
             const T *c = reinterpret_cast<const T *>(P.kc[slot]);
             const int par = P.kpar[slot];
-            const T br = T(P.br[g][k]), bi = T(P.bi[g][k]);
             const int f = P.tf[g][k];
             const bool lflip = (__popc(par & flips) & 1) != 0;
             const bool wodd = (par >> waxis) & 1;
-#pragma unroll
-            for (int m = 0; m < 16; ++m) {
-                const int w = t + m * TPL;
-                const int fw = w <= half ? w : L - w;
-                T val = __ldg(c + cb + fw);
-                if (lflip ^ (wodd && w > half)) val = -val;
-                const V s = (f == 0) ? A[m] : ((f == 1) ? B[m] : C[m]);
-                // v += (br + i bi) * val * s
-                const T pr = br * val, pi = bi * val;
-                v[m].x += pr * s.x - pi * s.y;
-                v[m].y += pr * s.y + pi * s.x;
-            }
+            T alo, ahi;
+            bool imag;
+            term_coef<T>(P.br[g][k], P.bi[g][k], lflip, wodd, alo, ahi, imag);
+            if (f == 2) mac_term<true>(v, C, c + cb, t, TPL, L, alo, ahi, imag);
+            else if (f == 1) mac_term<true>(v, B, c + cb, t, TPL, L, alo, ahi, imag);
+            else mac_term<true>(v, A, c + cb, t, TPL, L, alo, ahi, imag);
         }
         __syncthreads();
         fft_line<true>(v, my, t, logL, tws);
@@ -341,7 +380,7 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
                                                     const cx<T> *__restrict__ tw) {
     using V = cx<T>;
     extern __shared__ __align__(16) unsigned char smraw_p[];
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L), half = L >> 1;
+    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
     const int64_t Hp = P.Hp;
     T *crow = reinterpret_cast<T *>(smraw_p);                      // nker rows of Hp
     V *sm = reinterpret_cast<V *>(smraw_p + sizeof(T) * nker * Hp);  // two exchange lines
@@ -384,21 +423,13 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
             const int slot = P.tk[g][k];
             const T *c = crow + (int64_t)slot * Hp;
             const int par = P.kpar[slot];
-            const T br = T(P.br[g][k]), bi = T(P.bi[g][k]);
-            const bool useB = P.tf[g][k] != 0;
             const bool lflip = (par & flips & 1) != 0;
             const bool wodd = (par >> 1) & 1;
-#pragma unroll
-            for (int m = 0; m < 16; ++m) {
-                const int w = t + m * TPL;
-                const int fw = w <= half ? w : L - w;
-                T val = c[fw];
-                if (lflip ^ (wodd && w > half)) val = -val;
-                const V s = useB ? B[m] : A[m];
-                const T pr = br * val, pi = bi * val;
-                v[m].x += pr * s.x - pi * s.y;
-                v[m].y += pr * s.y + pi * s.x;
-            }
+            T alo, ahi;
+            bool imag;
+            term_coef<T>(P.br[g][k], P.bi[g][k], lflip, wodd, alo, ahi, imag);
+            if (P.tf[g][k] != 0) mac_term<false>(v, B, c, t, TPL, L, alo, ahi, imag);
+            else mac_term<false>(v, A, c, t, TPL, L, alo, ahi, imag);
         }
         __syncthreads();
         fft_line<true>(v, my, t, logL, tws);
