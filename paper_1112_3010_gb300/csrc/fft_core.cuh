@@ -232,44 +232,82 @@ __device__ __forceinline__ void final_stage(V (&v)[16], int t, int TPL, int Ns, 
     }
 }
 
+// One radix-16 stage (span Ns = 2^logNs) of an L-point line, then the
+// exchange through shared memory.  Addresses use pad16(a + 16 c) =
+// pad16(a) + 17 c: the stores of stage 0 go to 17 t + q, those of later
+// stages (Ns a multiple of 16) to pad16(base) + q * 17 Ns/16, and the loads to
+// pad16(t) + m * 17 TPL/16 when TPL is a multiple of 16.  Returns false when
+// this was the last stage (the result stays in v).
+template <bool INV, typename V>
+__device__ __forceinline__ bool fft_stage16(V (&v)[16], V *sm, int t, int logL, int logNs, bool last,
+                                            const V *__restrict__ tw) {
+    const int TPL = (1 << logL) >> 4;
+    const int Ns = 1 << logNs;
+    const int k = t & (Ns - 1);
+    if (logNs > 0) {
+        const V *ts = tw + (k - 16);  // w_{16 Ns}^{r k} at ts[r * Ns]
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            V w = ldtw(ts, r * Ns);
+            v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+        }
+    }
+    dft16<INV>(v);
+    if (last) return false;  // Ns*16 == L: v[q] = X[t + q*TPL]
+    __syncthreads();
+    if (logNs == 0) {
+        V *d = sm + 17 * t;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) d[q] = v[q];
+    } else {
+        const int base = ((t - k) << 4) + k;
+        const int st = Ns + (Ns >> 4);
+        V *d = sm + pad16(base);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) d[q * st] = v[q];
+    }
+    __syncthreads();
+    if (TPL >= 16) {
+        const V *s = sm + pad16(t);
+        const int st = TPL + (TPL >> 4);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = s[m * st];
+    } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = sm[pad16(t + m * TPL)];
+    }
+    return true;
+}
+
 // L-point FFT (forward: exp(-2 pi i nk/L); inverse: exp(+2 pi i nk/L), not
 // normalised) of one line.  On entry v[m] = x[t + m*TPL]; on exit
 // v[m] = X[t + m*TPL].  `sm` is this line's shared buffer of pad16(L) elements.
 // Every thread of the CTA must call this with the same logL (it synchronises).
 // `tw` is the table of L twiddles (shared memory for float, global for double).
-template <bool INV, typename V>
+// LOGL > 0 fixes log2 L at compile time (logL is then ignored): every stage is
+// unrolled, addresses become immediates, and inputs known to be zero or
+// outputs never read cost nothing.
+template <bool INV, int LOGL = 0, typename V>
 __device__ __forceinline__ void fft_line(V (&v)[16], V *sm, int t, int logL, const V *__restrict__ tw) {
-    const int L = 1 << logL;
-    const int TPL = L >> 4;
-    const int nst = logL >> 2;
-    const int rem = logL & 3;
-    int logNs = 0;
-    for (int s = 0; s < nst; ++s) {
-        const int Ns = 1 << logNs;
-        const int k = t & (Ns - 1);
-        if (s > 0) {
-            const V *ts = tw + (k - 16);  // w_{16 Ns}^{r k} at ts[r * Ns]
+    if constexpr (LOGL > 0) {
+        constexpr int nst = LOGL >> 2, rem = LOGL & 3;
 #pragma unroll
-            for (int r = 1; r < 16; ++r) {
-                V w = ldtw(ts, r * Ns);
-                v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
-            }
-        }
-        dft16<INV>(v);
-        if (s == nst - 1 && rem == 0) return;  // Ns*16 == L: v[q] = X[t + q*TPL]
-        __syncthreads();
-        const int base = ((t - k) << 4) + k;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) sm[pad16(base + (q << logNs))] = v[q];
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = sm[pad16(t + m * TPL)];
-        logNs += 4;
+        for (int s = 0; s < nst; ++s)
+            if (!fft_stage16<INV>(v, sm, t, LOGL, 4 * s, s == nst - 1 && rem == 0, tw)) return;
+        constexpr int TPL = (1 << LOGL) >> 4, Ns = 1 << (4 * nst);
+        if constexpr (rem == 1) final_stage<2, INV>(v, t, TPL, Ns, tw);
+        else if constexpr (rem == 2) final_stage<4, INV>(v, t, TPL, Ns, tw);
+        else if constexpr (rem == 3) final_stage<8, INV>(v, t, TPL, Ns, tw);
+    } else {
+        const int TPL = (1 << logL) >> 4;
+        const int nst = logL >> 2, rem = logL & 3;
+        for (int s = 0; s < nst; ++s)
+            if (!fft_stage16<INV>(v, sm, t, logL, 4 * s, s == nst - 1 && rem == 0, tw)) return;
+        const int Ns = 1 << (4 * nst);
+        if (rem == 1) final_stage<2, INV>(v, t, TPL, Ns, tw);
+        else if (rem == 2) final_stage<4, INV>(v, t, TPL, Ns, tw);
+        else if (rem == 3) final_stage<8, INV>(v, t, TPL, Ns, tw);
     }
-    const int Ns = 1 << logNs;
-    if (rem == 1) final_stage<2, INV>(v, t, TPL, Ns, tw);
-    else if (rem == 2) final_stage<4, INV>(v, t, TPL, Ns, tw);
-    else if (rem == 3) final_stage<8, INV>(v, t, TPL, Ns, tw);
 }
 
 }  // namespace sdf

@@ -14,9 +14,10 @@
 // tile; after ring k every unvisited occupied node lies at least
 // lb = (8k+1)h from every node of the tile, so a node stops summing once
 // K exp(-(lb - m)/tau) is below 1e-5 of its sum, or once even its sum plus
-// K exp(-lb/tau) is below theta_64 (it stays capped).  Each staged batch of
-// points first gets a cheap pass for the nearest one (skipped when the batch
-// lies beyond the current m), so the summing loop itself has no branch.  A
+// K exp(-lb/tau) is below theta_64 (it stays capped).  The log-sum-exp shift
+// m is the nearest point found by a cheap pass over the first batch of points
+// (and over a later batch only if it could hold a point so much nearer that a
+// term would exceed 2^60), so the summing loop itself has no branch.  A
 // tile whose nearest occupied bin is so far that K exp(-d/tau) < theta_64
 // keeps the capped value.  Visiting order is fixed, so the sums are
 // deterministic.
@@ -39,8 +40,8 @@ struct FixParams {
     int N0, N1, N2;
     int nb0, nb1, nb2;
     int64_t nnodes;
-    double h, tau, coef64;
-    double logK;
+    double coef64;
+    float h, tau, l2e_th, logK;  // spacing, tau, h log2(e)/tau, log K
     int fp64_out;
 };
 
@@ -141,9 +142,13 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
         c = min(c, (int)P.cheb[q]);
     }
     if (!flagged) return;
-    const double theta64 = P.coef64 * sqrt((double)P.dsc->sum_c2);
-    const double lt = log(theta64);
-    const double dlo = (c >= 1) ? (8.0 * (c - 1) + 1.0) * P.h : 0.0;
+    // log theta_64, worked out in double by one thread (the FP64 pipe is
+    // slow) and read by the CTA from shared memory
+    __shared__ float s_lt;
+    if (tid == 0) s_lt = (float)log(P.coef64 * sqrt((double)P.dsc->sum_c2));
+    __syncthreads();
+    const float lt = s_lt;
+    const float dlo = (c >= 1) ? (8.f * (c - 1) + 1.f) * P.h : 0.f;
     // every node of the tile: phi <= K exp(-dlo/tau) < theta64 -> stays capped
     if (c >= 255 || P.logK - dlo / P.tau < lt) return;
 
@@ -162,11 +167,11 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
         active[j] = mine[j];   // still summing
         early_cap[j] = false;  // shown below theta_64 before the sum finished
     }
-    const float h = (float)P.h, tau = (float)P.tau, itau = 1.f / tau, ih = 1.f / h;
+    const float h = P.h, tau = P.tau, itau = 1.f / tau, ih = 1.f / h;
     // distances are kept in grid units (node spacing 1); exp(-(r - m)/tau) =
     // 2^((m - r) * l2e_th) with l2e_th = h log2(e)/tau
-    const float l2e_th = (float)(P.h * 1.4426950408889634 / P.tau);
-    const float lnK = (float)P.logK;
+    const float l2e_th = P.l2e_th;
+    const float lnK = P.logK;
     // node and cell coordinates are integers below 2^13, so the squared
     // distances that matter (below 2^24) are exact in float
     const float xf = (float)x, yf = (float)y, zf = (float)z;
@@ -276,10 +281,12 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
             }
             __syncthreads();
             if ((active[0] || active[1]) && ncell > 0) {
-                // a new nearest node is possible only while some node's m
-                // exceeds the ring's lower bound: find it first and move the
-                // shift there, so that the sum below never rescales
-                if (mg[0] > lb_in || mg[1] > lb_in) {
+                // the shift m need not be the exact minimum, only keep every
+                // term in range: no shift yet, or a batch point that could
+                // be nearer than m by more than 60 tau ln 2 (term > 2^60),
+                // calls for the nearest point of the batch first
+                const float lim = 60.f / l2e_th;
+                if (mg[0] - lb_in > lim || mg[1] - lb_in > lim) {
                     float mn[NPT] = {INFINITY, INFINITY};
                     for (int e = 0; e < ncell; ++e) {
                         const float4 q = cell[e];
@@ -359,11 +366,11 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
                 // phi < theta_64 whatever the rest adds: capped
                 const float A = -m * itau + lsE;
                 const float hi = fmaxf(A, tailA), lo = fminf(A, tailA);
-                if (hi + log1pf(expf(lo - hi)) < (float)lt - 1e-4f) {
+                if (hi + log1pf(expf(lo - hi)) < lt - 1e-4f) {
                     active[j] = false;
                     early_cap[j] = true;
                 }
-            } else if (tailA < (float)lt - 1e-4f) {
+            } else if (tailA < lt - 1e-4f) {
                 active[j] = false;
                 early_cap[j] = true;
             }
@@ -374,13 +381,13 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
     TO *So = reinterpret_cast<TO *>(P.S);
     TO *dS = reinterpret_cast<TO *>(P.dS);
     TO *d2S = reinterpret_cast<TO *>(P.d2S);
-    const double scap = -P.tau * lt;
+    const float scap = -tau * lt;
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         if (!mine[j]) continue;
         const int64_t nd = node[j];
-        const double S = (double)mg[j] * P.h - P.tau * log((double)sE[j]);
-        const double sg = (P.sign && P.sign[nd] < 0) ? -1.0 : 1.0;
+        const float S = fmaf(mg[j], h, -tau * logf(sE[j]));
+        const float sg = (P.sign && P.sign[nd] < 0) ? -1.f : 1.f;
         if (early_cap[j] || !(S <= scap)) {
             ++capped;
             P.flags[nd] = SDF_FLAG_CAPPED | SDF_FLAG_FIXUP;
@@ -450,12 +457,13 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS
     F.nb1 = (int)p->nb[1];
     F.nb2 = (int)p->nb[2];
     F.nnodes = p->nnodes;
-    F.h = p->h;
-    F.tau = p->tau;
+    F.h = (float)p->h;
+    F.tau = (float)p->tau;
+    F.l2e_th = (float)(p->h * 1.4426950408889634 / p->tau);
     const int D = p->D;
     const double n = (double)p->M[0] * (double)p->M[1] * (D == 3 ? (double)p->M[2] : 1.0);
     F.coef64 = p->noise_c64 * ldexp(1.0, -53) * sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
-    F.logK = log((double)p->last_K);
+    F.logK = (float)log((double)p->last_K);
     F.fp64_out = 0;
     prof_begin(p, "fixup", p->stream);
     if (D == 2) {

@@ -138,7 +138,7 @@ __global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__rest
             const int64_t node = line * N0 + x;
             if (!(flags && (flags[node] & SDF_FLAG_CAPPED))) {
                 // a = w / phi = w exp(S/tau)
-                a = T((double)w[node] * exp((double)Ssaved[node] * inv_tau));
+                a = w[node] * exp(Ssaved[node] * T(inv_tau));
             }
         }
         v[m] = mk<V>(a, T(0));
@@ -193,6 +193,7 @@ struct FusedParams {
     int tk[kMaxGroups][3];     // kernel slot
     int tf[kMaxGroups][3];     // field
     double br[kMaxGroups][3], bi[kMaxGroups][3];
+    float brf[kMaxGroups][3], bif[kMaxGroups][3];  // the same in float (no FP64 work in float kernels)
     const void *kc[kMaxKernels];  // compressed spectra
     int kpar[kMaxKernels];        // parity bits
     int D;
@@ -263,9 +264,18 @@ __device__ __forceinline__ void mac_term(V (&v)[16], const V (&s)[16], const T *
 // coefficient folded in: lflip = the row's own fold flips an odd axis,
 // wodd = the kernel is odd along the line axis.
 template <typename T>
-__device__ __forceinline__ void term_coef(double br, double bi, bool lflip, bool wodd, T &alo, T &ahi, bool &imag) {
-    imag = (br == 0.0);
-    const T cf = T(imag ? bi : br);
+__device__ __forceinline__ void term_coef(const FusedParams &P, int g, int k, bool lflip, bool wodd, T &alo, T &ahi,
+                                          bool &imag) {
+    T br, bi;
+    if constexpr (sizeof(T) == 4) {
+        br = P.brf[g][k];
+        bi = P.bif[g][k];
+    } else {
+        br = P.br[g][k];
+        bi = P.bi[g][k];
+    }
+    imag = (br == T(0));
+    const T cf = imag ? bi : br;
     alo = lflip ? -cf : cf;
     ahi = (lflip != wodd) ? -cf : cf;
 }
@@ -325,7 +335,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
             const bool wodd = (par >> waxis) & 1;
             T alo, ahi;
             bool imag;
-            term_coef<T>(P.br[g][k], P.bi[g][k], lflip, wodd, alo, ahi, imag);
+            term_coef<T>(P, g, k, lflip, wodd, alo, ahi, imag);
             if (f == 2) mac_term<true>(v, C, c + cb, t, TPL, L, alo, ahi, imag);
             else if (f == 1) mac_term<true>(v, B, c + cb, t, TPL, L, alo, ahi, imag);
             else mac_term<true>(v, A, c + cb, t, TPL, L, alo, ahi, imag);
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
             const bool wodd = (par >> 1) & 1;
             T alo, ahi;
             bool imag;
-            term_coef<T>(P.br[g][k], P.bi[g][k], lflip, wodd, alo, ahi, imag);
+            term_coef<T>(P, g, k, lflip, wodd, alo, ahi, imag);
             if (P.tf[g][k] != 0) mac_term<false>(v, B, c, t, TPL, L, alo, ahi, imag);
             else mac_term<false>(v, A, c, t, TPL, L, alo, ahi, imag);
         }
@@ -534,12 +544,17 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
     const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
     const int N0 = P.N0;
-    const double c2 = (double)P.dsc->sum_c2;
-    const double gn = sqrt(c2);
-    const double theta64 = P.coef64 * gn;
-    const double theta32 = P.coef32 * gn;
-    const T theta = T(P.fixup ? theta32 : theta64);
-    const T scap = T(-P.tau * log(theta64));
+    // trust threshold and capped S: one thread works them out in double (the
+    // FP64 pipe is slow), the CTA reads them from shared memory
+    __shared__ T s_thr[2];
+    if (threadIdx.x == 0) {
+        const double gn = sqrt((double)P.dsc->sum_c2);
+        const double theta64 = P.coef64 * gn;
+        s_thr[0] = T(P.fixup ? P.coef32 * gn : theta64);
+        s_thr[1] = T(-P.tau * log(theta64));
+    }
+    __syncthreads();
+    const T theta = s_thr[0], scap = s_thr[1];
     const T tau = T(P.tau), itau = T(1.0 / P.tau), hs_inv = T(P.hs_inv);
     constexpr int NH = D * (D + 1) / 2;
 
@@ -579,7 +594,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
                 const bool tr = (trusted >> m) & 1;
                 switch (ch) {
                     case CH_MU: {
-                        const bool inside = fabs((double)val) >= 0.5;
+                        const bool inside = fabs(val) >= T(0.5);
                         if (!inside) sgn &= ~(1u << m);
                         if (P.sign) P.sign[node] = inside ? 1 : -1;
                         break;
@@ -696,6 +711,8 @@ static FusedParams make_fused_params(const sdf_plan_impl *p, bool adj = false) {
             F.tf[g][k] = grp[g].term[k].field;
             F.br[g][k] = grp[g].term[k].br;
             F.bi[g][k] = grp[g].term[k].bi;
+            F.brf[g][k] = (float)grp[g].term[k].br;
+            F.bif[g][k] = (float)grp[g].term[k].bi;
         }
     }
     for (size_t s = 0; s < p->kernels.size() && s < (size_t)kMaxKernels; ++s) {

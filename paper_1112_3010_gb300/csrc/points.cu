@@ -88,16 +88,20 @@ __global__ void k_dedupe(int D, int64_t K, const double *__restrict__ W, const i
         cnt[i] = 0;
         wf[0][i] = wf[1][i] = wf[2][i] = 0;
     }
-    // fixed-point scale: |w| * scale * K < 2^61
-    double scale = 0.0;
-    if (W) {
-        const double wm = __longlong_as_double((long long)dsc->wmax);
-        if (wm > 0.0) {
-            const int ex = ilogb((double)K * wm) + 1;  // K*wm < 2^ex
-            scale = ldexp(1.0, 61 - ex);
+    // fixed-point scale: |w| * scale * K < 2^61 (one thread works it out)
+    __shared__ double s_scale;
+    if (tid == 0) {
+        s_scale = 0.0;
+        if (W) {
+            const double wm = __longlong_as_double((long long)dsc->wmax);
+            if (wm > 0.0) {
+                const int ex = ilogb((double)K * wm) + 1;  // K*wm < 2^ex
+                s_scale = ldexp(1.0, 61 - ex);
+            }
         }
     }
     __syncthreads();
+    const double scale = s_scale;
     for (int i = s + tid; i < e; i += nt) {
         const long long en = entry[i];
         const int lc = (int)(en >> 40);
@@ -173,9 +177,13 @@ __device__ __forceinline__ int cheb_cap(const DevScalars *dsc, double coef64, do
 
 __global__ void k_cheb_x(const int *__restrict__ nuniq, unsigned char *out, int nb0, int64_t nbins,
                          const DevScalars *dsc, double coef64, double logK, double tau_over_h) {
+    // one thread works the cap out in double (the FP64 pipe is slow)
+    __shared__ int s_cap;
+    if (threadIdx.x == 0) s_cap = cheb_cap(dsc, coef64, logK, tau_over_h);
+    __syncthreads();
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbins) return;
-    const int cap = cheb_cap(dsc, coef64, logK, tau_over_h);
+    const int cap = s_cap;
     const int x = (int)(b % nb0);
     const int64_t row = b - x;
     int best = cap;
