@@ -384,11 +384,12 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <typename T>
+template <typename T, int LOGL = 0>
 __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in,
                                                     int n_out, int64_t in_fs, int64_t out_fs, FusedParams P, int nker,
                                                     const cx<T> *__restrict__ tw) {
     using V = cx<T>;
+    if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ __align__(16) unsigned char smraw_p[];
     const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
     const int64_t Hp = P.Hp;
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
             v[m] = (valid && m < 8 && e < n_in) ? src[e] : mk<V>(T(0), T(0));
         }
         __syncthreads();
-        fft_line<false>(v, my, t, logL, tws);
+        fft_line<false, LOGL>(v, my, t, logL, tws);
     };
     auto run_group = [&](int g, const V (&A)[16], const V (&B)[16]) {
         V v[16];
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
             else mac_term<false>(v, A, c, t, TPL, L, alo, ahi, imag);
         }
         __syncthreads();
-        fft_line<true>(v, my, t, logL, tws);
+        fft_line<true, LOGL>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + g * out_fs + (int64_t)u * n_out;
 #pragma unroll
@@ -529,12 +530,14 @@ struct EpiParams {
     int D;
     int fixup;  // FP32 plan: nodes below theta32 go to the fix-up
     double hs_inv;  // 1 / scale of the stored Hessian kernels
+    float tau_f, itau_f, hs_inv_f;  // tau, 1/tau, hs_inv in float (float kernels stay off the FP64 pipe)
 };
 
-template <typename T, int D, int MT>
+template <typename T, int D, int MT, int LOGL = 0>
 __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, int logL, int R, int64_t n_lines,
                                                    EpiParams P, const cx<T> *__restrict__ tw) {
     using V = cx<T>;
+    if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
@@ -555,7 +558,19 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     }
     __syncthreads();
     const T theta = s_thr[0], scap = s_thr[1];
-    const T tau = T(P.tau), itau = T(1.0 / P.tau), hs_inv = T(P.hs_inv);
+    T tau, itau, hs_inv;
+    if constexpr (sizeof(T) == 4) {
+        tau = P.tau_f;
+        itau = P.itau_f;
+        hs_inv = P.hs_inv_f;
+    } else {
+        tau = P.tau;
+        itau = 1.0 / P.tau;
+        hs_inv = P.hs_inv;
+    }
+    // bin row of this line, for the fix-up's tile flags
+    const int64_t brow = valid ? (int64_t)P.nb0 * (((int)(line % P.N1) >> 3) + (int64_t)P.nb1 * ((int)(line / P.N1) >> 3))
+                               : 0;
     constexpr int NH = D * (D + 1) / 2;
 
     T phi[8];
@@ -579,7 +594,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
 #pragma unroll
         for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
         __syncthreads();
-        fft_line<true>(v, my, t, logL, tws);
+        fft_line<true, LOGL>(v, my, t, logL, tws);
         if (!valid) continue;
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
@@ -607,11 +622,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
                         const T sv = ((sgn >> m) & 1) ? s : -s;
                         if (Sout) Sout[node] = sv;
                         if (P.flags) P.flags[node] = ok ? 0 : SDF_FLAG_CAPPED;
-                        if (!ok && P.fixup && P.tile_flag) {
-                            const int y = (int)(line % P.N1), z = (int)(line / P.N1);
-                            const int64_t b = (x >> 3) + (int64_t)P.nb0 * ((y >> 3) + (int64_t)P.nb1 * (z >> 3));
-                            P.tile_flag[b] = 1;
-                        }
+                        if (!ok && P.fixup && P.tile_flag) P.tile_flag[brow + (x >> 3)] = 1;
                         break;
                     }
                     case CH_GX:
@@ -806,10 +817,19 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         // paired-column variant: the built-in choice for 2D float plans that fit
         const size_t smem2p = (!dense_in && sizeof(T) == 4) ? fused2p_smem(p) : 0;
         if (smem2p && (p->tune_FV == 0 || p->tune_FV == 3)) {
-            if ((e = set_smem<T>((const void *)k_fused2p<T>, smem2p)) != cudaSuccess) return e;
-            k_fused2p<T><<<(unsigned)(M0 / 2 + 1), 2 * TPL, smem2p, st>>>(fin, fout, logL, fused_nin, (int)n_out,
-                                                                          in_fs, out_fs, F, (int)p->kernels.size(),
-                                                                          twl);
+#define SDF_F2P(LG)                                                                                        \
+    do {                                                                                                   \
+        if ((e = set_smem<T>((const void *)k_fused2p<T, LG>, smem2p)) != cudaSuccess) return e;            \
+        k_fused2p<T, LG><<<(unsigned)(M0 / 2 + 1), 2 * TPL, smem2p, st>>>(                                 \
+            fin, fout, logL, fused_nin, (int)n_out, in_fs, out_fs, F, (int)p->kernels.size(), twl);        \
+    } while (0)
+            if constexpr (sizeof(T) == 4) {
+                if (logL == 12) SDF_F2P(12);
+                else SDF_F2P(0);
+            } else {
+                SDF_F2P(0);
+            }
+#undef SDF_F2P
             prof_end(p, st);
             return cudaGetLastError();
         }
@@ -916,20 +936,29 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
     E.D = D;
     E.fixup = (p->prec == SDF_FP32) ? 1 : 0;
     E.hs_inv = 1.0 / hessian_scale(p);
+    E.tau_f = (float)p->tau;
+    E.itau_f = (float)(1.0 / p->tau);
+    E.hs_inv_f = (float)E.hs_inv;
     const int logL = p->logM[0];
     const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
     const size_t smem = line_smem(R, c.L, (int)sizeof(V));
     const int64_t grid = (n_lines + R - 1) / R;
     const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
-#define SDF_EPI(DD, MTT)                                                                                    \
-    do {                                                                                                    \
-        if ((e = set_smem<T>((const void *)k_epilogue<T, DD, MTT>, smem)) != cudaSuccess) return e;        \
-        k_epilogue<T, DD, MTT><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0); \
+#define SDF_EPI(DD, LG)                                                                                       \
+    do {                                                                                                      \
+        if ((e = set_smem<T>((const void *)k_epilogue<T, DD, 512, LG>, smem)) != cudaSuccess) return e;      \
+        k_epilogue<T, DD, 512, LG><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0); \
     } while (0)
     prof_begin(p, "epilogue", p->stream);
-    if (D == 2) SDF_EPI(2, 512);
-    else SDF_EPI(3, 512);
+    if constexpr (sizeof(T) == 4) {
+        if (D == 2 && logL == 12) SDF_EPI(2, 12);
+        else if (D == 2) SDF_EPI(2, 0);
+        else SDF_EPI(3, 0);
+    } else {
+        if (D == 2) SDF_EPI(2, 0);
+        else SDF_EPI(3, 0);
+    }
 #undef SDF_EPI
     prof_end(p, p->stream);
     (void)N2;
