@@ -1,6 +1,9 @@
-// passes.cu -- the FFT passes of one execute (Table 1 steps 2-6 of the paper,
-// and the same steps for the derivative kernels of Sec. 5 and the sign
-// kernels of Sec. 4).
+// passes.cuh -- kernels and launch helpers of the FFT passes of one execute
+// (Table 1 steps 2-6 of the paper, and the same steps for the derivative
+// kernels of Sec. 5 and the sign kernels of Sec. 4).  The launchers live in
+// passes_fwd.cu (x-pass, 3D y-pass), passes_fused.cu (fused pass) and
+// passes_inv.cu (inverse y-pass, epilogue, adjoint epilogue), which compile
+// in parallel.
 //
 // Grid layouts (x fastest unless stated; N_a nodes, M_a padded, M_a >= 2 N_a):
 //   2D:  x-pass   cells      -> T1[u][y]      (u < M0, y < N1)
@@ -15,9 +18,11 @@
 // CTA handles R consecutive lines so those accesses are R-element segments.
 // Input pruning: only the first N of M inputs of a forward line are nonzero.
 // Output pruning: only the first N outputs of an inverse line are kept.
+#pragma once
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "sdf_internal.cuh"
 
@@ -57,13 +62,14 @@ static inline int pick_R(int logL, size_t vbytes, int max_threads, int r_cap, si
 // Builds each line of the point fields from the deduplicated node list
 // (bin-grouped), transforms it along x and writes it transposed.
 // Field 0: (count, 0); field 1: (w_0, w_1); field 2: (w_2, 0).
-template <typename T, int MT>
+template <typename T, int MT, int LOGL = 0>
 __global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_start, const int *__restrict__ bin_nuniq,
                                                       const int *__restrict__ ucell, const int *__restrict__ ucount,
                                                       const double *__restrict__ uw, int N1, int nb0, int nb1,
                                                       int logL, int R, int nfield, int64_t n_lines, cx<T> *out,
                                                       int64_t out_fs, const cx<T> *__restrict__ tw) {
     using V = cx<T>;
+    if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
@@ -104,7 +110,7 @@ __global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_
         for (int m = 0; m < 8; ++m) v[m] = my[pad16(t + m * TPL)];
 #pragma unroll
         for (int m = 8; m < 16; ++m) v[m] = mk<V>(T(0), T(0));
-        fft_line<false>(v, my, t, logL, tws);
+        fft_line<false, LOGL>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + f * out_fs + line;
 #pragma unroll
@@ -115,12 +121,13 @@ __global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_
 
 // x-pass of a dense real grid a(X) = w(X)/phi(X) (the adjoint's input), with
 // phi = exp(-S/tau) from the forward's unsigned S; nodes flagged CAPPED give 0.
-template <typename T>
+template <typename T, int LOGL = 0>
 __global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__restrict__ Ssaved,
                                                       const uint8_t *__restrict__ flags, double inv_tau, int N0,
                                                       int logL, int R, int64_t n_lines, cx<T> *out,
                                                       const cx<T> *__restrict__ tw) {
     using V = cx<T>;
+    if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
@@ -144,7 +151,7 @@ __global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__rest
         v[m] = mk<V>(a, T(0));
     }
     __syncthreads();
-    fft_line<false>(v, my, t, logL, tws);
+    fft_line<false, LOGL>(v, my, t, logL, tws);
     if (valid) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) out[(int64_t)(t + m * TPL) * n_lines + line] = v[m];
@@ -155,11 +162,12 @@ __global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__rest
 // Contiguous lines of n_in stored values (the rest of the L inputs are zero),
 // forward transform, transposed output.  Used for the 3D y-pass and for the
 // plan-time kernel transforms (n_in = L).
-template <typename T, int MT>
+template <typename T, int MT, int LOGL = 0>
 __global__ void __launch_bounds__(MT) k_fwd_T(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int R,
                                                 int64_t n_lines, int nfield, int64_t in_fs, int64_t out_fs,
                                                 const cx<T> *__restrict__ tw) {
     using V = cx<T>;
+    if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(MT) k_fwd_T(const cx<T> *__restrict__ in, cx<T
             v[m] = (valid && e < n_in) ? src[e] : mk<V>(T(0), T(0));
         }
         __syncthreads();
-        fft_line<false>(v, my, t, logL, tws);
+        fft_line<false, LOGL>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + f * out_fs + line;
 #pragma unroll
@@ -282,11 +290,12 @@ __device__ __forceinline__ void term_coef(const FusedParams &P, int g, int k, bo
 
 // Forward along the last axis, multiply by the kernel spectra, inverse along the
 // same axis, keep the first n_out outputs.  Field spectra stay in registers.
-template <typename T, int D, int FV>
+template <typename T, int D, int FV, int LOGL = 0>
 __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int n_out,
                                                int R, int64_t n_lines, int64_t in_fs, int64_t out_fs, FusedParams P,
                                                const cx<T> *__restrict__ tw) {
     using V = cx<T>;
+    if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
@@ -320,7 +329,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
             v[m] = (valid && m < 8 && e < n_in) ? src[e] : mk<V>(T(0), T(0));
         }
         __syncthreads();
-        fft_line<false>(v, my, t, logL, tws);
+        fft_line<false, LOGL>(v, my, t, logL, tws);
     };
     auto run_group = [&](int g, const V (&A)[16], const V (&B)[16], const V (&C)[16]) {
         V v[16];
@@ -341,7 +350,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
             else mac_term<true>(v, A, c + cb, t, TPL, L, alo, ahi, imag);
         }
         __syncthreads();
-        fft_line<true>(v, my, t, logL, tws);
+        fft_line<true, LOGL>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + g * out_fs + line * n_out;
 #pragma unroll
@@ -470,7 +479,7 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
 }
 
 // Shared memory of k_fused2p (0 when the 2D float plan does not fit).
-static size_t fused2p_smem(const sdf_plan_impl *p) {
+static inline size_t fused2p_smem(const sdf_plan_impl *p) {
     if (p->D != 2 || p->prec != SDF_FP32 || p->nfield > 2) return 0;
     const size_t b = sizeof(float) * p->kernels.size() * spec_row_len(p) +
                      sizeof(float2) * (2 * pad16((int)p->M[1]) + p->M[1]);  // rows, two lines, twiddles
@@ -481,11 +490,12 @@ static size_t fused2p_smem(const sdf_plan_impl *p) {
 // ---------------------------------------------------------------- inverse (3D y)
 // Transposed input (all L elements), inverse transform, contiguous output of
 // the first n_out elements.
-template <typename T, int MT>
+template <typename T, int MT, int LOGL = 0>
 __global__ void __launch_bounds__(MT) k_inv_T(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_out, int R,
                                                 int64_t n_lines, int nfield, int64_t in_fs, int64_t out_fs,
                                                 const cx<T> *__restrict__ tw) {
     using V = cx<T>;
+    if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
@@ -500,7 +510,7 @@ __global__ void __launch_bounds__(MT) k_inv_T(const cx<T> *__restrict__ in, cx<T
 #pragma unroll
         for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
         __syncthreads();
-        fft_line<true>(v, my, t, logL, tws);
+        fft_line<true, LOGL>(v, my, t, logL, tws);
         if (valid) {
             V *o = out + f * out_fs + line * n_out;
 #pragma unroll
@@ -662,9 +672,9 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     }
 }
 
-// ---------------------------------------------------------------- launchers
+// ---------------------------------------------------------------- launch helpers
 template <typename T>
-static cudaError_t set_smem(const void *fn, size_t bytes) {
+static inline cudaError_t set_smem(const void *fn, size_t bytes) {
     if (bytes > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     return cudaSuccess;
 }
@@ -674,7 +684,7 @@ constexpr size_t kSmemBudget = 200 * 1024;
 // Lines per CTA of a transposed pass: the plan's tuning when set and valid,
 // else pick_R.
 template <typename T>
-static int tuned_R(const sdf_plan_impl *p, int logL) {
+static inline int tuned_R(const sdf_plan_impl *p, int logL) {
     const int def = pick_R(logL, sizeof(cx<T>), max_threads<T>(), 16, kSmemBudget);
     if (!p || p->tune_RT <= 0) return def;
     const int TPL = (1 << logL) >> 4;
@@ -683,33 +693,34 @@ static int tuned_R(const sdf_plan_impl *p, int logL) {
     return R;
 }
 
-// Launch kern<T, 512> (nthr <= 512).  Needs `cudaError_t e` in scope.
-#define SDF_LAUNCH_MT(kern, T, nthr, grid, smem, st, ...)                                     \
-    do {                                                                                    \
-        if ((e = set_smem<T>((const void *)kern<T, 512>, smem)) != cudaSuccess) return e;   \
-        kern<T, 512><<<(unsigned)(grid), (nthr), (smem), (st)>>>(__VA_ARGS__);               \
+// Launch kern<T, 512, LG> (nthr <= 512).  Needs `cudaError_t e` in scope.
+#define SDF_LAUNCH_MT(kern, T, LG, nthr, grid, smem, st, ...)                                   \
+    do {                                                                                      \
+        if ((e = set_smem<T>((const void *)kern<T, 512, LG>, smem)) != cudaSuccess) return e; \
+        kern<T, 512, LG><<<(unsigned)(grid), (nthr), (smem), (st)>>>(__VA_ARGS__);             \
     } while (0)
 
-template <typename T>
-cudaError_t fwd_T_launch(const cx<T> *in, cx<T> *out, int logL, int n_in, int64_t n_lines, int nfield, int64_t in_fs,
-                         int64_t out_fs, const cx<T> *tw, cudaStream_t st, sdf_plan_impl *p) {
-    const int R = tuned_R<T>(p, logL);
-    LineCfg c = line_cfg(logL, R);
-    const size_t smem = line_smem(R, c.L, (int)sizeof(cx<T>));
-    cudaError_t e;
-    const int64_t grid = (n_lines + R - 1) / R;
-    if (p) prof_begin(p, "fwd_y", st);
-    SDF_LAUNCH_MT(k_fwd_T, T, R * c.TPL, grid, smem, st, in, out, logL, n_in, R, n_lines, nfield, in_fs, out_fs, tw);
-    if (p) prof_end(p, st);
-    return cudaGetLastError();
-}
-template cudaError_t fwd_T_launch<double>(const double2 *, double2 *, int, int, int64_t, int, int64_t, int64_t,
-                                          const double2 *, cudaStream_t, sdf_plan_impl *);
-template cudaError_t fwd_T_launch<float>(const float2 *, float2 *, int, int, int64_t, int, int64_t, int64_t,
-                                         const float2 *, cudaStream_t, sdf_plan_impl *);
+// CALL(LG) with LG = logL for the float line lengths compiled with a fixed
+// size (256 to 4096 points: every length the workloads use) and LG = 0 (the
+// length read at run time) for the rest and for double.
+#define SDF_BY_LOGL(T, logL, CALL)          \
+    do {                                    \
+        if constexpr (sizeof(T) == 4) {     \
+            switch (logL) {                 \
+                case 8: CALL(8); break;     \
+                case 9: CALL(9); break;     \
+                case 10: CALL(10); break;   \
+                case 11: CALL(11); break;   \
+                case 12: CALL(12); break;   \
+                default: CALL(0); break;    \
+            }                               \
+        } else {                            \
+            CALL(0);                        \
+        }                                   \
+    } while (0)
 
 // adj: the adjoint programme (transform of a = w/phi) instead of the forward one
-static FusedParams make_fused_params(const sdf_plan_impl *p, bool adj = false) {
+static inline FusedParams make_fused_params(const sdf_plan_impl *p, bool adj = false) {
     FusedParams F;
     memset(&F, 0, sizeof(F));
     const int ng = adj ? p->adj_ngroup : p->ngroup;
@@ -738,321 +749,10 @@ static FusedParams make_fused_params(const sdf_plan_impl *p, bool adj = false) {
     return F;
 }
 
+// The fused pass (passes_fused.cu): forward along the last axis, multiply by
+// the kernel spectra, inverse; dense: the adjoint programme.
 template <typename T>
-static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void *dense_in, const uint8_t *flags_in) {
-    using V = cx<T>;
-    cudaStream_t st = p->stream;
-    cudaError_t e;
-    const int D = p->D;
-    const int nfield = dense_in ? 1 : (with_weights ? p->nfield : 1);
-    V *A = reinterpret_cast<V *>(p->bufA);
-    V *B = reinterpret_cast<V *>(p->bufB);
-    const int64_t N0 = p->N[0], N1 = p->N[1], N2 = p->N[2];
-    const int64_t M0 = p->M[0], M1 = p->M[1];
-    // ---- x-pass
-    {
-        const int logL = p->logM[0];
-        const int R = dense_in ? pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget) : tuned_R<T>(p, logL);
-        LineCfg c = line_cfg(logL, R);
-        const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
-        const size_t smem = line_smem(R, c.L, (int)sizeof(V));
-        const int64_t grid = (n_lines + R - 1) / R;
-        const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
-        if (dense_in) {
-            const T *const *pair = reinterpret_cast<const T *const *>(dense_in);
-            if ((e = set_smem<T>((const void *)k_xpass_dense<T>, smem)) != cudaSuccess) return e;
-            prof_begin(p, "xpass_dense", st);
-            k_xpass_dense<T><<<(unsigned)grid, R * c.TPL, smem, st>>>(pair[0], pair[1], flags_in, 1.0 / p->tau,
-                                                                     (int)N0, logL, R, n_lines, A, tw0);
-            prof_end(p, st);
-        } else {
-            prof_begin(p, "xpass", st);
-            SDF_LAUNCH_MT(k_xpass_cells, T, R * c.TPL, grid, smem, st, p->bin_start, p->bin_nuniq, p->ucell,
-                          p->ucount, p->uw, (int)N1, (int)p->nb[0], (int)p->nb[1], logL, R, nfield, n_lines, A,
-                          M0 * n_lines, tw0);
-            prof_end(p, st);
-        }
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const V *fin = A;
-    V *fout = B;
-    int64_t fused_lines = M0;
-    int fused_logL = p->logM[1];
-    int fused_nin = (int)N1;
-    int64_t in_fs = M0 * N1;
-    if (D == 3) {
-        // ---- y-pass: T1[u][z][y] (lines (u,z), contiguous y) -> T2[v][u][z]
-        const int64_t n_lines = M0 * N2;
-        if ((e = fwd_T_launch<T>(A, B, p->logM[1], (int)N1, n_lines, nfield, M0 * N2 * N1, M1 * n_lines,
-                                 reinterpret_cast<const V *>(p->tw[1]), st, p)) != cudaSuccess)
-            return e;
-        fin = B;
-        fout = A;
-        fused_lines = M1 * M0;
-        fused_logL = p->logM[2];
-        fused_nin = (int)N2;
-        in_fs = M1 * M0 * N2;
-    }
-    // ---- fused: forward along the last axis, multiply, inverse
-    {
-        const int logL = fused_logL;
-        const int TPL = (1 << logL) >> 4;
-        int R = 1;
-        while (R * 2 * TPL <= 256) R *= 2;
-        if (p->tune_RF > 0) {
-            R = p->tune_RF;
-            while (R > 1 && R * TPL > 512) R >>= 1;
-        }
-        // the two-CTAs-per-SM variant needs <= 256 threads
-        const bool fv = p->tune_FV == 1 && R * TPL <= 256;
-        LineCfg c = line_cfg(logL, R);
-        const size_t smem = line_smem(R, c.L, (int)sizeof(V));
-        FusedParams F = make_fused_params(p, dense_in != nullptr);
-        if (dense_in) F.nfield = 1;
-        const int64_t n_out = (D == 2) ? N1 : N2;
-        const int64_t out_fs = fused_lines * n_out;
-        const int64_t grid = (fused_lines + R - 1) / R;
-        const V *twl = reinterpret_cast<const V *>(p->tw[D - 1]);
-        prof_begin(p, "fused", st);
-        // paired-column variant: the built-in choice for 2D float plans that fit
-        const size_t smem2p = (!dense_in && sizeof(T) == 4) ? fused2p_smem(p) : 0;
-        if (smem2p && (p->tune_FV == 0 || p->tune_FV == 3)) {
-#define SDF_F2P(LG)                                                                                        \
-    do {                                                                                                   \
-        if ((e = set_smem<T>((const void *)k_fused2p<T, LG>, smem2p)) != cudaSuccess) return e;            \
-        k_fused2p<T, LG><<<(unsigned)(M0 / 2 + 1), 2 * TPL, smem2p, st>>>(                                 \
-            fin, fout, logL, fused_nin, (int)n_out, in_fs, out_fs, F, (int)p->kernels.size(), twl);        \
-    } while (0)
-            if constexpr (sizeof(T) == 4) {
-                if (logL == 12) SDF_F2P(12);
-                else SDF_F2P(0);
-            } else {
-                SDF_F2P(0);
-            }
-#undef SDF_F2P
-            prof_end(p, st);
-            return cudaGetLastError();
-        }
-#define SDF_FUSED(DD, FVV)                                                                                 \
-    do {                                                                                                   \
-        if ((e = set_smem<T>((const void *)k_fused<T, DD, FVV>, smem)) != cudaSuccess) return e;          \
-        k_fused<T, DD, FVV><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, fused_nin, (int)n_out, R, \
-                                                                  fused_lines, in_fs, out_fs, F, twl);     \
-    } while (0)
-        if (D == 2) {
-            if (fv) SDF_FUSED(2, 1);
-            else SDF_FUSED(2, 0);
-        } else {
-            if (fv) SDF_FUSED(3, 1);
-            else SDF_FUSED(3, 0);
-        }
-#undef SDF_FUSED
-        prof_end(p, st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-cudaError_t launch_forward(sdf_plan_impl *p, bool with_weights, const void *dense_in, int /*dense_mode*/,
-                           const uint8_t *flags_in) {
-    if (p->prec == SDF_FP64) return forward_impl<double>(p, with_weights, dense_in, flags_in);
-    return forward_impl<float>(p, with_weights, dense_in, flags_in);
-}
-
-// Inverse passes after the fused pass; the result of the fused pass is in
-// bufB (2D) or bufA (3D).  For 3D the inverse y-pass goes bufA -> bufB.
-template <typename T>
-static cudaError_t inverse_mid(sdf_plan_impl *p, int ngroup, const cx<T> **last_in) {
-    using V = cx<T>;
-    const int D = p->D;
-    if (D == 2) {
-        *last_in = reinterpret_cast<const V *>(p->bufB);
-        return cudaSuccess;
-    }
-    const int64_t N1 = p->N[1], N2 = p->N[2], M0 = p->M[0], M1 = p->M[1];
-    const int logL = p->logM[1];
-    const int R = tuned_R<T>(p, logL);
-    LineCfg c = line_cfg(logL, R);
-    const size_t smem = line_smem(R, c.L, (int)sizeof(V));
-    cudaError_t e;
-    const int64_t n_lines = M0 * N2;  // lines (u, z')
-    const int64_t grid = (n_lines + R - 1) / R;
-    prof_begin(p, "inv_y", p->stream);
-    SDF_LAUNCH_MT(k_inv_T, T, R * c.TPL, grid, smem, p->stream, reinterpret_cast<const V *>(p->bufA),
-                  reinterpret_cast<V *>(p->bufB), logL, (int)N1, R, n_lines, ngroup, M1 * n_lines, n_lines * N1,
-                  reinterpret_cast<const V *>(p->tw[1]));
-    prof_end(p, p->stream);
-    *last_in = reinterpret_cast<const V *>(p->bufB);
-    return cudaGetLastError();
-}
-
-template <typename T>
-static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, void *S, void *dS, void *d2S,
-                                         int8_t *sign, uint8_t *flags) {
-    using V = cx<T>;
-    const int D = p->D;
-    // groups actually computed: the sign group only with weights
-    int ng = p->ngroup;
-    if (!with_weights) {
-        while (ng > 0 && p->gch[ng - 1][0] == CH_MU) --ng;
-    }
-    const V *lin = nullptr;
-    cudaError_t e = inverse_mid<T>(p, ng, &lin);
-    if (e != cudaSuccess) return e;
-    EpiParams E;
-    memset(&E, 0, sizeof(E));
-    E.ngroup = ng;
-    int k = 0;
-    for (int g = 0; g < ng; ++g)
-        if (p->gch[g][0] == CH_MU) E.order[k++] = g;
-    for (int g = 0; g < ng; ++g)
-        if (p->gch[g][0] != CH_MU) E.order[k++] = g;
-    for (int g = 0; g < ng; ++g) {
-        E.gch[g][0] = p->gch[g][0];
-        E.gch[g][1] = p->gch[g][1];
-    }
-    const int64_t N0 = p->N[0], N1 = p->N[1], N2 = p->N[2], M0 = p->M[0];
-    const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
-    E.in_fs = M0 * n_lines;
-    E.S = S;
-    E.dS = dS;
-    E.d2S = d2S;
-    E.sign = with_weights ? sign : nullptr;
-    E.flags = flags;
-    E.tile_flag = p->tile_flag;
-    E.dsc = p->dsc;
-    E.tau = p->tau;
-    {
-        const double n = (double)p->M[0] * (double)p->M[1] * (D == 3 ? (double)p->M[2] : 1.0);
-        const double base = sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
-        E.coef64 = p->noise_c64 * ldexp(1.0, -53) * base;
-        E.coef32 = p->noise_c32 * ldexp(1.0, -24) * base;
-    }
-    E.nnodes = p->nnodes;
-    E.N0 = (int)N0;
-    E.N1 = (int)N1;
-    E.nb0 = (int)p->nb[0];
-    E.nb1 = (int)p->nb[1];
-    E.D = D;
-    E.fixup = (p->prec == SDF_FP32) ? 1 : 0;
-    E.hs_inv = 1.0 / hessian_scale(p);
-    E.tau_f = (float)p->tau;
-    E.itau_f = (float)(1.0 / p->tau);
-    E.hs_inv_f = (float)E.hs_inv;
-    const int logL = p->logM[0];
-    const int R = tuned_R<T>(p, logL);
-    LineCfg c = line_cfg(logL, R);
-    const size_t smem = line_smem(R, c.L, (int)sizeof(V));
-    const int64_t grid = (n_lines + R - 1) / R;
-    const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
-#define SDF_EPI(DD, LG)                                                                                       \
-    do {                                                                                                      \
-        if ((e = set_smem<T>((const void *)k_epilogue<T, DD, 512, LG>, smem)) != cudaSuccess) return e;      \
-        k_epilogue<T, DD, 512, LG><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0); \
-    } while (0)
-    prof_begin(p, "epilogue", p->stream);
-    if constexpr (sizeof(T) == 4) {
-        if (D == 2 && logL == 12) SDF_EPI(2, 12);
-        else if (D == 2) SDF_EPI(2, 0);
-        else SDF_EPI(3, 0);
-    } else {
-        if (D == 2) SDF_EPI(2, 0);
-        else SDF_EPI(3, 0);
-    }
-#undef SDF_EPI
-    prof_end(p, p->stream);
-    (void)N2;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_inverse_epilogue(sdf_plan_impl *p, bool with_weights, void *S, void *dS, void *d2S, int8_t *sign,
-                                    uint8_t *flags) {
-    if (p->prec == SDF_FP64) return inverse_epilogue_impl<double>(p, with_weights, S, dS, d2S, sign, flags);
-    return inverse_epilogue_impl<float>(p, with_weights, S, dS, d2S, sign, flags);
-}
-
-// ---------------------------------------------------------------- adjoint epilogue
-// Last inverse pass of the adjoint: the real / imaginary part of each group
-// goes to dense plane plane[g][0|1] (-1: dropped), node order x fastest.
-struct DenseParams {
-    int ngroup;
-    int plane[2][2];
-    int64_t in_fs, nnodes;
-    int N0;
-};
-
-template <typename T>
-__global__ void SDF_LB(T) k_epi_dense(const cx<T> *__restrict__ in, int logL, int R, int64_t n_lines, DenseParams P,
-                                      T *planes, const cx<T> *__restrict__ tw) {
-    using V = cx<T>;
-    extern __shared__ unsigned char smraw[];
-    V *sm = reinterpret_cast<V *>(smraw);
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
-    const int tid = threadIdx.x, lr = tid % R, t = tid / R;
-    const int64_t line = (int64_t)blockIdx.x * R + lr;
-    const bool valid = line < n_lines;
-    V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
-    const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
-    for (int g = 0; g < P.ngroup; ++g) {
-        V v[16];
-        const V *src = in + g * P.in_fs + line;
-#pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
-        __syncthreads();
-        fft_line<true>(v, my, t, logL, tws);
-        if (!valid) continue;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int x = t + m * TPL;
-            if (x >= P.N0) continue;
-            const int64_t node = line * P.N0 + x;
-            if (P.plane[g][0] >= 0) planes[P.plane[g][0] * P.nnodes + node] = v[m].x;
-            if (P.plane[g][1] >= 0) planes[P.plane[g][1] * P.nnodes + node] = v[m].y;
-        }
-    }
-}
-
-// Transform a = w/phi (dense x-pass, [y-pass], fused pass with the adjoint
-// programme, [inverse y-pass]) and write the D+1 convolution planes
-// (a * k_x, a * k_y[, a * k_z], a * (|X| f)) to p->adj_planes.
-template <typename T>
-static cudaError_t adjoint_transforms_impl(sdf_plan_impl *p, const void *w, const void *S_saved,
-                                           const uint8_t *flags) {
-    using V = cx<T>;
-    const void *pair[2] = {w, S_saved};
-    cudaError_t e = forward_impl<T>(p, false, pair, flags);
-    if (e != cudaSuccess) return e;
-    const V *lin = nullptr;
-    if ((e = inverse_mid<T>(p, p->adj_ngroup, &lin)) != cudaSuccess) return e;
-    const int D = p->D;
-    const int64_t N1 = p->N[1], N2 = p->N[2], M0 = p->M[0];
-    const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
-    DenseParams P;
-    memset(&P, 0, sizeof(P));
-    P.ngroup = p->adj_ngroup;
-    for (int g = 0; g < p->adj_ngroup; ++g)
-        for (int hh = 0; hh < 2; ++hh) {
-            const int ch = p->adj_gch[g][hh];
-            P.plane[g][hh] = ch == CH_AGX ? 0 : ch == CH_AGY ? 1 : ch == CH_AGZ ? 2 : ch == CH_ARF ? D : -1;
-        }
-    P.in_fs = M0 * n_lines;
-    P.nnodes = p->nnodes;
-    P.N0 = (int)p->N[0];
-    const int logL = p->logM[0];
-    const int R = pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget);
-    LineCfg c = line_cfg(logL, R);
-    const size_t smem = line_smem(R, c.L, (int)sizeof(V));
-    if ((e = set_smem<T>((const void *)k_epi_dense<T>, smem)) != cudaSuccess) return e;
-    prof_begin(p, "epi_dense", p->stream);
-    k_epi_dense<T><<<(unsigned)((n_lines + R - 1) / R), R * c.TPL, smem, p->stream>>>(
-        lin, logL, R, n_lines, P, reinterpret_cast<T *>(p->adj_planes), reinterpret_cast<const V *>(p->tw[0]));
-    prof_end(p, p->stream);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adjoint_transforms(sdf_plan_impl *p, const void *w, const void *S_saved, const uint8_t *flags) {
-    if (p->prec == SDF_FP64) return adjoint_transforms_impl<double>(p, w, S_saved, flags);
-    return adjoint_transforms_impl<float>(p, w, S_saved, flags);
-}
+cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL, int n_in, int64_t n_lines,
+                       int64_t in_fs, bool dense);
 
 }  // namespace sdf
