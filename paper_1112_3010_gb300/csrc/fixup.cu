@@ -14,7 +14,10 @@
 // tile; after ring k every unvisited occupied node lies at least
 // lb = (8k+1)h from every node of the tile, so a node stops summing once
 // K exp(-(lb - m)/tau) is below 1e-5 of its sum, or once even its sum plus
-// K exp(-lb/tau) is below theta_64 (it stays capped).  The log-sum-exp shift
+// K exp(-lb/tau) is below theta_64 (it stays capped).  Rings go in batches
+// that end at the first ring where some node could meet one of these tests
+// (a bound from its sums so far), so there are few batches per tile and no
+// node sums past its own stopping ring.  The log-sum-exp shift
 // m is the nearest point found by a cheap pass over the first batch of points
 // (and over a later batch only if it could hold a point so much nearer that a
 // term would exceed 2^60), so the summing loop itself has no branch.  A
@@ -22,6 +25,7 @@
 // keeps the capped value.  Visiting order is fixed, so the sums are
 // deterministic.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -200,11 +204,17 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
                         : ((k == 0) ? 1 : (2 * k + 1) * (2 * k + 1) * (2 * k + 1) - (2 * k - 1) * (2 * k - 1) * (2 * k - 1));
     };
     const int kmax = max(max(P.nb0, P.nb1), (D == 3) ? P.nb2 : 0);
-    // rings are visited in batches {0,1,2}, {3,4}, then one at a time: most
-    // tiles finish in the first batch, one staging round
-    for (int k0 = 0; k0 <= kmax;) {
+    // Rings are visited in batches: {0,1,2}, then up to the first ring at
+    // whose end some active node could stop or be capped (a lower bound
+    // worked out from its sums after the previous batch, s_kev), so no node
+    // sums past its own stopping point and the batches stay few.
+    __shared__ int s_kev[2];
+    if (tid == 0) s_kev[0] = s_kev[1] = INT_MAX;
+    int round = 0;
+    for (int k0 = 0; k0 <= kmax; ++round) {
         if (!__syncthreads_or(active[0] || active[1])) break;
-        const int k1 = min(kmax, (k0 == 0) ? 2 : (k0 == 3 ? 4 : k0));
+        const int k1 = (k0 == 0) ? min(kmax, 2) : min(kmax, max(k0, s_kev[round & 1]));
+        if (tid == 0) s_kev[(round + 1) & 1] = INT_MAX;  // this batch's checks go here
         // every node of ring k0 or beyond lies at least 8(k0-1)+1 from the tile
         const float lb_in = (k0 == 0) ? 0.f : 8.f * (k0 - 1) + 1.f;
         int nring = 0;
@@ -352,29 +362,37 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
             __syncthreads();
             i0 += max(taken, 1);
         }
-        // after ring k1 every unvisited node lies at least lb from this tile
+        // after ring k1 every unvisited node lies at least lb from this tile,
+        // so phi = e^{-m/tau} sE + (rest), rest <= K e^{-lb/tau}; in logs:
+        // A = log(e^{-m/tau} sE), tailA = log(K e^{-lb/tau})
         const float lb = (8.f * k1 + 1.f) * h;
-        const float tailA = -lb * itau + lnK;  // log of K exp(-lb/tau)
+        const float tailA = -lb * itau + lnK;
+        int kev = INT_MAX;
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             if (!active[j]) continue;
-            if (mg[j] < INFINITY) {
-                const float m = mg[j] * h;
-                const float lsE = logf(sE[j]);
-                // the rest adds less than 1e-5 of the sum: final
-                if ((lb - m) * itau >= lnK - lsE + 11.512925f) active[j] = false;
-                // phi < theta_64 whatever the rest adds: capped
-                const float A = -m * itau + lsE;
-                const float hi = fmaxf(A, tailA), lo = fminf(A, tailA);
-                if (hi + log1pf(expf(lo - hi)) < lt - 1e-4f) {
-                    active[j] = false;
-                    early_cap[j] = true;
-                }
-            } else if (tailA < lt - 1e-4f) {
+            const float A = (mg[j] < INFINITY) ? -mg[j] * h * itau + __logf(sE[j]) : -INFINITY;
+            // the rest adds less than 1e-5 of the sum: final
+            if (tailA <= A - 11.512925f) {
+                active[j] = false;
+                continue;
+            }
+            // phi < theta_64 whatever the rest adds: capped
+            const float hi = fmaxf(A, tailA), lo = fminf(A, tailA);
+            const float lphi = hi + __logf(1.f + __expf(lo - hi));  // log of the bound on phi
+            if (lphi < lt - 1e-4f) {
                 active[j] = false;
                 early_cap[j] = true;
+                continue;
             }
+            // the earliest ring end at which this node could stop (the sum
+            // can only grow to e^{lphi}) or be capped (needs tailA < lt)
+            float L = tau * (lnK + 11.512925f - lphi);
+            if (A < lt - 1e-4f) L = fminf(L, tau * (lnK - lt + 1e-4f));
+            const float kf = ceilf((L / h - 1.f) * 0.125f);
+            kev = min(kev, (kf < (float)kmax) ? (int)kf : kmax);
         }
+        if (kev < INT_MAX) atomicMin(&s_kev[(round + 1) & 1], kev);
         k0 = k1 + 1;
     }
     int fixed = 0, capped = 0;
