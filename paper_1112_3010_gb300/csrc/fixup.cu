@@ -11,10 +11,12 @@
 // One CTA per flagged tile (2x2 bins of 8x8 nodes in 2D, one 8^3 bin in 3D),
 // two nodes per thread so that each staged point feeds two sums.  Candidate
 // bins are visited in rings of Chebyshev distance k = 0, 1, 2, ... around the
-// tile; after ring k every unvisited occupied node lies at least
-// lb = (8k+1)h from every node of the tile, so a node stops summing once
-// K exp(-(lb - m)/tau) is below 1e-5 of its sum, or once even its sum plus
-// K exp(-lb/tau) is below theta_64 (it stays capped).  Rings go in batches
+// tile; every occupied node of ring k' lies at least (8(k'-1)+1)h from every
+// node of the tile, so after ring k the unvisited points add at most
+// T = sum_{k'>k} n_k' exp(-(8(k'-1)+1)h/tau), with the ring counts n_k' read
+// from the bins' prefix sums for a few rings ahead (the rest all at the next
+// distance).  A node stops summing once T is below 1e-5 of its sum, or once
+// even its sum plus T is below theta_64 (it stays capped).  Rings go in batches
 // that end at the first ring where some node could meet one of these tests
 // (a bound from its sums so far), so there are few batches per tile and no
 // node sums past its own stopping ring.  The log-sum-exp shift
@@ -35,6 +37,7 @@ namespace sdf {
 
 struct FixParams {
     const int *bin_start, *bin_nuniq, *ucell, *ucount;
+    const int *sat;  // summed-area table of the points per bin
     const unsigned char *cheb, *tile_flag;
     const DevScalars *dsc;
     DevScalars *dsc_w;
@@ -175,7 +178,6 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
     // distances are kept in grid units (node spacing 1); exp(-(r - m)/tau) =
     // 2^((m - r) * l2e_th) with l2e_th = h log2(e)/tau
     const float l2e_th = P.l2e_th;
-    const float lnK = P.logK;
     // node and cell coordinates are integers below 2^13, so the squared
     // distances that matter (below 2^24) are exact in float
     const float xf = (float)x, yf = (float)y, zf = (float)z;
@@ -209,12 +211,32 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
     // worked out from its sums after the previous batch, s_kev), so no node
     // sums past its own stopping point and the batches stay few.
     __shared__ int s_kev[2];
+    // points in the box of rings <= k1 + j (j <= kLook) and the log of the
+    // bound on what lies beyond ring k1 + i (i < kLook): ring k' holds
+    // n_k' points, all at least 8(k'-1)+1 nodes away
+    constexpr int kLook = 8;
+    __shared__ int s_cnt[kLook + 1];
+    __shared__ float s_logT[kLook];
+    const int ktot = P.bin_start[(int64_t)P.nb0 * P.nb1 * ((D == 3) ? P.nb2 : 1)];  // points binned
+    // points in the box of rings <= k around the tile, from the table
+    auto box_count = [&](int k) {
+        const int x0 = max(bx - k, 0) - 1, x1 = min(bx + TB - 1 + k, P.nb0 - 1);
+        const int y0 = max(by - k, 0) - 1, y1 = min(by + TB - 1 + k, P.nb1 - 1);
+        const int z0 = (D == 3) ? max(bz - k, 0) - 1 : -1, z1 = (D == 3) ? min(bz + k, P.nb2 - 1) : 0;
+        auto at = [&](int x, int y, int z) -> int {
+            return (x < 0 || y < 0 || z < 0) ? 0 : P.sat[x + (int64_t)P.nb0 * (y + (int64_t)P.nb1 * z)];
+        };
+        int n = at(x1, y1, z1) - at(x0, y1, z1) - at(x1, y0, z1) + at(x0, y0, z1);
+        if (D == 3) n -= at(x1, y1, z0) - at(x0, y1, z0) - at(x1, y0, z0) + at(x0, y0, z0);
+        return n;
+    };
     if (tid == 0) s_kev[0] = s_kev[1] = INT_MAX;
     int round = 0;
     for (int k0 = 0; k0 <= kmax; ++round) {
         if (!__syncthreads_or(active[0] || active[1])) break;
         const int k1 = (k0 == 0) ? min(kmax, 2) : min(kmax, max(k0, s_kev[round & 1]));
         if (tid == 0) s_kev[(round + 1) & 1] = INT_MAX;  // this batch's checks go here
+        if (tid <= kLook) s_cnt[tid] = box_count(min(k1 + tid, kmax));
         // every node of ring k0 or beyond lies at least 8(k0-1)+1 from the tile
         const float lb_in = (k0 == 0) ? 0.f : 8.f * (k0 - 1) + 1.f;
         int nring = 0;
@@ -362,35 +384,51 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
             __syncthreads();
             i0 += max(taken, 1);
         }
-        // after ring k1 every unvisited node lies at least lb from this tile,
-        // so phi = e^{-m/tau} sE + (rest), rest <= K e^{-lb/tau}; in logs:
-        // A = log(e^{-m/tau} sE), tailA = log(K e^{-lb/tau})
-        const float lb = (8.f * k1 + 1.f) * h;
-        const float tailA = -lb * itau + lnK;
+        if (tid < kLook) {
+            // log T_i, T_i = sum_{k'=k1+i+1}^{k1+kLook} n_k' e^{-lb(k'-1)/tau}
+            //                + (points beyond ring k1+kLook) e^{-lb(k1+kLook)/tau},
+            // summed relative to e^{-lb(k1)/tau} (every factor <= 1)
+            const float q = __expf(-8.f * h * itau);  // one ring further out
+            float w = 1.f, acc = 0.f;
+            for (int i = 0; i < kLook; ++i) {
+                if (i >= tid) acc += (float)(s_cnt[i + 1] - s_cnt[i]) * w;
+                w *= q;
+            }
+            acc += (float)(ktot - s_cnt[kLook]) * w;
+            s_logT[tid] = __logf(acc) - (8.f * k1 + 1.f) * h * itau;
+        }
+        __syncthreads();
+        // phi = e^{-m/tau} sE + (rest), rest <= T_0; in logs A = log(e^{-m/tau} sE)
+        const float tail0 = s_logT[0];
         int kev = INT_MAX;
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             if (!active[j]) continue;
             const float A = (mg[j] < INFINITY) ? -mg[j] * h * itau + __logf(sE[j]) : -INFINITY;
             // the rest adds less than 1e-5 of the sum: final
-            if (tailA <= A - 11.512925f) {
+            if (tail0 <= A - 11.512925f) {
                 active[j] = false;
                 continue;
             }
             // phi < theta_64 whatever the rest adds: capped
-            const float hi = fmaxf(A, tailA), lo = fminf(A, tailA);
+            const float hi = fmaxf(A, tail0), lo = fminf(A, tail0);
             const float lphi = hi + __logf(1.f + __expf(lo - hi));  // log of the bound on phi
             if (lphi < lt - 1e-4f) {
                 active[j] = false;
                 early_cap[j] = true;
                 continue;
             }
-            // the earliest ring end at which this node could stop (the sum
-            // can only grow to e^{lphi}) or be capped (needs tailA < lt)
-            float L = tau * (lnK + 11.512925f - lphi);
-            if (A < lt - 1e-4f) L = fminf(L, tau * (lnK - lt + 1e-4f));
-            const float kf = ceilf((L / h - 1.f) * 0.125f);
-            kev = min(kev, (kf < (float)kmax) ? (int)kf : kmax);
+            // the first later ring end (within the look-ahead) at which this
+            // node could stop (its sum can only grow to e^{lphi}) or be capped
+            int ev = kLook;
+            for (int i = 1; i < kLook; ++i) {
+                const float Ti = s_logT[i];
+                if (Ti <= lphi - 11.512925f || (A < lt - 1e-4f && Ti < lt - 1e-4f)) {
+                    ev = i;
+                    break;
+                }
+            }
+            kev = min(kev, min(k1 + ev, kmax));
         }
         if (kev < INT_MAX) atomicMin(&s_kev[(round + 1) & 1], kev);
         k0 = k1 + 1;
@@ -456,6 +494,7 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS
                          uint8_t *flags) {
     FixParams F;
     F.bin_start = p->bin_start;
+    F.sat = p->bin_count;  // launch_cheb wrote the table there
     F.bin_nuniq = p->bin_nuniq;
     F.ucell = p->ucell;
     F.ucount = p->ucount;

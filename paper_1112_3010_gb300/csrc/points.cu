@@ -335,6 +335,62 @@ cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, con
     return cudaGetLastError();
 }
 
+// Summed-area table of the points per bin, written over bin_count (free once
+// bin_start, its prefix sum in bin order, exists): sat[b] = points in the
+// bins (x' <= x, y' <= y, z' <= z).  One CTA per line scans along y (the
+// values are row prefix counts from bin_start), then in 3D along z.
+template <int PASS>
+__global__ void __launch_bounds__(1024) k_sat_axis(const int *__restrict__ bin_start, int *__restrict__ sat, int nb0,
+                                                   int nb1, int nb2) {
+    __shared__ int wsum[32];
+    const int64_t line = blockIdx.x;  // PASS 0: x + nb0 z; PASS 1: x + nb0 y
+    const int x = (int)(line % nb0);
+    const int64_t slab = (int64_t)nb0 * nb1;
+    const int n = (PASS == 0) ? nb1 : nb2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int carry = 0;
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        int64_t at = 0;
+        int v = 0;
+        if (i < n) {
+            if (PASS == 0) {
+                const int64_t row = (int64_t)nb0 * i + slab * (line / nb0);
+                at = row + x;
+                v = bin_start[row + x + 1] - bin_start[row];
+            } else {
+                at = line + slab * i;
+                v = sat[at];
+            }
+        }
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int w = (lane < nw) ? wsum[lane] : 0;
+            int s = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += u;
+            }
+            wsum[lane] = s - w;  // exclusive warp offsets
+        }
+        __syncthreads();
+        const int out = carry + wsum[wid] + incl;
+        if (i < n) sat[at] = out;
+        // the chunk's total: the last thread's inclusive value
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) wsum[0] = out;
+        __syncthreads();
+        carry = wsum[0];
+        __syncthreads();
+    }
+}
+
 cudaError_t launch_cheb(sdf_plan_impl *p) {
     cudaStream_t st = p->stream;
     const int64_t nb0 = p->nb[0], nb1 = p->nb[1], nb2 = p->nb[2];
@@ -351,6 +407,11 @@ cudaError_t launch_cheb(sdf_plan_impl *p) {
         cudaError_t e = cudaMemcpyAsync(p->cheb, tmp, p->nbins, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
     }
+    const int nz = (p->D == 3) ? (int)nb2 : 1;
+    auto threads = [](int64_t n) { return (unsigned)(n >= 1024 ? 1024 : ((n + 31) / 32) * 32); };
+    k_sat_axis<0><<<(unsigned)(nb0 * nz), threads(nb1), 0, st>>>(p->bin_start, p->bin_count, (int)nb0, (int)nb1, nz);
+    if (p->D == 3)
+        k_sat_axis<1><<<(unsigned)(nb0 * nb1), threads(nz), 0, st>>>(p->bin_start, p->bin_count, (int)nb0, (int)nb1, nz);
     prof_end(p, st);
     return cudaGetLastError();
 }
