@@ -161,6 +161,39 @@ def algorithmic_bytes(plan_info, name, stats, n_field, n_group, n_kern):
     return None
 
 
+# FP32 FMA-pipe operations per node-point term of the fix-up's summing loop
+# (2D, S + grad S + Hessian in moment form): r^2, r, the exponent, E, E/r,
+# the Hessian factor (3), five running sums (sE, sA, 2 gradient), the three
+# Hessian moments with their two products, and the per-point offsets shared
+# by the thread's two nodes.
+FIXUP_FMA_OPS = 19
+
+
+def fixup_peak_gterms():
+    """FP32-pipe bound on the fix-up's node-point terms per second (GB300)."""
+    sms, lanes, ghz = 152, 128, 2.07
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        ghz = float(json.load(open(p)).get("sm_max_mhz", 2070.0)) / 1000.0
+    return sms * lanes * ghz / FIXUP_FMA_OPS
+
+
+def measured_traffic(kernel, n_launch_terms=None):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, when
+    it was taken on the source that is built now (else None)."""
+    import hashlib
+    f = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(f):
+        return None
+    d = json.load(open(f)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_1112_3010_gb300", "csrc", d["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != d["sha256"]:
+        return None
+    return d["bytes_per_launch"]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -258,23 +291,38 @@ def main():
         p.profile(False)
     stats = [p.stats() for p in plans]
 
-    # roofline of the dominant kernel
-    peak, peak_kind = load_peaks()
+    # roofline of the dominant kernel, and of each FFT pass against HBM
+    hbm_peak, peak_kind = load_peaks()
     info = plans[0].info
     n_field, n_group, n_kern = 2, 4, info.n_kernels
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    passes = {}
+    for name in ("xpass", "fused", "epilogue"):
+        if name in prof:
+            n, t = prof[name]
+            b = algorithmic_bytes(info, name, None, n_field, n_group, n_kern)
+            gbs = b / (t / n * 1e-3) / 1e9
+            passes[name] = {"bytes_per_launch": b, "avg_ms": t / n, "achieved_GBs": gbs,
+                            "frac_of_" + peak_kind + "_hbm": gbs / hbm_peak}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
     roof = None
-    if dom:
-        name, (n, t) = dom
-        bytes_ = algorithmic_bytes(info, name, None, n_field, n_group, n_kern)
-        if bytes_ is not None:
-            ach = bytes_ / (t / n * 1e-3) / 1e9
-            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
-                    "avg_launch_ms": t / n}
-        else:
-            roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None,
-                    "frac": None, "traffic": None, "avg_launch_ms": t / n}
+    if dom == "fixup":
+        # node-point terms per second against the FP32 pipe: every term costs
+        # FIXUP_FMA_OPS issue slots of the 128-lane FMA pipe (and 2 MUFU ops,
+        # 16 lanes per SM, which bind later)
+        n, t = prof["fixup"]
+        terms = sum(st.n_fixup_terms for st in stats)  # all plans, one execute each
+        ach = terms / (t / n * len(plans) * 1e-3) / 1e9
+        peak = fixup_peak_gterms()
+        roof = {"kernel": "fixup", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gterm/s",
+                "frac": ach / peak, "traffic": measured_traffic("fixup", n_launch_terms=terms / len(plans)),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / %d FMA-pipe ops per term"
+                               % FIXUP_FMA_OPS,
+                "avg_launch_ms": t / n}
+    elif dom in passes:
+        pz = passes[dom]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": pz["achieved_GBs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": pz["achieved_GBs"] / hbm_peak, "traffic": measured_traffic(dom),
+                "peak_source": peak_kind, "avg_launch_ms": pz["avg_ms"]}
     per_kernel = {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0]),
                       "share": v[1] / max(1e-9, sum(x[1] for x in prof.values()))} for k, v in prof.items()}
 
@@ -366,7 +414,7 @@ def main():
                        "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
                        "tile_schedule": [{"lines_T": a, "lines_F": b, "fused_variant": c} for a, b, c in tuning]},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
-            "kernels": per_kernel, "fp64_path": fp64,
+            "kernels": per_kernel, "fft_passes": passes, "fp64_path": fp64,
             "fixup": [{"tau": s.tau, "tiles": st.n_fixup_tiles, "nodes": st.n_fixup_nodes,
                        "capped_in_fixup": st.n_capped, "terms": st.n_fixup_terms, "theta32": st.theta32,
                        "theta64": st.theta64,

@@ -48,6 +48,7 @@ struct FixParams {
     int nb0, nb1, nb2;
     int64_t nnodes;
     double coef64;
+    float log_coef64;
     float h, tau, l2e_th, logK;  // spacing, tau, h log2(e)/tau, log K
     int fp64_out;
 };
@@ -149,10 +150,10 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
         c = min(c, (int)P.cheb[q]);
     }
     if (!flagged) return;
-    // log theta_64, worked out in double by one thread (the FP64 pipe is
-    // slow) and read by the CTA from shared memory
+    // log theta_64 = log(coef64) + log(sum c^2)/2, a threshold: float is
+    // enough (the FP64 pipe is slow); one thread, read from shared memory
     __shared__ float s_lt;
-    if (tid == 0) s_lt = (float)log(P.coef64 * sqrt((double)P.dsc->sum_c2));
+    if (tid == 0) s_lt = P.log_coef64 + 0.5f * logf((float)P.dsc->sum_c2);
     __syncthreads();
     const float lt = s_lt;
     const float dlo = (c >= 1) ? (8.f * (c - 1) + 1.f) * P.h : 0.f;
@@ -521,6 +522,7 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS
     const double n = (double)p->M[0] * (double)p->M[1] * (D == 3 ? (double)p->M[2] : 1.0);
     F.coef64 = p->noise_c64 * ldexp(1.0, -53) * sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
     F.logK = (float)log((double)p->last_K);
+    F.log_coef64 = (float)log(F.coef64);
     F.fp64_out = 0;
     prof_begin(p, "fixup", p->stream);
     if (D == 2) {

@@ -561,10 +561,18 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     // FP64 pipe is slow), the CTA reads them from shared memory
     __shared__ T s_thr[2];
     if (threadIdx.x == 0) {
-        const double gn = sqrt((double)P.dsc->sum_c2);
-        const double theta64 = P.coef64 * gn;
-        s_thr[0] = T(P.fixup ? P.coef32 * gn : theta64);
-        s_thr[1] = T(-P.tau * log(theta64));
+        if constexpr (sizeof(T) == 4) {
+            // thresholds: float is enough
+            const float gn = sqrtf((float)P.dsc->sum_c2);
+            const float theta64 = (float)P.coef64 * gn;
+            s_thr[0] = P.fixup ? (float)P.coef32 * gn : theta64;
+            s_thr[1] = -P.tau_f * logf(theta64);
+        } else {
+            const double gn = sqrt((double)P.dsc->sum_c2);
+            const double theta64 = P.coef64 * gn;
+            s_thr[0] = T(P.fixup ? P.coef32 * gn : theta64);
+            s_thr[1] = T(-P.tau * log(theta64));
+        }
     }
     __syncthreads();
     const T theta = s_thr[0], scap = s_thr[1];
