@@ -26,11 +26,11 @@ __global__ void k_snap(int D, int64_t K, const double *__restrict__ P, const dou
                        int N0, int N1, int N2, int nb0, int nb1, int *pt_bin, int *pt_lc, int *bin_count,
                        DevScalars *dsc) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
+    const bool live = k < K;
     int j[3] = {0, 0, 0};
     const int Nn[3] = {N0, N1, N2};
-    bool ok = true;
-    for (int a = 0; a < D; ++a) {
+    bool ok = live;
+    for (int a = 0; live && a < D; ++a) {
         const double y = P[k * D + a];
         // nearest node, ties up: floor(y/h + 0.5)
         const double q = floor(y / h + 0.5);
@@ -40,20 +40,28 @@ __global__ void k_snap(int D, int64_t K, const double *__restrict__ P, const dou
             j[a] = (int)q;
         }
     }
-    if (!ok) {
+    if (live && !ok) {
         pt_lc[k] = -1;
         set_status(dsc, SDF_ERR_POINT_OUT_OF_GRID);
-        return;
     }
-    const int b = (j[0] >> 3) + nb0 * ((j[1] >> 3) + nb1 * (j[2] >> 3));
-    const int lc = (j[0] & 7) | ((j[1] & 7) << 3) | ((j[2] & 7) << 6);
-    pt_bin[k] = b;
-    pt_lc[k] = lc;
-    atomicAdd(&bin_count[b], 1);
+    if (ok) {
+        const int b = (j[0] >> 3) + nb0 * ((j[1] >> 3) + nb1 * (j[2] >> 3));
+        const int lc = (j[0] & 7) | ((j[1] & 7) << 3) | ((j[2] & 7) << 6);
+        pt_bin[k] = b;
+        pt_lc[k] = lc;
+        atomicAdd(&bin_count[b], 1);
+    }
     if (W) {
+        // max |w| over the warp first: one atomic per warp, not per point
+        // (non-negative doubles order like their bit patterns)
         double m = 0.0;
-        for (int a = 0; a < D; ++a) m = fmax(m, fabs(W[k * D + a]));
-        if (isfinite(m) && m > 0.0) atomicMax(&dsc->wmax, (unsigned long long)__double_as_longlong(m));
+        for (int a = 0; ok && a < D; ++a) m = fmax(m, fabs(W[k * D + a]));
+        unsigned long long bits = (isfinite(m) && m > 0.0) ? (unsigned long long)__double_as_longlong(m) : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_xor_sync(0xffffffffu, bits, o);
+            bits = u > bits ? u : bits;
+        }
+        if ((threadIdx.x & 31) == 0 && bits) atomicMax(&dsc->wmax, bits);
     }
 }
 
@@ -162,6 +170,85 @@ __global__ void k_dedupe(int D, int64_t K, const double *__restrict__ W, const i
         const int total = wsum[wid] + incl;
         bin_nuniq[b] = total;
         atomicAdd(reinterpret_cast<unsigned long long *>(&dsc->n_unique), (unsigned long long)total);
+    }
+}
+
+// 2D: one warp per bin (64 cells), BPC bins per CTA -- most bins are empty,
+// and a CTA per bin would spend the pass launching CTAs.  Same results as
+// k_dedupe: per-node counts and fixed-point weight sums, occupied nodes in
+// node order.
+template <int BPC>
+__global__ void __launch_bounds__(32 * BPC) k_dedupe_w(int64_t K, int64_t nbins, const double *__restrict__ W,
+                                                      const int *__restrict__ bin_start,
+                                                      const long long *__restrict__ entry, int *bin_nuniq, int *ucell,
+                                                      int *ucount, double *uw, DevScalars *dsc) {
+    constexpr int NC = 64;
+    __shared__ int cnt[BPC][NC];
+    __shared__ long long wf[2][BPC][NC];
+    __shared__ double s_scale;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        // fixed-point scale: |w| * scale * K < 2^61
+        s_scale = 0.0;
+        if (W) {
+            const double wm = __longlong_as_double((long long)dsc->wmax);
+            if (wm > 0.0) s_scale = ldexp(1.0, 61 - (ilogb((double)K * wm) + 1));
+        }
+    }
+    __syncthreads();
+    const double scale = s_scale;
+    const int64_t b = (int64_t)blockIdx.x * BPC + w;
+    if (b >= nbins) return;
+    const int s = bin_start[b], e = bin_start[b + 1];
+    if (s == e) {
+        if (lane == 0) bin_nuniq[b] = 0;
+        return;
+    }
+    for (int c = lane; c < NC; c += 32) {
+        cnt[w][c] = 0;
+        wf[0][w][c] = wf[1][w][c] = 0;
+    }
+    __syncwarp();
+    for (int i = s + lane; i < e; i += 32) {
+        const long long en = entry[i];
+        const int lc = (int)(en >> 40);
+        const int64_t k = en & ((1LL << 40) - 1);
+        atomicAdd(&cnt[w][lc], 1);
+        if (W) {
+            for (int a = 0; a < 2; ++a) {
+                const long long q = llrint(W[k * 2 + a] * scale);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&wf[a][w][lc]), (unsigned long long)q);
+            }
+        }
+    }
+    __syncwarp();
+    // compaction in node order: lane owns cells 2 lane, 2 lane + 1
+    const int n0 = cnt[w][2 * lane], n1 = cnt[w][2 * lane + 1];
+    const int mine = (n0 > 0) + (n1 > 0);
+    unsigned long long c2 = (unsigned long long)n0 * n0 + (unsigned long long)n1 * n1;
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int pos = s + incl - mine;
+    const double inv = (scale > 0.0) ? 1.0 / scale : 0.0;
+    for (int q = 0; q < 2; ++q) {
+        const int c = 2 * lane + q;
+        const int n = q ? n1 : n0;
+        if (!n) continue;
+        ucell[pos] = c;
+        ucount[pos] = n;
+        uw[3 * (int64_t)pos + 0] = (double)wf[0][w][c] * inv;
+        uw[3 * (int64_t)pos + 1] = (double)wf[1][w][c] * inv;
+        uw[3 * (int64_t)pos + 2] = 0.0;
+        ++pos;
+    }
+    for (int o = 16; o > 0; o >>= 1) c2 += __shfl_down_sync(0xffffffffu, c2, o);
+    if (lane == 0) atomicAdd(&dsc->sum_c2, c2);
+    if (lane == 31) {
+        bin_nuniq[b] = incl;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&dsc->n_unique), (unsigned long long)incl);
     }
 }
 
@@ -326,8 +413,8 @@ cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, con
     prof_end(p, st);
     prof_begin(p, "dedupe", st);
     if (p->D == 2)
-        k_dedupe<64><<<(unsigned)p->nbins, 64, 0, st>>>(p->D, K, weights, p->bin_start, p->pt_entry, p->bin_nuniq,
-                                                       p->ucell, p->ucount, p->uw, p->dsc);
+        k_dedupe_w<8><<<(unsigned)((p->nbins + 7) / 8), 256, 0, st>>>(K, p->nbins, weights, p->bin_start, p->pt_entry,
+                                                                      p->bin_nuniq, p->ucell, p->ucount, p->uw, p->dsc);
     else
         k_dedupe<512><<<(unsigned)p->nbins, 128, 0, st>>>(p->D, K, weights, p->bin_start, p->pt_entry,
                                                          p->bin_nuniq, p->ucell, p->ucount, p->uw, p->dsc);
