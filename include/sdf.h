@@ -166,9 +166,12 @@ sdf_status sdf_execute(sdf_plan plan, int64_t K, const double *points,
 
 /*
  * sdf_execute_host -- sdf_execute with HOST buffers (same shapes and types):
- * copies points/weights to plan-owned device buffers, executes, copies the
- * requested outputs back, and waits for the stream.  Page-locked host memory
- * makes the copies asynchronous DMA.  Returns the device status as sdf_sync().
+ * copies points/weights to plan-owned device buffers, executes, brings the
+ * requested outputs back, and waits for the stream.  S, dS and d2S in
+ * page-locked (pinned, device-mapped) host memory are written by the kernels
+ * directly, over the CPU-GPU link while the rest of the execute runs; other
+ * outputs, and outputs in pageable memory, are staged on the device and
+ * copied at the end.  Returns the device status as sdf_sync().
  */
 sdf_status sdf_execute_host(sdf_plan plan, int64_t K, const double *points,
                             const double *weights, void *S, void *dS, void *d2S,

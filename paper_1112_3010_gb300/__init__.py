@@ -363,7 +363,7 @@ class Plan:
         return out
 
     def execute_host(self, points, weights=None, out=None):
-        """sdf_execute_host on host tensors (pinned memory makes the copies DMA)."""
+        """sdf_execute_host on host tensors (pinned S/dS/d2S are written by the kernels directly)."""
         t = self.torch
         pts = points.to(dtype=t.float64).contiguous()
         w = None if weights is None else weights.to(dtype=t.float64).contiguous()

@@ -515,6 +515,18 @@ sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double
     return SDF_OK;
 }
 
+// Device address of a pinned, mapped host buffer (kernels can store there
+// directly over the CPU-GPU link), else nullptr.
+static void *mapped_host(void *ptr) {
+    if (!ptr) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 sdf_status sdf_execute_host(sdf_plan p, int64_t K, const double *points, const double *weights, void *S, void *dS,
                             void *d2S, int8_t *sign, uint8_t *flags) {
     sdf_status s = check_execute_args(p, K, points, weights, dS, d2S, sign);
@@ -523,9 +535,13 @@ sdf_status sdf_execute_host(sdf_plan p, int64_t K, const double *points, const d
     const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
     const int64_t nn = p->nnodes;
     const int nh = D * (D + 1) / 2;
+    // S and its derivatives go straight to pinned host buffers (the kernels
+    // write them over the link while the rest computes); other outputs and
+    // unpinned buffers go through device staging and a copy at the end
+    void *mS = mapped_host(S), *mdS = mapped_host(dS), *md2 = mapped_host(d2S);
     size_t need = sizeof(double) * K * D * (weights ? 2 : 1);
-    size_t oS = need, odS = oS + (S ? esz * nn : 0), od2 = odS + (dS ? esz * nn * D : 0),
-           osg = od2 + (d2S ? esz * nn * nh : 0), ofl = osg + (sign ? nn : 0), tot = ofl + (flags ? nn : 0);
+    size_t oS = need, odS = oS + ((S && !mS) ? esz * nn : 0), od2 = odS + ((dS && !mdS) ? esz * nn * D : 0),
+           osg = od2 + ((d2S && !md2) ? esz * nn * nh : 0), ofl = osg + (sign ? nn : 0), tot = ofl + (flags ? nn : 0);
     if (tot > p->staging_bytes) {
         cudaStreamSynchronize(p->stream);
         cudaFree(p->staging);
@@ -539,16 +555,16 @@ sdf_status sdf_execute_host(sdf_plan p, int64_t K, const double *points, const d
     double *dw = weights ? dpts + K * D : nullptr;
     CK(cudaMemcpyAsync(dpts, points, sizeof(double) * K * D, cudaMemcpyHostToDevice, p->stream));
     if (weights) CK(cudaMemcpyAsync(dw, weights, sizeof(double) * K * D, cudaMemcpyHostToDevice, p->stream));
-    void *dS_ = S ? base + oS : nullptr;
-    void *ddS = dS ? base + odS : nullptr;
-    void *dd2 = d2S ? base + od2 : nullptr;
+    void *dS_ = S ? (mS ? mS : base + oS) : nullptr;
+    void *ddS = dS ? (mdS ? mdS : base + odS) : nullptr;
+    void *dd2 = d2S ? (md2 ? md2 : base + od2) : nullptr;
     int8_t *dsg = sign ? reinterpret_cast<int8_t *>(base + osg) : nullptr;
     uint8_t *dfl = flags ? reinterpret_cast<uint8_t *>(base + ofl) : nullptr;
     s = sdf_execute(p, K, dpts, dw, dS_, ddS, dd2, dsg, dfl);
     if (s != SDF_OK) return s;
-    if (S) CK(cudaMemcpyAsync(S, dS_, esz * nn, cudaMemcpyDeviceToHost, p->stream));
-    if (dS) CK(cudaMemcpyAsync(dS, ddS, esz * nn * D, cudaMemcpyDeviceToHost, p->stream));
-    if (d2S) CK(cudaMemcpyAsync(d2S, dd2, esz * nn * nh, cudaMemcpyDeviceToHost, p->stream));
+    if (S && !mS) CK(cudaMemcpyAsync(S, dS_, esz * nn, cudaMemcpyDeviceToHost, p->stream));
+    if (dS && !mdS) CK(cudaMemcpyAsync(dS, ddS, esz * nn * D, cudaMemcpyDeviceToHost, p->stream));
+    if (d2S && !md2) CK(cudaMemcpyAsync(d2S, dd2, esz * nn * nh, cudaMemcpyDeviceToHost, p->stream));
     if (sign) CK(cudaMemcpyAsync(sign, dsg, nn, cudaMemcpyDeviceToHost, p->stream));
     if (flags) CK(cudaMemcpyAsync(flags, dfl, nn, cudaMemcpyDeviceToHost, p->stream));
     return sdf_sync(p);

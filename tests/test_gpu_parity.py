@@ -128,3 +128,25 @@ def test_execute_host_matches_device():
     plan.execute_host(torch.from_numpy(s.points).pin_memory(), torch.from_numpy(s.weights).pin_memory(), out)
     for k in out:
         assert torch.equal(out[k], dev[k].cpu()), k
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_execute_host_fixup_outputs(pinned):
+    # a small tau so that the fix-up rewrites many nodes: with pinned buffers
+    # S, dS and d2S are written by the kernels straight into host memory,
+    # with pageable ones they are staged on the device and copied
+    s = wl.stars(N=256, K=3000, n_shapes=2, tau=0.004, seed=21)
+    plan = pkg.Plan(2, s.dims, s.h, s.tau, precision="fp32", outputs=("S", "dS", "d2S", "sign"))
+    dev = plan.execute(torch.from_numpy(s.points).cuda(), torch.from_numpy(s.weights).cuda())
+    assert plan.stats().n_fixup_nodes > 0
+    shp = (s.dims[1], s.dims[0])
+
+    def host(shape, dtype):
+        t = torch.empty(shape, dtype=dtype)
+        return t.pin_memory() if pinned else t
+
+    out = {"S": host(shp, torch.float32), "dS": host((2,) + shp, torch.float32),
+           "d2S": host((3,) + shp, torch.float32), "sign": host(shp, torch.int8), "flags": host(shp, torch.uint8)}
+    plan.execute_host(torch.from_numpy(s.points), torch.from_numpy(s.weights), out)
+    for k in out:
+        assert torch.equal(out[k], dev[k].cpu()), k
