@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
     __shared__ int soff[NT + 1];      // first staged cell of each taken bin, then the total
     __shared__ int ssrc[NT];          // the bin's first entry in ucell / ucount
     __shared__ int sbin[NT];          // the bin's index
+    __shared__ float4 sbox[NT];       // the bin's first node (x, y, z) and whether it holds points
     __shared__ int wtot[32];
     const int tid = threadIdx.x;
     const int nt0 = (P.nb0 + TB - 1) / TB, nt1 = (P.nb1 + TB - 1) / TB;
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
         for (int i0 = 0; i0 < nring;) {
             // one candidate bin per thread
             const int i = i0 + tid;
-            int nb = 0, gb = -1, s0 = 0;
+            int nb = 0, gb = -1, s0 = 0, cx = 0, cy = 0, cz = 0;
             if (i < nring) {
                 int k = k0, ii = i;
                 while (ii >= nring_of(k)) {
@@ -261,6 +262,9 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
                     ring3(k, ii, dx, dy, dz);
                 }
                 const int qx = bx + dx, qy = by + dy, qz = bz + dz;
+                cx = qx;
+                cy = qy;
+                cz = qz;
                 if (qx >= 0 && qx < P.nb0 && qy >= 0 && qy < P.nb1 && (D == 2 || (qz >= 0 && qz < P.nb2))) {
                     gb = qx + P.nb0 * (qy + P.nb1 * qz);
                     nb = P.bin_nuniq[gb];
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
                 soff[tid] = off;
                 ssrc[tid] = s0;
                 sbin[tid] = gb;
+                sbox[tid] = make_float4(8.f * cx, 8.f * cy, 8.f * cz, nb > 0 ? 1.f : 0.f);
             }
             if (tid == taken - 1) soff[taken] = off + nb;
             __syncthreads();
@@ -319,8 +324,30 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
                 // be nearer than m by more than 60 tau ln 2 (term > 2^60),
                 // calls for the nearest point of the batch first
                 const float lim = 60.f / l2e_th;
+                // bin boxes are close enough unless tau is below ~0.3 h: the
+                // nearest point may then lie a bin diagonal (7 sqrt(D) nodes)
+                // beyond the box bound, its term 2^(-7 sqrt(D) l2e_th)
+                const bool by_bins = 7.f * ((D == 2) ? 1.4143f : 1.7321f) * l2e_th < 60.f;
                 if (mg[0] - lb_in > lim || mg[1] - lb_in > lim) {
                     float mn[NPT] = {INFINITY, INFINITY};
+                    if (by_bins) {
+                        // distance to the nearest occupied bin's box: a lower
+                        // bound on the nearest point within one bin diagonal
+                        for (int b = 0; b < taken; ++b) {
+                            const float4 bq = sbox[b];
+                            if (bq.w == 0.f) continue;
+                            const float ex = fmaxf(fmaxf(bq.x - xf, xf - (bq.x + 7.f)), 0.f);
+                            const float ey = (D == 2) ? 0.f : fmaxf(fmaxf(bq.y - yf, yf - (bq.y + 7.f)), 0.f);
+                            const float base = fmaf(ex, ex, ey * ey);
+#pragma unroll
+                            for (int j = 0; j < NPT; ++j) {
+                                const float c = (D == 2) ? yf + kOff * j : zf + kOff * j;
+                                const float lo = (D == 2) ? bq.y : bq.z;
+                                const float ec = fmaxf(fmaxf(lo - c, c - (lo + 7.f)), 0.f);
+                                mn[j] = fminf(mn[j], fmaf(ec, ec, base));
+                            }
+                        }
+                    } else {
                     for (int e = 0; e < ncell; ++e) {
                         const float4 q = cell[e];
                         const float d0 = xf - q.x, d1 = yf - q.y;
@@ -331,6 +358,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
                             const float cj = cl + kOff * j;
                             mn[j] = fminf(mn[j], fmaf(cj, cj, base));
                         }
+                    }
                     }
 #pragma unroll
                     for (int j = 0; j < NPT; ++j) {
