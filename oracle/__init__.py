@@ -14,6 +14,9 @@ Every quantity is the paper's definition summed directly over the points:
   kappdiscreteZ) or topological degree (eq. normflux), and R (eq. Rdef).
 * :func:`adjoint` -- dL/dY_k and dL/dtau of L = sum_X w(X) S(X), the chain
   rule applied to eq. STilde.
+* :func:`curvature` -- Gaussian, mean and principal curvatures from grad S
+  and the Hessian (Sec. 5): of the graph z = S(x, y) in 2D, of the level
+  surfaces of S in 3D.
 * :func:`sign_from_mu` -- inside/outside from mu: inside iff |mu| >= 1/2
   (the nonzero-winding rule of Sec. 4.1), positive inside (Sec. 1).
 """
@@ -63,6 +66,8 @@ def _load():
             lib.oracle_adjoint.argtypes = [ctypes.c_int, i64, d, i64, d, d,
                                            ctypes.c_double, d, d]
             lib.oracle_adjoint.restype = None
+            lib.oracle_curvature.argtypes = [ctypes.c_int, i64, d, d, d]
+            lib.oracle_curvature.restype = None
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -139,6 +144,17 @@ def adjoint(points, X, wX, tau):
     _load().oracle_adjoint(D, K, _dp(Y), Xa.shape[0], _dp(Xa), _dp(w),
                            float(tau), _dp(dY), _dp(dt))
     return dY, float(dt[0])
+
+
+def curvature(dS, d2S):
+    """Curvatures (n x 4: K, H, k1, k2) from grad S (n x D) and the Hessian
+    (n x D(D+1)/2): the graph z = S(x, y) in 2D, level surfaces in 3D."""
+    g = _c64(dS)
+    D = g.shape[1]
+    h = _c64(d2S, (g.shape[0], D * (D + 1) // 2))
+    out = np.empty((g.shape[0], 4))
+    _load().oracle_curvature(D, g.shape[0], _dp(g), _dp(h), _dp(out))
+    return out
 
 
 def sign_from_mu(mu):

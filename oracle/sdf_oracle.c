@@ -251,3 +251,56 @@ void oracle_adjoint(int D, int64_t K, const double *Y, int64_t nX,
     free(Sx);
     free(wr);
 }
+
+/*
+ * oracle_curvature -- curvature fields from grad S and the Hessian at nX
+ * points (Sec. 5: from the derivatives one obtains "derived quantities such as
+ * curvature (Gaussian, mean and principal curvatures)" of the surface S(X)).
+ *   2D: the surface is the graph z = S(x, y) (a Monge patch, upward normal),
+ *       W = 1 + S_x^2 + S_y^2:
+ *         K = (S_xx S_yy - S_xy^2) / W^2
+ *         H = ((1 + S_y^2) S_xx - 2 S_x S_y S_xy + (1 + S_x^2) S_yy) / (2 W^{3/2})
+ *   3D: the paper is silent; read as the level surfaces of S, normal
+ *       n = grad S/|grad S|, g = |grad S|:
+ *         H = (g^2 tr(Hess) - grad S^T Hess grad S) / (2 g^3)
+ *         K = grad S^T adj(Hess) grad S / g^4   (adj: the adjugate matrix)
+ *       and 0 where g = 0.
+ *   Principal curvatures k1 >= k2: H +- sqrt(max(H^2 - K, 0)).
+ * dS: nX x D, d2S: nX x D(D+1)/2 (xx, yy[, zz], xy[, xz, yz]);
+ * out: nX x 4 (K, H, k1, k2).
+ */
+void oracle_curvature(int D, int64_t nX, const double *dS, const double *d2S, double *out) {
+    const int nH = D * (D + 1) / 2;
+    for (int64_t i = 0; i < nX; ++i) {
+        const double *g = dS + i * D, *h = d2S + i * nH;
+        double K = 0.0, H = 0.0;
+        if (D == 2) {
+            const double sx = g[0], sy = g[1], sxx = h[0], syy = h[1], sxy = h[2];
+            const double W = 1.0 + sx * sx + sy * sy;
+            K = (sxx * syy - sxy * sxy) / (W * W);
+            H = ((1.0 + sy * sy) * sxx - 2.0 * sx * sy * sxy + (1.0 + sx * sx) * syy) / (2.0 * pow(W, 1.5));
+        } else {
+            const double sx = g[0], sy = g[1], sz = g[2];
+            const double a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5];
+            const double g2 = sx * sx + sy * sy + sz * sz;
+            if (g2 > 0.0) {
+                const double gn = sqrt(g2);
+                /* grad S^T Hess grad S */
+                const double gHg = sx * (a * sx + d * sy + e * sz) + sy * (d * sx + b * sy + f * sz) +
+                                   sz * (e * sx + f * sy + c * sz);
+                H = (g2 * (a + b + c) - gHg) / (2.0 * g2 * gn);
+                /* grad S^T adj(Hess) grad S, adj of [[a,d,e],[d,b,f],[e,f,c]] */
+                const double gAg = sx * sx * (b * c - f * f) + sy * sy * (a * c - e * e) + sz * sz * (a * b - d * d) +
+                                   2.0 * sx * sy * (e * f - c * d) + 2.0 * sx * sz * (d * f - b * e) +
+                                   2.0 * sy * sz * (d * e - a * f);
+                K = gAg / (g2 * g2);
+            }
+        }
+        const double disc = H * H - K;
+        const double sq = disc > 0.0 ? sqrt(disc) : 0.0;
+        out[i * 4 + 0] = K;
+        out[i * 4 + 1] = H;
+        out[i * 4 + 2] = H + sq;
+        out[i * 4 + 3] = H - sq;
+    }
+}

@@ -339,3 +339,119 @@ def test_example2_percent_error_below_printed_bound():
     tau, bound = np.loadtxt(os.path.join(GOLDEN, "example2_mean_percent_error.txt"))
     got = _percent_error_stat(2.0 ** -10, 10000, tau, seed=2)
     assert got < bound
+
+
+# ---------------------------------------------------------------- curvature
+# (Sec. 5: Gaussian, mean and principal curvatures from the derivatives)
+
+
+def _rot2(t):
+    return np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]])
+
+
+def _rot3(a, b, c):
+    rz = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+    ry = np.array([[np.cos(b), 0, np.sin(b)], [0, 1, 0], [-np.sin(b), 0, np.cos(b)]])
+    rx = np.array([[1, 0, 0], [0, np.cos(c), -np.sin(c)], [0, np.sin(c), np.cos(c)]])
+    return rz @ ry @ rx
+
+
+def _pack(Hm):
+    """Symmetric Hessian matrices (n x D x D) -> planes xx, yy[, zz], xy[, xz, yz]."""
+    D = Hm.shape[1]
+    if D == 2:
+        return np.stack([Hm[:, 0, 0], Hm[:, 1, 1], Hm[:, 0, 1]], axis=1)
+    return np.stack([Hm[:, 0, 0], Hm[:, 1, 1], Hm[:, 2, 2], Hm[:, 0, 1], Hm[:, 0, 2], Hm[:, 1, 2]], axis=1)
+
+
+def test_curvature_2d_sphere_cap_closed_form():
+    # graph z = sqrt(R^2 - x^2 - y^2): a sphere, K = 1/R^2, H = -1/R everywhere
+    R = 0.7
+    rng = np.random.default_rng(3)
+    xy = rng.uniform(-0.4, 0.4, size=(50, 2))
+    x, y = xy[:, 0], xy[:, 1]
+    z = np.sqrt(R * R - x * x - y * y)
+    g = np.stack([-x / z, -y / z], axis=1)
+    Hm = np.empty((50, 2, 2))
+    Hm[:, 0, 0] = -(R * R - y * y) / z ** 3
+    Hm[:, 1, 1] = -(R * R - x * x) / z ** 3
+    Hm[:, 0, 1] = Hm[:, 1, 0] = -x * y / z ** 3
+    c = oracle.curvature(g, _pack(Hm))
+    assert np.allclose(c[:, 0], 1 / R ** 2, rtol=1e-12)
+    assert np.allclose(c[:, 1], -1 / R, rtol=1e-12)
+    assert np.allclose(c[:, 2], -1 / R, atol=1e-6) and np.allclose(c[:, 3], -1 / R, atol=1e-6)
+
+
+def test_curvature_2d_saddle_closed_form():
+    # graph z = x y: K = -1/W^2, H = -x y / W^{3/2}, W = 1 + x^2 + y^2
+    rng = np.random.default_rng(4)
+    xy = rng.uniform(-1, 1, size=(50, 2))
+    x, y = xy[:, 0], xy[:, 1]
+    g = np.stack([y, x], axis=1)
+    d2 = np.stack([np.zeros(50), np.zeros(50), np.ones(50)], axis=1)
+    c = oracle.curvature(g, d2)
+    W = 1 + x * x + y * y
+    assert np.allclose(c[:, 0], -1 / W ** 2, rtol=1e-12)
+    assert np.allclose(c[:, 1], -x * y / W ** 1.5, rtol=1e-12, atol=1e-15)
+    assert np.allclose(c[:, 2] * c[:, 3], c[:, 0], rtol=1e-10)
+    # a rotation of the plane is an isometry of the graph
+    Q = _rot2(0.7)
+    p = xy @ Q.T  # f(p) = p_x p_y with p = Q X
+    gp = np.stack([p[:, 1], p[:, 0]], axis=1) @ Q  # grad_X = Q^T grad_p
+    Hp = np.array([[0.0, 1.0], [1.0, 0.0]])
+    HX = np.einsum("ji,jk,kl->il", Q, Hp, Q)
+    c2 = oracle.curvature(gp, _pack(np.broadcast_to(HX, (50, 2, 2))))
+    Wp = 1 + p[:, 0] ** 2 + p[:, 1] ** 2
+    assert np.allclose(c2[:, 0], -1 / Wp ** 2, rtol=1e-12)
+
+
+def test_curvature_2d_cone_from_single_point():
+    # K = 1: S = r (a cone), developable: K = 0, H = 1/(2 sqrt(2) r)
+    Y = np.array([[0.4, 0.55]])
+    X = np.array([[0.9, 0.2], [0.1, 0.1], [0.45, 0.9]])
+    ev = oracle.evaluate(Y, X, 0.01, want=("dS", "d2S"))
+    c = oracle.curvature(ev["dS"], ev["d2S"])
+    r = np.linalg.norm(X - Y, axis=1)
+    assert np.allclose(c[:, 0], 0.0, atol=1e-12)
+    assert np.allclose(c[:, 1], 1 / (2 * np.sqrt(2) * r), rtol=1e-10)
+
+
+def test_curvature_3d_level_sets_closed_forms():
+    # one point: level sets are spheres of radius r, H = 1/r, K = 1/r^2
+    Y = np.array([[0.5, 0.5, 0.5]])
+    X = np.array([[0.9, 0.2, 0.3], [0.1, 0.6, 0.8]])
+    ev = oracle.evaluate(Y, X, 0.01, want=("dS", "d2S"))
+    c = oracle.curvature(ev["dS"], ev["d2S"])
+    r = np.linalg.norm(X - Y, axis=1)
+    assert np.allclose(c[:, 1], 1 / r, rtol=1e-10)
+    assert np.allclose(c[:, 0], 1 / r ** 2, rtol=1e-10)
+    # S = distance to the z axis: cylinders, H = 1/(2 rho), K = 0, k1 = 1/rho, k2 = 0
+    rng = np.random.default_rng(5)
+    P = rng.uniform(-1, 1, size=(40, 3))
+    rho = np.hypot(P[:, 0], P[:, 1])
+    g = np.stack([P[:, 0] / rho, P[:, 1] / rho, np.zeros(40)], axis=1)
+    Hm = np.zeros((40, 3, 3))
+    Hm[:, 0, 0] = P[:, 1] ** 2 / rho ** 3
+    Hm[:, 1, 1] = P[:, 0] ** 2 / rho ** 3
+    Hm[:, 0, 1] = Hm[:, 1, 0] = -P[:, 0] * P[:, 1] / rho ** 3
+    c = oracle.curvature(g, _pack(Hm))
+    assert np.allclose(c[:, 1], 1 / (2 * rho), rtol=1e-12)
+    assert np.allclose(c[:, 0], 0.0, atol=1e-12)
+    assert np.allclose(c[:, 2], 1 / rho, rtol=1e-6) and np.allclose(c[:, 3], 0.0, atol=1e-6)
+
+
+@pytest.mark.parametrize("a,b", [(0.5, 2.0), (1.0, 1.0), (0.3, -0.8)])
+def test_curvature_3d_rotated_paraboloid_vertex(a, b):
+    # S = x + (y^2/a + z^2/b)/2: at the vertex the level set has principal
+    # curvatures 1/a, 1/b (normal +x); any rotation leaves them unchanged,
+    # which exercises every cross term of the adjugate
+    Hf = np.diag([0.0, 1 / a, 1 / b])
+    gf = np.array([1.0, 0.0, 0.0])
+    for ang in ((0, 0, 0), (0.3, 1.1, -0.7), (2.0, -0.4, 0.9)):
+        Q = _rot3(*ang)
+        g = (Q.T @ gf)[None, :]
+        Hm = (Q.T @ Hf @ Q)[None]
+        c = oracle.curvature(g, _pack(Hm))[0]
+        assert np.isclose(c[1], 0.5 * (1 / a + 1 / b), rtol=1e-12)
+        assert np.isclose(c[0], 1 / (a * b), rtol=1e-12)
+        assert np.isclose(c[2], max(1 / a, 1 / b), rtol=1e-9) and np.isclose(c[3], min(1 / a, 1 / b), rtol=1e-9)
