@@ -198,6 +198,27 @@ sdf_status sdf_backward(sdf_plan plan, int64_t K, const double *points,
                         const void *w, const void *S_saved,
                         const uint8_t *flags, double *dL_dY, double *dL_dtau);
 
+/*
+ * sdf_curvature -- curvature fields from the grad S and Hessian planes an
+ * sdf_execute wrote (Sec. 5: the derivatives give "derived quantities such as
+ * curvature (Gaussian, mean and principal curvatures)" of the surface S(X)).
+ *   2D: the graph z = S(x, y) as a Monge patch, W = 1 + S_x^2 + S_y^2:
+ *       K = (S_xx S_yy - S_xy^2)/W^2,
+ *       H = ((1 + S_y^2) S_xx - 2 S_x S_y S_xy + (1 + S_x^2) S_yy)/(2 W^{3/2}).
+ *   3D: the paper is silent; the level surfaces of S, g = |grad S|:
+ *       H = (g^2 tr(Hess) - grad S^T Hess grad S)/(2 g^3),
+ *       K = grad S^T adj(Hess) grad S / g^4 (0 where g = 0).
+ *   Principal curvatures k1 >= k2 = H +- sqrt(max(H^2 - K, 0)).
+ *   dS, d2S  device, the D and D(D+1)/2 planes of one execute (plan type).
+ *   flags    device N^D flags of the same execute, or NULL; nodes with
+ *            SDF_FLAG_CAPPED get 0.
+ *   curv     device, 4 planes of N^D (plan type): K, H, k1, k2.
+ * Caller-owned buffers; enqueued on the plan's stream (asynchronous, errors
+ * as for sdf_execute).  SDF_ERR_INVALID_ARG for a NULL plan or plane.
+ */
+sdf_status sdf_curvature(sdf_plan plan, const void *dS, const void *d2S,
+                         const uint8_t *flags, void *curv);
+
 /* Wait for the plan's stream; return (and clear) any error recorded on the
  * device since the last sdf_sync, or SDF_ERR_CUDA for an asynchronous fault. */
 sdf_status sdf_sync(sdf_plan plan);

@@ -32,7 +32,7 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_last_error", "sdf_profile_enable", "sdf_profile_read",
             "sdf_plan_set_noise_constants", "sdf_execute_noalloc", "sdf_batch_create",
             "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy",
-            "sdf_plan_set_tuning", "sdf_plan_autotune"]
+            "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature"]
 
 
 class SDFError(RuntimeError):
@@ -89,6 +89,7 @@ def load_library(path: str | None = None):
         L.sdf_execute.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
         L.sdf_execute_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
         L.sdf_backward.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+        L.sdf_curvature.argtypes = [vp, vp, vp, vp, vp]
         L.sdf_sync.argtypes = [vp]
         L.sdf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         L.sdf_get_stats.argtypes = [vp, ctypes.POINTER(ExecStats)]
@@ -125,7 +126,7 @@ def load_library(path: str | None = None):
         L.sdf_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), ctypes.c_int]
         L.sdf_profile_read.restype = ctypes.c_int
         for n in ("sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
-                  "sdf_plan_get_info", "sdf_get_stats"):
+                  "sdf_plan_get_info", "sdf_get_stats", "sdf_curvature"):
             getattr(L, n).restype = ctypes.c_int
         _LIBH = L
         return L
@@ -170,6 +171,10 @@ def sdf_execute_host(handle, K, points, weights, S, dS, d2S, sign, flags):
 def sdf_backward(handle, K, points, w, S_saved, flags, dL_dY, dL_dtau):
     _ck(_lib().sdf_backward(handle, int(K), _ptr(points), _ptr(w), _ptr(S_saved), _ptr(flags),
                             _ptr(dL_dY), _ptr(dL_dtau)), "sdf_backward")
+
+
+def sdf_curvature(handle, dS, d2S, flags, curv):
+    _ck(_lib().sdf_curvature(handle, _ptr(dS), _ptr(d2S), _ptr(flags), _ptr(curv)), "sdf_curvature")
 
 
 def sdf_sync(handle):
@@ -373,6 +378,15 @@ class Plan:
         sdf_execute_host(self.handle, pts.shape[0], pts, w, out.get("S"), out.get("dS"),
                          out.get("d2S"), out.get("sign"), out.get("flags"))
         return out
+
+    def curvature(self, out):
+        """Gaussian, mean and principal curvatures (4, *grid) from an execute's
+        output dict (needs dS and d2S; flags used when present)."""
+        t = self.torch
+        curv = t.empty((4,) + tuple(out["S"].shape), dtype=self.dtype, device="cuda")
+        sdf_curvature(self.handle, out["dS"], out["d2S"], out.get("flags"), curv)
+        self.sync()
+        return curv
 
     def backward(self, points, w, S_saved, flags=None):
         """dL/dY (K x D, float64, device) and dL/dtau (float64 scalar)."""
