@@ -263,6 +263,18 @@ sdf_status sdf_plan_autotune(sdf_plan plan, int64_t K, const double *points,
                              int *lines_F, int *fused_variant);
 
 /*
+ * sdf_plan_set_full_range -- SDF_FP32 plans: when enable != 0, the fix-up
+ * computes every node whose phi is below theta_32, with no cap at theta_64:
+ * S, grad S and the Hessian come from the shifted direct sum of Sec. 2.4
+ * (eq. Bound1) however small phi is, so nothing is flagged SDF_FLAG_CAPPED.
+ * This is the range the paper reaches only with multiple-precision FFTs
+ * (Secs. 3.3-3.4, Example 1 at tau/h ~ 0.03).  Costs fix-up time in
+ * proportion to the untrusted nodes.  SDF_ERR_UNSUPPORTED for SDF_FP64 plans
+ * (they have no fix-up); SDF_ERR_INVALID_ARG for a NULL plan.
+ */
+sdf_status sdf_plan_set_full_range(sdf_plan plan, int enable);
+
+/*
  * sdf_profile_enable -- when enable != 0, every kernel the plan launches is
  * bracketed by a pair of CUDA events recorded on the plan's stream (the
  * stream the kernel runs on), so the durations are device times of that

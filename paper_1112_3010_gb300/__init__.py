@@ -32,7 +32,7 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_last_error", "sdf_profile_enable", "sdf_profile_read",
             "sdf_plan_set_noise_constants", "sdf_execute_noalloc", "sdf_batch_create",
             "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy",
-            "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature"]
+            "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature", "sdf_plan_set_full_range"]
 
 
 class SDFError(RuntimeError):
@@ -90,6 +90,7 @@ def load_library(path: str | None = None):
         L.sdf_execute_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
         L.sdf_backward.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         L.sdf_curvature.argtypes = [vp, vp, vp, vp, vp]
+        L.sdf_plan_set_full_range.argtypes = [vp, ctypes.c_int]
         L.sdf_sync.argtypes = [vp]
         L.sdf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         L.sdf_get_stats.argtypes = [vp, ctypes.POINTER(ExecStats)]
@@ -126,7 +127,7 @@ def load_library(path: str | None = None):
         L.sdf_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), ctypes.c_int]
         L.sdf_profile_read.restype = ctypes.c_int
         for n in ("sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
-                  "sdf_plan_get_info", "sdf_get_stats", "sdf_curvature"):
+                  "sdf_plan_get_info", "sdf_get_stats", "sdf_curvature", "sdf_plan_set_full_range"):
             getattr(L, n).restype = ctypes.c_int
         _LIBH = L
         return L
@@ -171,6 +172,10 @@ def sdf_execute_host(handle, K, points, weights, S, dS, d2S, sign, flags):
 def sdf_backward(handle, K, points, w, S_saved, flags, dL_dY, dL_dtau):
     _ck(_lib().sdf_backward(handle, int(K), _ptr(points), _ptr(w), _ptr(S_saved), _ptr(flags),
                             _ptr(dL_dY), _ptr(dL_dtau)), "sdf_backward")
+
+
+def sdf_plan_set_full_range(handle, enable):
+    _ck(_lib().sdf_plan_set_full_range(handle, 1 if enable else 0), "sdf_plan_set_full_range")
 
 
 def sdf_curvature(handle, dS, d2S, flags, curv):
@@ -285,7 +290,8 @@ _OUTS = {"S": SDF_OUT_S, "dS": SDF_OUT_DS, "d2S": SDF_OUT_D2S, "sign": SDF_OUT_S
 class Plan:
     """A plan for one grid (D, dims, h) and tau, on the current torch stream."""
 
-    def __init__(self, D, dims, h, tau, precision="fp32", outputs=("S", "dS", "sign"), stream=None):
+    def __init__(self, D, dims, h, tau, precision="fp32", outputs=("S", "dS", "sign"), stream=None,
+                 full_range=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -305,6 +311,8 @@ class Plan:
                                       self.outputs, self.stream.cuda_stream)
         self.dtype = torch.float64 if self.precision == SDF_FP64 else torch.float32
         self.n_nodes = int(np.prod(self.dims))
+        if full_range:
+            sdf_plan_set_full_range(self.handle, True)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

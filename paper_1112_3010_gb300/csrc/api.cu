@@ -638,6 +638,16 @@ sdf_status sdf_plan_set_tuning(sdf_plan p, int lines_T, int lines_F, int fused_v
     return SDF_OK;
 }
 
+sdf_status sdf_plan_set_full_range(sdf_plan p, int enable) {
+    if (!p) return SDF_ERR_INVALID_ARG;
+    if (p->prec != SDF_FP32) {
+        set_last_error("sdf_plan_set_full_range: SDF_FP32 plans only (the fix-up supplies the range)");
+        return SDF_ERR_UNSUPPORTED;
+    }
+    p->full_range = enable != 0;
+    return SDF_OK;
+}
+
 // Device time of the named kernels over `reps` executes (after one warm-up).
 static sdf_status time_kernels(sdf_plan p, int64_t K, const double *points, const double *weights, int reps,
                                const char *const *names, int nnames, double *ms) {

@@ -24,7 +24,9 @@
 // (and over a later batch only if it could hold a point so much nearer that a
 // term would exceed 2^60), so the summing loop itself has no branch.  A
 // tile whose nearest occupied bin is so far that K exp(-d/tau) < theta_64
-// keeps the capped value.  Visiting order is fixed, so the sums are
+// keeps the capped value.  In full-range mode nothing is capped: every node
+// the float transform does not trust gets the sum, however small phi is (the
+// regime the paper reaches only with multiple-precision arithmetic).  Visiting order is fixed, so the sums are
 // deterministic.
 #include <cuda_runtime.h>
 #include <limits.h>
@@ -50,7 +52,7 @@ struct FixParams {
     double coef64;
     float log_coef64;
     float h, tau, l2e_th, logK;  // spacing, tau, h log2(e)/tau, log K
-    int fp64_out;
+    int full;  // full range: no capping at theta_64 (every untrusted node is summed)
 };
 
 constexpr int kFixCap = 1024;  // cells staged in shared memory at once
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
     const float lt = s_lt;
     const float dlo = (c >= 1) ? (8.f * (c - 1) + 1.f) * P.h : 0.f;
     // every node of the tile: phi <= K exp(-dlo/tau) < theta64 -> stays capped
-    if (c >= 255 || P.logK - dlo / P.tau < lt) return;
+    if (!P.full && (c >= 255 || P.logK - dlo / P.tau < lt)) return;
 
     // this thread's nodes: (x, y, z) and the same plus kOff along y (2D) or z (3D)
     const int x = (D == 2) ? bx * 8 + (tid % (8 * TB)) : bx * 8 + (tid & 7);
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
             // phi < theta_64 whatever the rest adds: capped
             const float hi = fmaxf(A, tail0), lo = fminf(A, tail0);
             const float lphi = hi + __logf(1.f + __expf(lo - hi));  // log of the bound on phi
-            if (lphi < lt - 1e-4f) {
+            if (!P.full && lphi < lt - 1e-4f) {
                 active[j] = false;
                 early_cap[j] = true;
                 continue;
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
             int ev = kLook;
             for (int i = 1; i < kLook; ++i) {
                 const float Ti = s_logT[i];
-                if (Ti <= lphi - 11.512925f || (A < lt - 1e-4f && Ti < lt - 1e-4f)) {
+                if (Ti <= lphi - 11.512925f || (!P.full && A < lt - 1e-4f && Ti < lt - 1e-4f)) {
                     ev = i;
                     break;
                 }
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
         const int64_t nd = node[j];
         const float S = fmaf(mg[j], h, -tau * logf(sE[j]));
         const float sg = (P.sign && P.sign[nd] < 0) ? -1.f : 1.f;
-        if (early_cap[j] || !(S <= scap)) {
+        if (!P.full && (early_cap[j] || !(S <= scap))) {
             ++capped;
             P.flags[nd] = SDF_FLAG_CAPPED | SDF_FLAG_FIXUP;
             continue;
@@ -551,7 +553,7 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS
     F.coef64 = p->noise_c64 * ldexp(1.0, -53) * sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
     F.logK = (float)log((double)p->last_K);
     F.log_coef64 = (float)log(F.coef64);
-    F.fp64_out = 0;
+    F.full = p->full_range ? 1 : 0;
     prof_begin(p, "fixup", p->stream);
     if (D == 2) {
         const int64_t nt = ((p->nb[0] + kTB2 - 1) / kTB2) * ((p->nb[1] + kTB2 - 1) / kTB2);

@@ -125,6 +125,7 @@ struct sdf_plan_impl {
     // tile schedule (0: built-in rule): lines per CTA of the transposed passes
     // and of the fused pass, and the fused pass's register variant
     int tune_RT = 0, tune_RF = 0, tune_FV = 0;
+    bool full_range = false;  // fix-up without the theta_64 cap (sdf_plan_set_full_range)
     // profiling
     bool prof_on = false;
     int64_t nlaunch = 0;      // kernels launched by the current/last execute
