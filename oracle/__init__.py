@@ -17,6 +17,9 @@ Every quantity is the paper's definition summed directly over the points:
 * :func:`curvature` -- Gaussian, mean and principal curvatures from grad S
   and the Hessian (Sec. 5): of the graph z = S(x, y) in 2D, of the level
   surfaces of S in 3D.
+* :func:`mesh_sources` -- triangle incentres and area-weighted normals as the
+  3D degree's sources (Sec. 4.2, Example 5); :func:`solid_angle_degree` --
+  the exact degree of a closed triangle mesh (a textbook check).
 * :func:`sign_from_mu` -- inside/outside from mu: inside iff |mu| >= 1/2
   (the nonzero-winding rule of Sec. 4.1), positive inside (Sec. 1).
 """
@@ -68,6 +71,10 @@ def _load():
             lib.oracle_adjoint.restype = None
             lib.oracle_curvature.argtypes = [ctypes.c_int, i64, d, d, d]
             lib.oracle_curvature.restype = None
+            lib.oracle_mesh_sources.argtypes = [i64, d, ctypes.POINTER(i64), d, d, d]
+            lib.oracle_mesh_sources.restype = None
+            lib.oracle_solid_angle_degree.argtypes = [i64, d, ctypes.POINTER(i64), i64, d, d]
+            lib.oracle_solid_angle_degree.restype = None
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -154,6 +161,32 @@ def curvature(dS, d2S):
     h = _c64(d2S, (g.shape[0], D * (D + 1) // 2))
     out = np.empty((g.shape[0], 4))
     _load().oracle_curvature(D, g.shape[0], _dp(g), _dp(h), _dp(out))
+    return out
+
+
+def _i64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def mesh_sources(V, F, center=None):
+    """Incentres Y (nf x 3) and area-weighted normals P (nf x 3) of a triangle
+    mesh; ``center`` (3,) applies the Example 5 orientation rule."""
+    Va = _c64(V).reshape(-1, 3)
+    Fa = np.ascontiguousarray(F, dtype=np.int64).reshape(-1, 3)
+    Y = np.empty((Fa.shape[0], 3))
+    P = np.empty((Fa.shape[0], 3))
+    c = None if center is None else _c64(center).reshape(3)
+    _load().oracle_mesh_sources(Fa.shape[0], _dp(Va), _i64p(Fa), _dp(c), _dp(Y), _dp(P))
+    return Y, P
+
+
+def solid_angle_degree(V, F, X):
+    """Exact degree (solid angle / 4 pi) of a closed triangle mesh at X (n x 3)."""
+    Va = _c64(V).reshape(-1, 3)
+    Fa = np.ascontiguousarray(F, dtype=np.int64).reshape(-1, 3)
+    Xa = _c64(X).reshape(-1, 3)
+    out = np.empty(Xa.shape[0])
+    _load().oracle_solid_angle_degree(Fa.shape[0], _dp(Va), _i64p(Fa), Xa.shape[0], _dp(Xa), _dp(out))
     return out
 
 

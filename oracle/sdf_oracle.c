@@ -304,3 +304,74 @@ void oracle_curvature(int D, int64_t nX, const double *dS, const double *d2S, do
         out[i * 4 + 3] = H - sq;
     }
 }
+
+/*
+ * oracle_mesh_sources -- point sources of a triangle mesh for the 3D degree
+ * (Sec. 4.2 and Example 5): Y_k = the incentre of triangle k (vertices A, B,
+ * C weighted by the opposite side lengths), P_k = (B - A) x (C - A) / 2, the
+ * edge cross product scaled to the triangle's area (area-weighted normal).
+ * If center != NULL, P_k is negated where <Y_k - center, P_k> < 0 (the
+ * orientation rule of Example 5, with the object's centre as origin);
+ * otherwise the faces' vertex order orients P_k.
+ * V: nv x 3, F: nf x 3 vertex indices; Y, P: nf x 3.
+ */
+void oracle_mesh_sources(int64_t nf, const double *V, const int64_t *F, const double *center, double *Y, double *P) {
+    for (int64_t k = 0; k < nf; ++k) {
+        const double *A = V + 3 * F[3 * k], *B = V + 3 * F[3 * k + 1], *C = V + 3 * F[3 * k + 2];
+        double ab[3], ac[3], bc[3];
+        for (int a = 0; a < 3; ++a) {
+            ab[a] = B[a] - A[a];
+            ac[a] = C[a] - A[a];
+            bc[a] = C[a] - B[a];
+        }
+        const double la = sqrt(bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]); /* opposite A */
+        const double lb = sqrt(ac[0] * ac[0] + ac[1] * ac[1] + ac[2] * ac[2]); /* opposite B */
+        const double lc = sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]); /* opposite C */
+        const double sum = la + lb + lc;
+        for (int a = 0; a < 3; ++a) Y[3 * k + a] = (la * A[a] + lb * B[a] + lc * C[a]) / sum;
+        double n[3] = {0.5 * (ab[1] * ac[2] - ab[2] * ac[1]), 0.5 * (ab[2] * ac[0] - ab[0] * ac[2]),
+                       0.5 * (ab[0] * ac[1] - ab[1] * ac[0])};
+        if (center) {
+            double dot = 0.0;
+            for (int a = 0; a < 3; ++a) dot += (Y[3 * k + a] - center[a]) * n[a];
+            if (dot < 0.0)
+                for (int a = 0; a < 3; ++a) n[a] = -n[a];
+        }
+        for (int a = 0; a < 3; ++a) P[3 * k + a] = n[a];
+    }
+}
+
+/*
+ * oracle_solid_angle_degree -- the exact degree of a closed oriented triangle
+ * mesh about each evaluation point: (1/4 pi) sum_k Omega_k(X), Omega_k the
+ * signed solid angle of triangle k seen from X (Van Oosterom and Strackee's
+ * formula: tan(Omega/2) = a.(b x c) / (|a||b||c| + (a.b)|c| + (a.c)|b| +
+ * (b.c)|a|), a, b, c the vertices relative to X).  1 inside a closed
+ * outward-oriented surface, 0 outside (a textbook check for the normalized
+ * flux of Sec. 4.2).
+ */
+void oracle_solid_angle_degree(int64_t nf, const double *V, const int64_t *F, int64_t nX, const double *X,
+                               double *deg) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nX; ++i) {
+        const double *x = X + 3 * i;
+        double tot = 0.0;
+        for (int64_t k = 0; k < nf; ++k) {
+            double p[3][3], l[3];
+            for (int v = 0; v < 3; ++v) {
+                const double *q = V + 3 * F[3 * k + v];
+                for (int a = 0; a < 3; ++a) p[v][a] = q[a] - x[a];
+                l[v] = sqrt(p[v][0] * p[v][0] + p[v][1] * p[v][1] + p[v][2] * p[v][2]);
+            }
+            const double triple = p[0][0] * (p[1][1] * p[2][2] - p[1][2] * p[2][1]) -
+                                  p[0][1] * (p[1][0] * p[2][2] - p[1][2] * p[2][0]) +
+                                  p[0][2] * (p[1][0] * p[2][1] - p[1][1] * p[2][0]);
+            const double d01 = p[0][0] * p[1][0] + p[0][1] * p[1][1] + p[0][2] * p[1][2];
+            const double d02 = p[0][0] * p[2][0] + p[0][1] * p[2][1] + p[0][2] * p[2][2];
+            const double d12 = p[1][0] * p[2][0] + p[1][1] * p[2][1] + p[1][2] * p[2][2];
+            const double den = l[0] * l[1] * l[2] + d01 * l[2] + d02 * l[1] + d12 * l[0];
+            tot += 2.0 * atan2(triple, den);
+        }
+        deg[i] = tot / (4.0 * ORACLE_PI);
+    }
+}

@@ -230,3 +230,87 @@ def config_c3():
 def config_c5():
     """3D differentiation: 128^3 grid, K=20000 jittered sphere points."""
     return jittered_sphere(N=128, K=20000, radius=0.3, sigma=0.01, tau=0.01, seed=5)
+
+
+# ---------------------------------------------------------------- triangle meshes
+# Closed, outward-wound (counter-clockwise seen from outside) triangle meshes of
+# the Example 5 objects: a sphere, a cube and a capped cylinder.  Geometry only:
+# the sources (incentres, normals) are the method's job.
+
+def mesh_sphere(center=(0.5, 0.5, 0.5), r=0.3, n_lat=24, n_lon=48):
+    """UV sphere: (V, F) with F int64 vertex indices."""
+    c = np.asarray(center, float)
+    V = [c + [0, 0, r], c - [0, 0, r]]
+    for i in range(1, n_lat):
+        th = np.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2 * np.pi * j / n_lon
+            V.append(c + r * np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)]))
+    V = np.array(V)
+
+    def ring(i, j):  # vertex of latitude ring i (1 .. n_lat-1), longitude j
+        return 2 + (i - 1) * n_lon + (j % n_lon)
+
+    F = []
+    for j in range(n_lon):
+        F.append([0, ring(1, j), ring(1, j + 1)])
+        F.append([1, ring(n_lat - 1, j + 1), ring(n_lat - 1, j)])
+    for i in range(1, n_lat - 1):
+        for j in range(n_lon):
+            a, b, cc, d = ring(i, j), ring(i, j + 1), ring(i + 1, j), ring(i + 1, j + 1)
+            F.append([a, cc, d])
+            F.append([a, d, b])
+    return V, np.array(F, dtype=np.int64)
+
+
+def mesh_cube(center=(0.5, 0.5, 0.5), half=0.25, n=8):
+    """Cube with each face cut into n x n squares of two triangles."""
+    c = np.asarray(center, float)
+    V, F = [], []
+    for axis in range(3):
+        for s in (-1.0, 1.0):
+            u, v = [a for a in range(3) if a != axis]
+            base = len(V)
+            for i in range(n + 1):
+                for j in range(n + 1):
+                    p = np.zeros(3)
+                    p[axis] = s * half
+                    p[u] = -half + 2 * half * i / n
+                    p[v] = -half + 2 * half * j / n
+                    V.append(c + p)
+            for i in range(n):
+                for j in range(n):
+                    a = base + i * (n + 1) + j
+                    b, cc, d = a + (n + 1), a + 1, a + (n + 1) + 1
+                    # (u, v, axis) right-handed when (axis+1)%3 == u; flip for the -s face
+                    tri = [[a, b, d], [a, d, cc]]
+                    right = (axis + 1) % 3 == u
+                    if (s > 0) != right:
+                        tri = [[a, d, b], [a, cc, d]]
+                    F.extend(tri)
+    return np.array(V), np.array(F, dtype=np.int64)
+
+
+def mesh_cylinder(center=(0.5, 0.5, 0.5), r=0.2, half_height=0.25, n_theta=48, n_z=12):
+    """Capped cylinder along z: side quads and triangle-fan caps."""
+    c = np.asarray(center, float)
+    V, F = [], []
+    for k in range(n_z + 1):
+        z = -half_height + 2 * half_height * k / n_z
+        for j in range(n_theta):
+            t = 2 * np.pi * j / n_theta
+            V.append(c + [r * np.cos(t), r * np.sin(t), z])
+    for k in range(n_z):
+        for j in range(n_theta):
+            a = k * n_theta + j
+            b = k * n_theta + (j + 1) % n_theta
+            cc, d = a + n_theta, b + n_theta
+            F.append([a, b, d])
+            F.append([a, d, cc])
+    bot, top = len(V), len(V) + 1
+    V.append(c + [0, 0, -half_height])
+    V.append(c + [0, 0, half_height])
+    for j in range(n_theta):
+        F.append([bot, (j + 1) % n_theta, j])
+        F.append([top, n_z * n_theta + j, n_z * n_theta + (j + 1) % n_theta])
+    return np.array(V), np.array(F, dtype=np.int64)

@@ -455,3 +455,69 @@ def test_curvature_3d_rotated_paraboloid_vertex(a, b):
         assert np.isclose(c[1], 0.5 * (1 / a + 1 / b), rtol=1e-12)
         assert np.isclose(c[0], 1 / (a * b), rtol=1e-12)
         assert np.isclose(c[2], max(1 / a, 1 / b), rtol=1e-9) and np.isclose(c[3], min(1 / a, 1 / b), rtol=1e-9)
+
+
+# ---------------------------------------------------------------- triangle meshes
+# (Sec. 4.2 and Example 5: incentres and edge-cross-product normals as sources)
+
+
+def test_mesh_sources_incentre_and_area_normal():
+    # 3-4-5 right triangle: inradius (3 + 4 - 5)/2 = 1, incentre (1, 1); area 6
+    V = np.array([[0, 0, 0], [4, 0, 0], [0, 3, 0]], float)
+    Y, P = oracle.mesh_sources(V, np.array([[0, 1, 2]]))
+    assert np.allclose(Y[0], [1, 1, 0]) and np.allclose(P[0], [0, 0, 6])
+    # reversed winding reverses the normal; the Example 5 rule (centre below
+    # the triangle) points it away from the centre either way
+    _, Pr = oracle.mesh_sources(V, np.array([[0, 2, 1]]))
+    assert np.allclose(Pr[0], [0, 0, -6])
+    _, Pc = oracle.mesh_sources(V, np.array([[0, 2, 1]]), center=[1, 1, -1])
+    assert np.allclose(Pc[0], [0, 0, 6])
+    # equilateral triangle: incentre = centroid; any triangle: the incentre is
+    # equidistant (the inradius 2 area / perimeter) from the three side lines
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        T = rng.uniform(-1, 1, size=(3, 3))
+        Y, P = oracle.mesh_sources(T, np.array([[0, 1, 2]]))
+        area = np.linalg.norm(P[0])
+        per = sum(np.linalg.norm(T[i] - T[(i + 1) % 3]) for i in range(3))
+        for i in range(3):
+            a, b = T[i], T[(i + 1) % 3]
+            e = (b - a) / np.linalg.norm(b - a)
+            w = Y[0] - a
+            dist = np.linalg.norm(w - np.dot(w, e) * e)
+            assert np.isclose(dist, 2 * area / per, rtol=1e-9)
+    E = np.array([[0, 0, 0], [1, 0, 0], [0.5, np.sqrt(3) / 2, 0]])
+    Y, _ = oracle.mesh_sources(E, np.array([[0, 1, 2]]))
+    assert np.allclose(Y[0], E.mean(axis=0))
+
+
+@pytest.mark.parametrize("kind", ["sphere", "cube", "cylinder"])
+def test_solid_angle_degree_is_the_integer_degree(kind):
+    V, F = {"sphere": wl.mesh_sphere, "cube": wl.mesh_cube, "cylinder": wl.mesh_cylinder}[kind]()
+    rng = np.random.default_rng(9)
+    X = rng.uniform(0, 1, size=(400, 3))
+    d = oracle.solid_angle_degree(V, F, X)
+    assert np.all(np.abs(d - np.round(d)) < 1e-9)
+    assert set(np.round(d).astype(int)) <= {0, 1}
+    # sources from the winding and from the Example 5 rule agree for these
+    # convex objects around their centre
+    _, P1 = oracle.mesh_sources(V, F)
+    _, P2 = oracle.mesh_sources(V, F, center=[0.5, 0.5, 0.5])
+    assert np.allclose(P1, P2)
+    # total area-weighted normal of a closed surface vanishes
+    assert np.abs(P1.sum(axis=0)).max() < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["sphere", "cube"])
+def test_normalized_flux_of_mesh_sources_approaches_the_degree(kind):
+    # eq. normflux with incentres and area normals is a quadrature of the
+    # solid angle: away from the surface it is within a few percent of it
+    V, F = {"sphere": wl.mesh_sphere, "cube": wl.mesh_cube}[kind]()
+    Y, P = oracle.mesh_sources(V, F)
+    rng = np.random.default_rng(10)
+    X = rng.uniform(0, 1, size=(300, 3))
+    far = np.min(np.linalg.norm(X[:, None, :] - Y[None, :, :], axis=2), axis=1) > 0.08
+    mu = oracle.evaluate(Y, X[far], 0.01, weights=P, want=("mu",))["mu"]
+    d = oracle.solid_angle_degree(V, F, X[far])
+    assert np.abs(mu - d).max() < 0.05
+    assert np.array_equal(oracle.sign_from_mu(mu), np.where(d > 0.5, 1, -1).astype(np.int8))
