@@ -199,6 +199,29 @@ sdf_status sdf_backward(sdf_plan plan, int64_t K, const double *points,
                         const uint8_t *flags, double *dL_dY, double *dL_dtau);
 
 /*
+ * sdf_mesh_sources -- point sources of an oriented triangle mesh for the 3D
+ * degree (Sec. 4.2, Example 5): triangle k becomes the point Y_k = its
+ * incentre (vertices weighted by the opposite side lengths) with the weight
+ * P_k = (B - A) x (C - A) / 2, the edge cross product scaled to the
+ * triangle's area (area-weighted outward normal, so mu ~ 1 inside).
+ *   nf, nv     triangles and vertices.
+ *   V          device, nv x 3 doubles (world coordinates, as points).
+ *   F          device, nf x 3 int64 vertex indices (A, B, C).
+ *   center     host, 3 doubles, or NULL.  NULL: the faces' vertex order
+ *              orients P_k (counter-clockwise seen from outside = outward).
+ *              Given: P_k is negated where <Y_k - center, P_k> < 0 (the rule
+ *              of Example 5, for objects star-shaped about center).
+ *   points, weights  device, nf x 3 doubles each (caller-owned): pass them
+ *              to sdf_execute as points and weights.
+ * 3D plans only (SDF_ERR_UNSUPPORTED otherwise); a face index outside
+ * [0, nv) sets SDF_ERR_INVALID_ARG, reported by sdf_sync.  Enqueued on the
+ * plan's stream.
+ */
+sdf_status sdf_mesh_sources(sdf_plan plan, int64_t nf, int64_t nv, const double *V,
+                            const int64_t *F, const double *center, double *points,
+                            double *weights);
+
+/*
  * sdf_curvature -- curvature fields from the grad S and Hessian planes an
  * sdf_execute wrote (Sec. 5: the derivatives give "derived quantities such as
  * curvature (Gaussian, mean and principal curvatures)" of the surface S(X)).

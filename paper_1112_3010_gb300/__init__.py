@@ -32,7 +32,8 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_last_error", "sdf_profile_enable", "sdf_profile_read",
             "sdf_plan_set_noise_constants", "sdf_execute_noalloc", "sdf_batch_create",
             "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy",
-            "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature", "sdf_plan_set_full_range"]
+            "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature", "sdf_plan_set_full_range",
+            "sdf_mesh_sources"]
 
 
 class SDFError(RuntimeError):
@@ -91,6 +92,7 @@ def load_library(path: str | None = None):
         L.sdf_backward.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         L.sdf_curvature.argtypes = [vp, vp, vp, vp, vp]
         L.sdf_plan_set_full_range.argtypes = [vp, ctypes.c_int]
+        L.sdf_mesh_sources.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
         L.sdf_sync.argtypes = [vp]
         L.sdf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         L.sdf_get_stats.argtypes = [vp, ctypes.POINTER(ExecStats)]
@@ -127,7 +129,7 @@ def load_library(path: str | None = None):
         L.sdf_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), ctypes.c_int]
         L.sdf_profile_read.restype = ctypes.c_int
         for n in ("sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
-                  "sdf_plan_get_info", "sdf_get_stats", "sdf_curvature", "sdf_plan_set_full_range"):
+                  "sdf_plan_get_info", "sdf_get_stats", "sdf_curvature", "sdf_plan_set_full_range", "sdf_mesh_sources"):
             getattr(L, n).restype = ctypes.c_int
         _LIBH = L
         return L
@@ -176,6 +178,15 @@ def sdf_backward(handle, K, points, w, S_saved, flags, dL_dY, dL_dtau):
 
 def sdf_plan_set_full_range(handle, enable):
     _ck(_lib().sdf_plan_set_full_range(handle, 1 if enable else 0), "sdf_plan_set_full_range")
+
+
+def sdf_mesh_sources(handle, nf, nv, V, F, center, points, weights):
+    c = None
+    if center is not None:
+        c = (ctypes.c_double * 3)(*[float(x) for x in center])
+    _ck(_lib().sdf_mesh_sources(handle, int(nf), int(nv), _ptr(V), _ptr(F),
+                                ctypes.cast(c, ctypes.c_void_p) if c is not None else None,
+                                _ptr(points), _ptr(weights)), "sdf_mesh_sources")
 
 
 def sdf_curvature(handle, dS, d2S, flags, curv):
@@ -386,6 +397,18 @@ class Plan:
         sdf_execute_host(self.handle, pts.shape[0], pts, w, out.get("S"), out.get("dS"),
                          out.get("d2S"), out.get("sign"), out.get("flags"))
         return out
+
+    def mesh_sources(self, V, F, center=None):
+        """Incentres and area-weighted normals (device, nf x 3 each) of a
+        triangle mesh (V: nv x 3, F: nf x 3 int64) for execute()."""
+        t = self.torch
+        Vd = V.to(device="cuda", dtype=t.float64).contiguous()
+        Fd = F.to(device="cuda", dtype=t.int64).contiguous()
+        pts = t.empty((Fd.shape[0], 3), dtype=t.float64, device="cuda")
+        w = t.empty_like(pts)
+        sdf_mesh_sources(self.handle, Fd.shape[0], Vd.shape[0], Vd, Fd, center, pts, w)
+        self.sync()
+        return pts, w
 
     def curvature(self, out):
         """Gaussian, mean and principal curvatures (4, *grid) from an execute's
