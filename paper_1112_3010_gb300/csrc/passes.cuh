@@ -692,13 +692,21 @@ constexpr size_t kSmemBudget = 200 * 1024;
 // Lines per CTA of a transposed pass: the plan's tuning when set and valid,
 // else pick_R.
 template <typename T>
-static inline int tuned_R(const sdf_plan_impl *p, int logL) {
-    const int def = pick_R(logL, sizeof(cx<T>), max_threads<T>(), 16, kSmemBudget);
+static inline int tuned_R(const sdf_plan_impl *p, int logL, int maxthr = max_threads<T>()) {
+    const int def = pick_R(logL, sizeof(cx<T>), maxthr, 16, kSmemBudget);
     if (!p || p->tune_RT <= 0) return def;
     const int TPL = (1 << logL) >> 4;
     int R = p->tune_RT;
-    while (R > 1 && (R * TPL > max_threads<T>() || line_smem(R, 1 << logL, (int)sizeof(cx<T>)) > kSmemBudget)) R >>= 1;
+    while (R > 1 && (R * TPL > maxthr || line_smem(R, 1 << logL, (int)sizeof(cx<T>)) > kSmemBudget)) R >>= 1;
     return R;
+}
+
+// The x-pass may run 1024-thread CTAs for float lines of a compile-time
+// length (those variants fit 64 registers): four 4096-point lines per CTA
+// write whole 32-byte sectors of the transposed output.
+template <typename T>
+static inline int xpass_max_threads(int logL) {
+    return (sizeof(T) == 4 && logL >= 8 && logL <= 12) ? 1024 : max_threads<T>();
 }
 
 // Launch kern<T, 512, LG> (nthr <= 512).  Needs `cudaError_t e` in scope.

@@ -39,7 +39,8 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
     // ---- x-pass
     {
         const int logL = p->logM[0];
-        const int R = dense_in ? pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget) : tuned_R<T>(p, logL);
+        const int R = dense_in ? pick_R(logL, sizeof(V), max_threads<T>(), 16, kSmemBudget)
+                               : tuned_R<T>(p, logL, xpass_max_threads<T>(logL));
         LineCfg c = line_cfg(logL, R);
         const int64_t n_lines = N1 * (D == 3 ? N2 : 1);
         const size_t smem = line_smem(R, c.L, (int)sizeof(V));
@@ -59,12 +60,26 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
             prof_end(p, st);
         } else {
             prof_begin(p, "xpass", st);
-#define SDF_XC(LG)                                                                                        \
-    SDF_LAUNCH_MT(k_xpass_cells, T, LG, R * c.TPL, grid, smem, st, p->bin_start, p->bin_nuniq, p->ucell, \
-                  p->ucount, p->uw, (int)N1, (int)p->nb[0], (int)p->nb[1], logL, R, nfield, n_lines, A,  \
-                  M0 * n_lines, tw0)
+#define SDF_XC_MT(MTT, LG)                                                                                \
+    do {                                                                                                  \
+        if ((e = set_smem<T>((const void *)k_xpass_cells<T, MTT, LG>, smem)) != cudaSuccess) return e;   \
+        k_xpass_cells<T, MTT, LG><<<(unsigned)grid, R * c.TPL, smem, st>>>(                              \
+            p->bin_start, p->bin_nuniq, p->ucell, p->ucount, p->uw, (int)N1, (int)p->nb[0], (int)p->nb[1], \
+            logL, R, nfield, n_lines, A, M0 * n_lines, tw0);                                              \
+    } while (0)
+#define SDF_XC(LG)                                              \
+    do {                                                        \
+        if constexpr (LG > 0) {                                 \
+            if (R * c.TPL > 512) {                              \
+                SDF_XC_MT(1024, LG);                            \
+                break;                                          \
+            }                                                   \
+        }                                                       \
+        SDF_XC_MT(512, LG);                                     \
+    } while (0)
             SDF_BY_LOGL(T, logL, SDF_XC);
 #undef SDF_XC
+#undef SDF_XC_MT
             prof_end(p, st);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
