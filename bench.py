@@ -5,7 +5,9 @@ padded to 4096^2), K = 40000 points sampled along 8 seeded non-intersecting
 star polygons with chord tangents, tau in {0.002, 0.0005}; outputs S (signed),
 grad S, Hessian and sign.  One step = one execute per tau value.  Inputs are
 resident in HBM before the timed region; L2 is flushed (256 MiB write) between
-timed steps, outside the CUDA-event brackets.
+timed steps, outside the CUDA-event brackets.  The two problems of a step are
+independent: each plan has its own stream, forked from and joined back to the
+timing stream, so they run concurrently (the FP64 path the same way).
 
 Also reported: the same metric through sdf_execute_host (host buffers, copies
 inside the timed region), the plain FP64 GPU path with max|S - S_FP64| over its
@@ -223,10 +225,13 @@ def main():
     pkg.load_library()
     stream = torch.cuda.Stream()
     shapes = workloads()
+    # one stream per problem: the two executes of a step run concurrently (one
+    # problem's ALU-bound fix-up overlaps the other's memory-bound passes)
+    pstreams = [torch.cuda.Stream() for _ in shapes]
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         plans = [pkg.Plan(2, s.dims, s.h, s.tau, precision="fp32", outputs=("S", "dS", "d2S", "sign"),
-                          stream=stream) for s in shapes]
+                          stream=ps) for s, ps in zip(shapes, pstreams)]
         pts = [torch.from_numpy(s.points).cuda() for s in shapes]
         wts = [torch.from_numpy(s.weights).cuda() for s in shapes]
         outs = [p.alloc_outputs(["S", "dS", "d2S", "sign", "flags"]) for p in plans]
@@ -238,18 +243,34 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
-    def step():
-        for p, x, w, o in zip(plans, pts, wts, outs):
-            pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], o["flags"])
+    def fork_join(run, main, streams):
+        """run() enqueues on `streams` after everything already on `main`;
+        `main` then waits for all of them."""
+        fork = torch.cuda.Event()
+        fork.record(main)
+        for st in streams:
+            st.wait_event(fork)
+        run()
+        for st in streams:
+            main.wait_stream(st)
+
+    def step(serial=False):
+        def run():
+            for p, x, w, o in zip(plans, pts, wts, outs):
+                pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], o["flags"])
+        if not serial:
+            fork_join(run, stream, pstreams)
+            return
+        # one problem at a time (the kernel-timing pass)
+        for p, x, w, o, ps in zip(plans, pts, wts, outs, pstreams):
+            fork_join(lambda: pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"],
+                                              o["flags"]), stream, [ps])
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
     for p in plans:
         p.sync()
-    for p in plans:
-        p.profile(True)
-        p.profile_read()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = Clocks()
     if dist:
@@ -279,6 +300,17 @@ def main():
         total_ms = float(t.item())
     pts_per_step = sum(s.n_nodes for s in shapes)
     value = world * pts_per_step * args.steps / (total_ms * 1e-3)
+    # kernel times: the same steps again, the two problems one after the
+    # other so that each kernel's CUDA-event duration is its own (events on
+    # the stream each kernel runs on)
+    for p in plans:
+        p.profile(True)
+        p.profile_read()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            step(serial=True)
+    torch.cuda.synchronize()
     prof = {}
     per_plan = []
     for p in plans:
@@ -337,9 +369,16 @@ def main():
         hp = [torch.from_numpy(s.points).pin_memory() for s in shapes]
         hw = [torch.from_numpy(s.weights).pin_memory() for s in shapes]
 
+        import concurrent.futures as cf
+        pool = cf.ThreadPoolExecutor(len(plans))
+
         def host_step():
-            for p, x, w, o in zip(plans, hp, hw, host_out):
-                pkg.sdf_execute_host(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], None)
+            # the public call is synchronous: one host thread per problem
+            # (ctypes releases the GIL) so the two run concurrently
+            futs = [pool.submit(pkg.sdf_execute_host, p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"],
+                                o["sign"], None) for p, x, w, o in zip(plans, hp, hw, host_out)]
+            for f in futs:
+                f.result()
 
         for _ in range(2):
             host_step()
@@ -358,12 +397,15 @@ def main():
     if args.fp64_steps > 0:
         with torch.cuda.stream(stream):
             p64 = [pkg.Plan(2, s.dims, s.h, s.tau, precision="fp64", outputs=("S", "dS", "d2S", "sign"),
-                            stream=stream) for s in shapes]
+                            stream=ps) for s, ps in zip(shapes, pstreams)]
             o64 = [p.alloc_outputs(["S", "dS", "d2S", "sign", "flags"]) for p in p64]
+        torch.cuda.synchronize()
 
         def step64():
-            for p, x, w, o in zip(p64, pts, wts, o64):
-                pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], o["flags"])
+            def run():
+                for p, x, w, o in zip(p64, pts, wts, o64):
+                    pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], o["flags"])
+            fork_join(run, stream, pstreams)
 
         with torch.cuda.stream(stream):
             step64()
@@ -412,6 +454,9 @@ def main():
                        "K": K_PTS, "taus": list(TAUS), "outputs": "S,dS,d2S,sign,flags",
                        "precision": "mixed (fp32 FFT + shifted direct-sum fix-up)",
                        "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "concurrency": "the two problems (one per tau) run on two streams of one GPU; "
+                                      "kernel times and rooflines from a second pass of the same steps "
+                                      "run one problem at a time",
                        "tile_schedule": [{"lines_T": a, "lines_F": b, "fused_variant": c} for a, b, c in tuning]},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "kernels": per_kernel, "fft_passes": passes, "fp64_path": fp64,
