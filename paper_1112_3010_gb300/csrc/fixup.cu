@@ -124,8 +124,10 @@ template <int D> __device__ __forceinline__ constexpr int sym_index(int a, int b
     return a * D - a * (a - 1) / 2 + (b - a);
 }
 
-template <int D, typename TO>
-__global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 2) k_fixup(FixParams P) {
+// LVL: 0 = S only, 1 = S and grad S, 2 = S, grad S and the Hessian (only the
+// sums the requested outputs need are accumulated).
+template <int D, typename TO, int LVL>
+__global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : (LVL == 2 ? 2 : 3)) k_fixup(FixParams P) {
     constexpr int TB = (D == 2) ? kTB2 : 1;  // tile edge in bins
     constexpr int NT = (D == 2) ? 32 * kTB2 * kTB2 : 256;
     constexpr int NH = D * (D + 1) / 2;
@@ -396,18 +398,22 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
                         const float ir = fminf(rsqrt_approx(r2), r2);
                         const float rg = r2 * ir;
                         const float E = q.w * ex2_approx(fmaf(-rg, l2e_th, mk[j]));
-                        const float Eir = E * ir;
-                        const float F = Eir * ir * fmaf(ir, ih, itau);
                         sE[j] += E;
-                        sA[j] += Eir;
+                        if constexpr (LVL >= 1) {
+                            const float Eir = E * ir;
 #pragma unroll
-                        for (int a = 0; a < D; ++a) sG[j][a] = fmaf(Eir, d[a], sG[j][a]);
-                        int qh = 0;
+                            for (int a = 0; a < D; ++a) sG[j][a] = fmaf(Eir, d[a], sG[j][a]);
+                            if constexpr (LVL >= 2) {
+                                const float F = Eir * ir * fmaf(ir, ih, itau);
+                                sA[j] += Eir;
+                                int qh = 0;
 #pragma unroll
-                        for (int a = 0; a < D; ++a) {
-                            const float Fd = F * d[a];
+                                for (int a = 0; a < D; ++a) {
+                                    const float Fd = F * d[a];
 #pragma unroll
-                            for (int bb = a; bb < D; ++bb, ++qh) sB[j][qh] = fmaf(Fd, d[bb], sB[j][qh]);
+                                    for (int bb = a; bb < D; ++bb, ++qh) sB[j][qh] = fmaf(Fd, d[bb], sB[j][qh]);
+                                }
+                            }
                         }
                     }
                 }
@@ -482,6 +488,10 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
         }
         ++fixed;
         if (So) So[nd] = (TO)(sg * S);
+        if constexpr (LVL == 0) {
+            P.flags[nd] = SDF_FLAG_FIXUP;
+            continue;
+        }
         const float inv = 1.f / sE[j];
         float g[D];
 #pragma unroll
@@ -489,7 +499,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 4 : 
             g[a] = sG[j][a] * inv;
             if (dS) dS[a * P.nnodes + nd] = (TO)g[a];
         }
-        if (d2S) {
+        if (LVL >= 2 && d2S) {
             // sB is stored row by row (xx, xy, [xz,] yy, ...); d2S is
             // diagonal first, then the pairs a < b
             const float Ad = sA[j] * ih * inv;
@@ -555,12 +565,21 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS
     F.log_coef64 = (float)log(F.coef64);
     F.full = p->full_range ? 1 : 0;
     prof_begin(p, "fixup", p->stream);
-    if (D == 2) {
-        const int64_t nt = ((p->nb[0] + kTB2 - 1) / kTB2) * ((p->nb[1] + kTB2 - 1) / kTB2);
-        k_fixup<2, float><<<(unsigned)nt, 32 * kTB2 * kTB2, 0, p->stream>>>(F);
-    } else {
-        k_fixup<3, float><<<(unsigned)p->nbins, 256, 0, p->stream>>>(F);
-    }
+    // only the derivatives the caller asked for are summed
+    const int lvl = d2S ? 2 : (dS ? 1 : 0);
+#define SDF_FIX(DD, LV)                                                                          \
+    do {                                                                                         \
+        if (DD == 2) {                                                                           \
+            const int64_t nt = ((p->nb[0] + kTB2 - 1) / kTB2) * ((p->nb[1] + kTB2 - 1) / kTB2);  \
+            k_fixup<2, float, LV><<<(unsigned)nt, 32 * kTB2 * kTB2, 0, p->stream>>>(F);           \
+        } else {                                                                                 \
+            k_fixup<3, float, LV><<<(unsigned)p->nbins, 256, 0, p->stream>>>(F);                  \
+        }                                                                                        \
+    } while (0)
+    if (lvl == 2) SDF_FIX(D, 2);
+    else if (lvl == 1) SDF_FIX(D, 1);
+    else SDF_FIX(D, 0);
+#undef SDF_FIX
     prof_end(p, p->stream);
     return cudaGetLastError();
 }
