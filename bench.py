@@ -40,6 +40,24 @@ TAUS = (0.002, 0.0005)
 WORKLOAD = "2D mixed precision: 2048^2 grid padded to 4096^2, K=40000 on 8 star polygons, tau in {0.002, 0.0005}"
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of a per-rank number over all ranks: the replicas start
+    together (barrier) and the job ends when the slowest one does."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_step, steps, seconds):
+    """Whole-job throughput of `world` replicas, each processing
+    `units_per_step` units per step for `steps` steps, the job taking
+    `seconds` (the max over ranks)."""
+    return world * units_per_step * steps / seconds
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -294,12 +312,9 @@ def main():
     clk = clocks.stop(local)
     ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, device="cuda")
     pts_per_step = sum(s.n_nodes for s in shapes)
-    value = world * pts_per_step * args.steps / (total_ms * 1e-3)
+    value = job_throughput(world, pts_per_step, args.steps, total_ms * 1e-3)
     # kernel times: the same steps again, the two problems one after the
     # other so that each kernel's CUDA-event duration is its own (events on
     # the stream each kernel runs on)
@@ -383,13 +398,15 @@ def main():
         for _ in range(2):
             host_step()
         n_e2e = max(3, args.steps // 2)
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             host_step()
-        el = time.perf_counter() - t0
+        el = max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
         h2d = sum(2 * s.K * 2 * 8 for s in shapes)
         d2h = sum(s.n_nodes * (4 * 6 + 1) for s in shapes)
-        e2e = {"value": world * pts_per_step * n_e2e / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_throughput(world, pts_per_step, n_e2e, el), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * el / n_e2e}
 
     # the plain FP64 GPU path on the same workload, and max|S - S_FP64|
