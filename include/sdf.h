@@ -68,6 +68,9 @@ typedef enum {
 
 typedef enum { SDF_FP64 = 0, SDF_FP32 = 1 } sdf_precision;
 
+/* Kernel sets (sdf_plan_set_kernel). */
+typedef enum { SDF_KERNEL_EXP = 0, SDF_KERNEL_GREEN = 1 } sdf_kernel_set;
+
 /* Output fields a plan prepares kernel spectra for (bit mask). */
 enum {
     SDF_OUT_S = 1,    /* S (always computed)                               */
@@ -296,6 +299,48 @@ sdf_status sdf_plan_autotune(sdf_plan plan, int64_t K, const double *points,
  * (they have no fix-up); SDF_ERR_INVALID_ARG for a NULL plan.
  */
 sdf_status sdf_plan_set_full_range(sdf_plan plan, int enable);
+
+/*
+ * sdf_plan_set_kernel -- choose the kernel phi is convolved from.
+ *   SDF_KERNEL_EXP    exp(-||o||/tau): the paper's G~ (eq. GTildeDefinition)
+ *                     with its constants dropped (eq. wavefunc).  The default.
+ *   SDF_KERNEL_GREEN  the exact Green's function of -tau^2 lap phi + phi =
+ *                     psi (Sec. 2.1: K_0(r/tau)/(2 pi tau^2) in 2D, eq.
+ *                     GreensFunction2D; exp(-r/tau)/(4 pi tau^2 r) in 3D, eq.
+ *                     GreensFunction3D), scaled as in eq. phiapproxSol with
+ *                     gamma = D/2 (psi_k = tau^-D/2 on a box of side tau,
+ *                     Sec. 2.2): g(o) = tau^-D/2 c_D Gamma_D(||o||/tau), see
+ *                     sdf_green_profile.  At o = 0, where the mid-point value
+ *                     is infinite, g is the integral of tau^-D/2 G over the
+ *                     source's box, tau^-D/2 c_D A_D.  S = -tau log phi keeps
+ *                     the constants, so S tends to R only as tau -> 0
+ *                     (App. A); grad S, the Hessian and the sign are computed
+ *                     as for SDF_KERNEL_EXP from the matching derivative
+ *                     kernels.
+ * Rebuilds the plan's kernel spectra (synchronous, allocates).  Errors:
+ * SDF_ERR_INVALID_ARG for a NULL plan or an unknown set; SDF_ERR_UNSUPPORTED
+ * for SDF_KERNEL_GREEN on an SDF_FP32 plan (its fix-up sums exp(-r/tau)
+ * terms) or on a plan of a batch.  sdf_backward on a plan with
+ * SDF_KERNEL_GREEN returns SDF_ERR_UNSUPPORTED (the adjoint is derived for
+ * exp(-r/tau)).  Call between executes, not while one is in flight.
+ */
+sdf_status sdf_plan_set_kernel(sdf_plan plan, int kernel_set);
+
+/*
+ * sdf_green_profile -- host only, no device work: the radial profile of the
+ * exact Green's function set in the unit z = r/tau, G = tau^-D c_D Gamma_D(z)
+ * (c_1 = 1/2, c_2 = 1/(2 pi), c_3 = 1/(4 pi); Gamma_1 = exp(-z),
+ * Gamma_2 = K_0(z), Gamma_3 = exp(-z)/z; Sec. 2.1).
+ *   D         1, 2 or 3.
+ *   n, z      n host values z >= 0.
+ *   g, g1, g2 host arrays of n: Gamma_D(z), Gamma_D'(z), Gamma_D''(z).  For
+ *             z = 0: g = A_D (the integral of Gamma_D over [-1/2, 1/2]^D,
+ *             from the divergence theorem; 1 for D = 1) and g1 = g2 = 0.
+ * SDF_ERR_INVALID_ARG for D outside 1..3, NULL arrays with n > 0, or a z that
+ * is negative or not finite (the arrays are then partly written).
+ */
+sdf_status sdf_green_profile(int D, int64_t n, const double *z, double *g,
+                             double *g1, double *g2);
 
 /*
  * sdf_profile_enable -- when enable != 0, every kernel the plan launches is

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libsdf_gb300.so")
 SDF_FP64, SDF_FP32 = 0, 1
 SDF_OUT_S, SDF_OUT_DS, SDF_OUT_D2S, SDF_OUT_SIGN = 1, 2, 4, 8
 SDF_FLAG_CAPPED, SDF_FLAG_FIXUP, SDF_FLAG_SOURCE = 1, 2, 4
+SDF_KERNEL_EXP, SDF_KERNEL_GREEN = 0, 1
 STATUS = {0: "SDF_OK", 1: "SDF_ERR_INVALID_ARG", 2: "SDF_ERR_UNSUPPORTED",
           3: "SDF_ERR_POINT_OUT_OF_GRID", 4: "SDF_ERR_OOM", 5: "SDF_ERR_CUDA",
           6: "SDF_ERR_TIMEOUT", 7: "SDF_ERR_CAPACITY"}
@@ -33,7 +34,7 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_plan_set_noise_constants", "sdf_execute_noalloc", "sdf_batch_create",
             "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy",
             "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature", "sdf_plan_set_full_range",
-            "sdf_mesh_sources"]
+            "sdf_mesh_sources", "sdf_plan_set_kernel", "sdf_green_profile"]
 
 
 class SDFError(RuntimeError):
@@ -92,6 +93,8 @@ def load_library(path: str | None = None):
         L.sdf_backward.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         L.sdf_curvature.argtypes = [vp, vp, vp, vp, vp]
         L.sdf_plan_set_full_range.argtypes = [vp, ctypes.c_int]
+        L.sdf_plan_set_kernel.argtypes = [vp, ctypes.c_int]
+        L.sdf_green_profile.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp]
         L.sdf_mesh_sources.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
         L.sdf_sync.argtypes = [vp]
         L.sdf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
@@ -129,7 +132,8 @@ def load_library(path: str | None = None):
         L.sdf_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), ctypes.c_int]
         L.sdf_profile_read.restype = ctypes.c_int
         for n in ("sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
-                  "sdf_plan_get_info", "sdf_get_stats", "sdf_curvature", "sdf_plan_set_full_range", "sdf_mesh_sources"):
+                  "sdf_plan_get_info", "sdf_get_stats", "sdf_curvature", "sdf_plan_set_full_range", "sdf_mesh_sources",
+                  "sdf_plan_set_kernel", "sdf_green_profile"):
             getattr(L, n).restype = ctypes.c_int
         _LIBH = L
         return L
@@ -178,6 +182,21 @@ def sdf_backward(handle, K, points, w, S_saved, flags, dL_dY, dL_dtau):
 
 def sdf_plan_set_full_range(handle, enable):
     _ck(_lib().sdf_plan_set_full_range(handle, 1 if enable else 0), "sdf_plan_set_full_range")
+
+
+def sdf_plan_set_kernel(handle, kernel_set):
+    _ck(_lib().sdf_plan_set_kernel(handle, int(kernel_set)), "sdf_plan_set_kernel")
+
+
+def sdf_green_profile(D, z):
+    """Gamma_D(z), Gamma_D'(z), Gamma_D''(z) of the Green's function set (host
+    arrays; see include/sdf.h)."""
+    z = np.ascontiguousarray(z, dtype=np.float64).ravel()
+    g, g1, g2 = (np.empty_like(z) for _ in range(3))
+    vp = ctypes.c_void_p
+    _ck(_lib().sdf_green_profile(int(D), z.size, vp(z.ctypes.data), vp(g.ctypes.data), vp(g1.ctypes.data),
+                                 vp(g2.ctypes.data)), "sdf_green_profile")
+    return g, g1, g2
 
 
 def sdf_mesh_sources(handle, nf, nv, V, F, center, points, weights):
@@ -296,13 +315,14 @@ def sdf_plan_destroy(handle):
 
 # ---------------------------------------------------------------- convenience
 _OUTS = {"S": SDF_OUT_S, "dS": SDF_OUT_DS, "d2S": SDF_OUT_D2S, "sign": SDF_OUT_SIGN}
+_KERNELS = {"exp": SDF_KERNEL_EXP, "green": SDF_KERNEL_GREEN}
 
 
 class Plan:
     """A plan for one grid (D, dims, h) and tau, on the current torch stream."""
 
     def __init__(self, D, dims, h, tau, precision="fp32", outputs=("S", "dS", "sign"), stream=None,
-                 full_range=False):
+                 full_range=False, kernel="exp"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -324,6 +344,13 @@ class Plan:
         self.n_nodes = int(np.prod(self.dims))
         if full_range:
             sdf_plan_set_full_range(self.handle, True)
+        if kernel != "exp":
+            self.set_kernel(kernel)
+
+    def set_kernel(self, kernel):
+        """'exp' (the paper's G~, default) or 'green' (the exact Green's
+        function, SDF_FP64 plans)."""
+        sdf_plan_set_kernel(self.handle, _KERNELS[kernel])
 
     def close(self):
         if getattr(self, "handle", None) is not None:

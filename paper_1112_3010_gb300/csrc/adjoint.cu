@@ -24,7 +24,6 @@ namespace sdf {
 cudaError_t launch_adjoint_transforms(sdf_plan_impl *p, const void *w, const void *S_saved, const uint8_t *flags);
 cudaError_t build_kernel_list(sdf_plan_impl *p, const std::vector<int> &ids);
 
-constexpr int kAdjParts = 1024;  // blocks of each reduction (fixed: deterministic sums)
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_wsum(const T *__restrict__ w, const T *__restrict__ S,

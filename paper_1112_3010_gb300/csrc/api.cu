@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "green.cuh"
 #include "sdf_internal.cuh"
 
 namespace sdf {
@@ -648,6 +649,55 @@ sdf_status sdf_plan_set_full_range(sdf_plan p, int enable) {
     return SDF_OK;
 }
 
+sdf_status sdf_plan_set_kernel(sdf_plan p, int kernel_set) {
+    if (!p || (kernel_set != SDF_KERNEL_EXP && kernel_set != SDF_KERNEL_GREEN)) return SDF_ERR_INVALID_ARG;
+    if (kernel_set == p->kernel_set) return SDF_OK;
+    if (kernel_set == SDF_KERNEL_GREEN && p->prec != SDF_FP64) {
+        set_last_error("sdf_plan_set_kernel: the Green's function set needs an SDF_FP64 plan");
+        return SDF_ERR_UNSUPPORTED;
+    }
+    if (p->shares_spectra) {
+        set_last_error("sdf_plan_set_kernel: the plan uses spectra owned by another plan of its batch");
+        return SDF_ERR_UNSUPPORTED;
+    }
+    CK(cudaStreamSynchronize(p->stream));
+    // drop every spectrum (forward and adjoint) and the adjoint programme
+    for (auto &k : p->kernels) {
+        cudaFree(k.c);
+        const int64_t esz = (p->prec == SDF_FP64) ? 8 : 4;
+        p->workspace_bytes -= esz * spec_rows(p) * spec_row_len(p);
+    }
+    p->kernels.clear();
+    for (int i = 0; i < KER_COUNT; ++i) p->kslot[i] = -1;
+    if (p->adj_ngroup > 0) {
+        const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
+        cudaFree(p->adj_planes);
+        cudaFree(p->adj_part);
+        p->adj_planes = nullptr;
+        p->adj_part = nullptr;
+        p->workspace_bytes -= esz * (p->D + 1) * p->nnodes + sizeof(double) * 2 * kAdjParts;
+        p->adj_ngroup = 0;
+    }
+    p->kernel_set = kernel_set;
+    CK(build_kernel_list(p, plan_kernel_ids(p)));
+    plan_programme(p);
+    return SDF_OK;
+}
+
+sdf_status sdf_green_profile(int D, int64_t n, const double *z, double *g, double *g1, double *g2) {
+    if (D < 1 || D > 3 || n < 0 || (n > 0 && (!z || !g || !g1 || !g2))) return SDF_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(z[i] >= 0.0) || !std::isfinite(z[i])) return SDF_ERR_INVALID_ARG;
+        if (z[i] == 0.0) {
+            g[i] = green_origin_integral(D);
+            g1[i] = g2[i] = 0.0;
+        } else {
+            green_profile(D, z[i], &g[i], &g1[i], &g2[i]);
+        }
+    }
+    return SDF_OK;
+}
+
 // Device time of the named kernels over `reps` executes (after one warm-up).
 static sdf_status time_kernels(sdf_plan p, int64_t K, const double *points, const double *weights, int reps,
                                const char *const *names, int nnames, double *ms) {
@@ -755,6 +805,10 @@ void sdf_plan_destroy(sdf_plan p) {
 sdf_status sdf_backward(sdf_plan p, int64_t K, const double *points, const void *w, const void *S_saved,
                         const uint8_t *flags, double *dL_dY, double *dL_dtau) {
     if (!p || !points || !w || !S_saved || !dL_dY || !dL_dtau) return SDF_ERR_INVALID_ARG;
+    if (p->kernel_set != SDF_KERNEL_EXP) {
+        set_last_error("sdf_backward: the adjoint is derived for the exp(-r/tau) kernel set only");
+        return SDF_ERR_UNSUPPORTED;
+    }
     if (!(p->outputs & SDF_OUT_DS)) return SDF_ERR_INVALID_ARG;
     if (K < 1 || K >= (int64_t(1) << 31) - 1) return SDF_ERR_INVALID_ARG;
     CK(ensure_points(p, K));

@@ -126,6 +126,7 @@ struct sdf_plan_impl {
     // and of the fused pass, and the fused pass's register variant
     int tune_RT = 0, tune_RF = 0, tune_FV = 0;
     bool full_range = false;  // fix-up without the theta_64 cap (sdf_plan_set_full_range)
+    int kernel_set = SDF_KERNEL_EXP;  // sdf_plan_set_kernel
     // profiling
     bool prof_on = false;
     int64_t nlaunch = 0;      // kernels launched by the current/last execute
@@ -152,6 +153,7 @@ cudaError_t launch_adjoint(sdf_plan_impl *p, int64_t K, const double *points, co
                            const uint8_t *flags, double *dL_dY, double *dL_dtau);
 
 double hessian_scale(const sdf_plan_impl *p);
+double green_origin_integral(int D);  // A_D of the exact Green's function set (spectra.cu)
 
 // Compressed spectrum of one kernel: one row per folded line-axis frequency
 // (2D: f0; 3D: (f1, f0)), each row the folded last-axis frequencies padded to
@@ -174,6 +176,7 @@ int kernel_parity(int id, int D);
 void set_last_error(const char *msg);  // text returned by sdf_last_error()
 double theta_coef(const sdf_plan_impl *p, int prec);
 constexpr int kSpectraParts = 1024;
+constexpr int kAdjParts = 1024;  // blocks of each adjoint reduction (fixed: deterministic sums)
 cudaError_t build_spectra_into(sdf_plan_impl *p, double2 *bufX, double2 *bufY, double *part, double *host_part,
                                double2 *const *tw64);
 

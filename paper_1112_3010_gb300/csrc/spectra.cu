@@ -14,6 +14,15 @@
 //   RF   r E                                       (d/dtau of E, adjoint)
 // All but PHI are 0 at the origin (Sec. 4.1 sets f_c(0) = f_s(0) = f_r(0) = 0).
 //
+// Exact Green's function kernel set (green.cuh): E above becomes
+// g = P Gamma(z), z = r/tau, P = tau^-D/2 c_D, with the derivative kernels
+// -tau d_a g and -tau d_ab g, so that the epilogue's grad S = G/phi and
+// Hessian = H/phi - ... hold unchanged:
+//   PHI  P Gamma(z)                   (P A_D at the origin)
+//   G_a  -P Gamma'(z) n_a
+//   H_ab -P [Gamma''(z) n_a n_b / tau + Gamma'(z) (delta_ab - n_a n_b) / r]
+// The winding kernels do not depend on the kernel set.
+//
 // Symmetry.  A kernel odd along the axes in `parity` has a spectrum
 // (-i)^popcount(parity) * c(k) with c real, even/odd per axis like the kernel.
 // c is stored on fold(k_a) = min(k_a, M_a - k_a) in [0, M_a/2] with the 1/prod(M)
@@ -26,6 +35,7 @@
 #include <cmath>
 #include <vector>
 
+#include "green.cuh"
 #include "sdf_internal.cuh"
 
 namespace sdf {
@@ -40,7 +50,39 @@ struct SampleCfg {
     int64_t M[3], N[3];
     double h, tau;
     int id;
+    int kset;           // SDF_KERNEL_EXP or SDF_KERNEL_GREEN
+    double gP, gA;      // Green set: P = tau^-D/2 c_D and A_D (Gamma at the origin)
 };
+
+__device__ double green_kernel_value(const SampleCfg &c, const double o[3], double r, double r2) {
+    const int D = c.D;
+    const double tau = c.tau;
+    if (r == 0.0) return c.id == KER_PHI ? c.gP * c.gA : 0.0;
+    const double n[3] = {o[0] / r, o[1] / r, D == 3 ? o[2] / r : 0.0};
+    double g, g1, g2;
+    green_profile(D, r / tau, &g, &g1, &g2);
+    const double P = c.gP;
+    auto hess = [&](int a, int b) {
+        const double nn = n[a] * n[b];
+        return -P * (g2 * nn / tau + g1 * ((a == b ? 1.0 : 0.0) - nn) / r);
+    };
+    switch (c.id) {
+        case KER_PHI: return P * g;
+        case KER_GX: return -P * g1 * n[0];
+        case KER_GY: return -P * g1 * n[1];
+        case KER_GZ: return -P * g1 * n[2];
+        case KER_HXX: return hess(0, 0);
+        case KER_HYY: return hess(1, 1);
+        case KER_HZZ: return hess(2, 2);
+        case KER_HXY: return hess(0, 1);
+        case KER_HXZ: return hess(0, 2);
+        case KER_HYZ: return hess(1, 2);
+        case KER_W1: return D == 2 ? o[1] / r2 : o[0] / (r2 * r);
+        case KER_W2: return D == 2 ? o[0] / r2 : o[1] / (r2 * r);
+        case KER_W3: return o[2] / (r2 * r);
+        default: return 0.0;  // no tau-derivative kernel for this set
+    }
+}
 
 __device__ double kernel_value(const SampleCfg &c, const double o[3]) {
     const int D = c.D;
@@ -48,6 +90,7 @@ __device__ double kernel_value(const SampleCfg &c, const double o[3]) {
     for (int a = 0; a < D; ++a) r2 += o[a] * o[a];
     const double r = sqrt(r2);
     const double tau = c.tau;
+    if (c.kset == SDF_KERNEL_GREEN) return green_kernel_value(c, o, r, r2);
     if (c.id == KER_PHI) return exp(-r / tau);
     if (r == 0.0) return 0.0;
     const double E = exp(-r / tau);
@@ -153,6 +196,61 @@ static int parity_of(int id, int D) {
     }
 }
 
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n from the
+// Chebyshev guesses).
+static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double t = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double dt = p1 / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-16) break;
+        }
+        x[i] = t;
+        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+// A_D = integral of Gamma_D over [-1/2, 1/2]^D (green.cuh): c_D A_D = 1 minus
+// the outward flux of -c_D grad Gamma_D through the 2D faces; on the face
+// u_0 = 1/2, d Gamma/dn = Gamma'(r) / (2 r).  D = 1: Gamma_1(0) = 1.
+double green_origin_integral(int D) {
+    static double cache[4] = {0, 0, 0, 0};
+    if (D < 2 || D > 3) return 1.0;
+    if (cache[D] != 0.0) return cache[D];
+    std::vector<double> x, w;
+    gauss_legendre(48, x, w);
+    double flux = 0.0;  // integral over one face of Gamma'(r) / (2 r)
+    if (D == 2) {
+        for (size_t i = 0; i < x.size(); ++i) {
+            const double y = 0.5 * x[i], r = sqrt(0.25 + y * y);
+            double g, g1, g2;
+            green_profile(2, r, &g, &g1, &g2);
+            flux += 0.5 * w[i] * g1 / (2.0 * r);
+        }
+    } else {
+        for (size_t i = 0; i < x.size(); ++i)
+            for (size_t j = 0; j < x.size(); ++j) {
+                const double y = 0.5 * x[i], z = 0.5 * x[j], r = sqrt(0.25 + y * y + z * z);
+                double g, g1, g2;
+                green_profile(3, r, &g, &g1, &g2);
+                flux += 0.25 * w[i] * w[j] * g1 / (2.0 * r);
+            }
+    }
+    const double cA = 1.0 + green_cD(D) * 2.0 * D * flux;
+    cache[D] = cA / green_cD(D);
+    return cache[D];
+}
+
 cudaError_t build_spectra(sdf_plan_impl *p) {
     cudaError_t e;
     const int D = p->D;
@@ -193,6 +291,9 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
         c.h = p->h;
         c.tau = p->tau;
         c.id = ks.id;
+        c.kset = p->kernel_set;
+        c.gP = pow(p->tau, -0.5 * D) * green_cD(D);
+        c.gA = green_origin_integral(D);
         k_sample<<<nblk, 256, 0, st>>>(c, bufX, part, total);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         // D forward passes, each along the fastest axis with a rotating layout
@@ -260,6 +361,9 @@ cudaError_t build_spectra_into(sdf_plan_impl *p, double2 *bufX, double2 *bufY, d
         c.h = p->h;
         c.tau = p->tau;
         c.id = ks.id;
+        c.kset = p->kernel_set;
+        c.gP = pow(p->tau, -0.5 * D) * green_cD(D);
+        c.gA = green_origin_integral(D);
         k_sample<<<nblk, 256, 0, st>>>(c, bufX, part, total);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         double2 *src = bufX, *dst = bufY;

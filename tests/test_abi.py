@@ -74,3 +74,35 @@ def test_oracle_is_not_linked_by_the_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "sdf_oracle" not in txt, f
+
+
+def test_green_profile_host_utility():
+    """sdf_green_profile (host only) against scipy's K_0 / K_1 and the closed
+    forms of the 1D and 3D profiles; z = 0 gives the unit-box integral."""
+    import numpy as np
+    import scipy.integrate as si
+    import scipy.special as sp
+
+    import paper_1112_3010_gb300 as pkg
+    pkg.load_library()
+    z = np.concatenate([np.logspace(-8, 0, 40), np.linspace(1.0, 60.0, 200), [19.999, 20.0, 20.001, 700.0]])
+    g, g1, g2 = pkg.sdf_green_profile(2, z)
+    k0, k1 = sp.k0(z), sp.k1(z)
+    np.testing.assert_allclose(g, k0, rtol=1e-13)
+    np.testing.assert_allclose(-g1, k1, rtol=1e-13)
+    np.testing.assert_allclose(g2, k0 + k1 / z, rtol=1e-13)
+    g, g1, g2 = pkg.sdf_green_profile(3, z)
+    np.testing.assert_allclose(g, np.exp(-z) / z, rtol=1e-14)
+    np.testing.assert_allclose(g1, -np.exp(-z) * (1 / z + 1 / z ** 2), rtol=1e-14)
+    g, g1, g2 = pkg.sdf_green_profile(1, z)
+    np.testing.assert_allclose(g, np.exp(-z), rtol=1e-15)
+    # the unit-box integrals by direct adaptive quadrature of the singular integrands
+    a2 = 4 * si.dblquad(lambda y, x: sp.k0(np.hypot(x, y)), 0, 0.5, 0, 0.5, epsabs=1e-14, epsrel=1e-13)[0]
+    assert abs(pkg.sdf_green_profile(2, [0.0])[0][0] - a2) < 1e-12
+    a3 = 8 * si.tplquad(lambda c, b, a: np.exp(-np.sqrt(a * a + b * b + c * c)) / np.sqrt(a * a + b * b + c * c),
+                        0, 0.5, 0, 0.5, 0, 0.5, epsabs=1e-12, epsrel=1e-12)[0]
+    assert abs(pkg.sdf_green_profile(3, [0.0])[0][0] - a3) < 1e-10
+    with pytest.raises(pkg.SDFError):
+        pkg.sdf_green_profile(2, [-1.0])
+    with pytest.raises(pkg.SDFError):
+        pkg.sdf_green_profile(4, [1.0])
