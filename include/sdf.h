@@ -58,7 +58,8 @@ typedef struct sdf_plan_s *sdf_plan;
 typedef enum {
     SDF_OK = 0,
     SDF_ERR_INVALID_ARG = 1,       /* bad argument; nothing was enqueued        */
-    SDF_ERR_UNSUPPORTED = 2,       /* D not 2 or 3, or a grid too large         */
+    SDF_ERR_UNSUPPORTED = 2,       /* D not 1..3, a grid too large, or a        */
+                                   /* combination the plan does not support    */
     SDF_ERR_POINT_OUT_OF_GRID = 3, /* some point snapped outside [0, N_a)       */
     SDF_ERR_OOM = 4,               /* device allocation failed                  */
     SDF_ERR_CUDA = 5,              /* a CUDA runtime call failed                */
@@ -126,10 +127,14 @@ typedef struct {
 /*
  * sdf_plan_create -- build a plan for a D-dimensional grid.
  *   out        receives the plan (NULL on failure).
- *   D          2 or 3 (else SDF_ERR_UNSUPPORTED).
- *   dims       host array of D node counts, x first, each in [2, 4096] (2D) or
- *              [2, 1024] (3D); M_a (above) must fit the device (else
- *              SDF_ERR_UNSUPPORTED).
+ *   D          1, 2 or 3 (else SDF_ERR_UNSUPPORTED).  D = 1 (Sec. 2.1 treats
+ *              1D alongside 2D and 3D) runs the whole path in one CTA per
+ *              execute: no sign output (SDF_OUT_SIGN gives
+ *              SDF_ERR_UNSUPPORTED), no sdf_backward, sdf_curvature,
+ *              batches or autotuning.
+ *   dims       host array of D node counts, x first, each in [2, 2048] (1D),
+ *              [2, 4096] (2D) or [2, 512] (3D); M_a (above) must fit the
+ *              device (else SDF_ERR_UNSUPPORTED).
  *   h          grid spacing (> 0).  tau: the paper's tau (> 0).
  *   precision  SDF_FP64 or SDF_FP32.
  *   outputs    mask of SDF_OUT_* bits.  SDF_OUT_S is implied.

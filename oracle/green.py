@@ -101,7 +101,7 @@ def evaluate(Y: np.ndarray, X: np.ndarray, tau: float, want=("S", "dS", "d2S"), 
     n, D = X.shape
     P = prefactor(D, tau)
     A = origin_integral(D)
-    pairs = [(0, 1)] if D == 2 else [(0, 1), (0, 2), (1, 2)]
+    pairs = [(a, b) for a in range(D) for b in range(a + 1, D)]  # xy[, xz, yz]
     out = {"S": np.empty(n)}
     if "dS" in want or "d2S" in want:
         out["dS"] = np.empty((n, D))

@@ -210,6 +210,11 @@ std::vector<int> plan_kernel_ids(const sdf_plan_impl *p) {
     const int D = p->D;
     const bool ds = p->outputs & SDF_OUT_DS, d2 = p->outputs & SDF_OUT_D2S, sg = p->outputs & SDF_OUT_SIGN;
     std::vector<int> ids = {KER_PHI};
+    if (D == 1) {
+        if (ds) ids.push_back(KER_GX);
+        if (d2) ids.push_back(KER_HXX);
+        return ids;
+    }
     if (ds) {
         ids.push_back(KER_GX);
         ids.push_back(KER_GY);
@@ -241,7 +246,12 @@ void plan_programme(sdf_plan_impl *p) {
     const bool ds = p->outputs & SDF_OUT_DS, d2 = p->outputs & SDF_OUT_D2S, sg = p->outputs & SDF_OUT_SIGN;
     p->nfield = sg ? (D == 2 ? 2 : 3) : 1;
     p->ngroup = 0;
-    if (D == 2) {
+    if (D == 1) {
+        // one line, one CTA (line1d.cu): phi and phi' share a transform, the
+        // Hessian kernel has its own
+        add_pair(p, KER_PHI, CH_PHI, ds ? KER_GX : -1, CH_GX);
+        if (d2) add_pair(p, KER_HXX, CH_HXX, -1, CH_NONE);
+    } else if (D == 2) {
         add_pair(p, KER_PHI, CH_PHI, ds ? KER_GX : -1, CH_GX);
         if (ds) add_pair(p, KER_GY, CH_GY, d2 ? KER_HXX : -1, CH_HXX);
         if (d2) add_pair(p, KER_HYY, CH_HYY, KER_HXY, CH_HXY);
@@ -390,11 +400,15 @@ sdf_status sdf::plan_create_shared(sdf_plan *out, int D, const int64_t *dims, do
                                    unsigned outputs, void *stream, const sdf_plan_impl *share_from) {
     if (!out) return SDF_ERR_INVALID_ARG;
     *out = nullptr;
-    if (D != 2 && D != 3) return SDF_ERR_UNSUPPORTED;
+    if (D < 1 || D > 3) return SDF_ERR_UNSUPPORTED;
     if (!dims || !(h > 0.0) || !(tau > 0.0) || !std::isfinite(h) || !std::isfinite(tau)) return SDF_ERR_INVALID_ARG;
     if (precision != SDF_FP64 && precision != SDF_FP32) return SDF_ERR_INVALID_ARG;
     if (outputs & ~15u) return SDF_ERR_INVALID_ARG;
-    const int64_t nmax = (D == 2) ? 4096 : 512;
+    if (D == 1 && (outputs & SDF_OUT_SIGN)) {
+        set_last_error("sdf_plan_create: no sign in 1D (the paper defines winding numbers in 2D, degrees in 3D)");
+        return SDF_ERR_UNSUPPORTED;
+    }
+    const int64_t nmax = (D == 1) ? 2048 : ((D == 2) ? 4096 : 512);
     for (int a = 0; a < D; ++a)
         if (dims[a] < 2 || dims[a] > nmax) return SDF_ERR_UNSUPPORTED;
     auto t0 = std::chrono::steady_clock::now();
@@ -500,6 +514,10 @@ sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double
     p->last_K = K;
     p->nlaunch = 0;
     const bool ww = weights != nullptr;
+    if (p->D == 1) {
+        CK(launch_line1d(p, K, points, S, dS, d2S, flags));
+        return SDF_OK;
+    }
     CK(launch_points(p, K, points, weights));
     uint8_t *fl = flags;
     int8_t *sg = sign;
@@ -725,6 +743,10 @@ static sdf_status time_kernels(sdf_plan p, int64_t K, const double *points, cons
 sdf_status sdf_plan_autotune(sdf_plan p, int64_t K, const double *points, const double *weights, int reps,
                              int *lines_T, int *lines_F, int *fused_variant) {
     if (!p || !points || reps < 1) return SDF_ERR_INVALID_ARG;
+    if (p->D == 1) {
+        set_last_error("sdf_plan_autotune: a 1D plan has no tile schedule");
+        return SDF_ERR_UNSUPPORTED;
+    }
     const char *tnames[] = {"xpass", "fwd_y", "inv_y", "epilogue"};
     const char *fnames[] = {"fused"};
     double best = 1e300;
@@ -807,6 +829,10 @@ sdf_status sdf_backward(sdf_plan p, int64_t K, const double *points, const void 
     if (!p || !points || !w || !S_saved || !dL_dY || !dL_dtau) return SDF_ERR_INVALID_ARG;
     if (p->kernel_set != SDF_KERNEL_EXP) {
         set_last_error("sdf_backward: the adjoint is derived for the exp(-r/tau) kernel set only");
+        return SDF_ERR_UNSUPPORTED;
+    }
+    if (p->D == 1) {
+        set_last_error("sdf_backward: 2D and 3D plans only");
         return SDF_ERR_UNSUPPORTED;
     }
     if (!(p->outputs & SDF_OUT_DS)) return SDF_ERR_INVALID_ARG;

@@ -64,7 +64,7 @@ sdf_status sdf_batch_create(sdf_batch *out, int n, int D, const int64_t *dims, c
     if (!out) return SDF_ERR_INVALID_ARG;
     *out = nullptr;
     if (n < 1 || !dims || !h || !tau || n_streams < 1 || n_streams > 32) return SDF_ERR_INVALID_ARG;
-    if (D != 2 && D != 3) return SDF_ERR_UNSUPPORTED;
+    if (D != 2 && D != 3) return SDF_ERR_UNSUPPORTED;  // 1D plans are one CTA each: no batch
     sdf_batch_s *b = new (std::nothrow) sdf_batch_s();
     if (!b) return SDF_ERR_OOM;
     b->n = n;

@@ -72,6 +72,10 @@ extern "C" sdf_status sdf_curvature(sdf_plan p, const void *dS, const void *d2S,
         set_last_error("sdf_curvature: null plan or plane");
         return SDF_ERR_INVALID_ARG;
     }
+    if (p->D == 1) {
+        set_last_error("sdf_curvature: 2D and 3D plans only");
+        return SDF_ERR_UNSUPPORTED;
+    }
     const int64_t n = p->nnodes;
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
     prof_begin(p, "curvature", p->stream);

@@ -149,6 +149,8 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool with_sign, void *S, void *dS, vo
                          uint8_t *flags);
 cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags);
 cudaError_t build_spectra(sdf_plan_impl *p);
+cudaError_t launch_line1d(sdf_plan_impl *p, int64_t K, const double *points, void *S, void *dS, void *d2S,
+                          uint8_t *flags);
 cudaError_t launch_adjoint(sdf_plan_impl *p, int64_t K, const double *points, const void *w, const void *S_saved,
                            const uint8_t *flags, double *dL_dY, double *dL_dtau);
 
@@ -160,7 +162,7 @@ double green_origin_integral(int D);  // A_D of the exact Green's function set (
 // a multiple of 4 values (16-byte aligned rows).
 inline int64_t spec_row_len(const sdf_plan_impl *p) { return ((p->M[p->D - 1] / 2 + 1) + 3) & ~int64_t(3); }
 inline int64_t spec_rows(const sdf_plan_impl *p) {
-    return p->D == 2 ? p->M[0] / 2 + 1 : (p->M[0] / 2 + 1) * (p->M[1] / 2 + 1);
+    return p->D == 1 ? 1 : (p->D == 2 ? p->M[0] / 2 + 1 : (p->M[0] / 2 + 1) * (p->M[1] / 2 + 1));
 }
 
 sdf_status plan_create_shared(sdf_plan *out, int D, const int64_t *dims, double h, double tau, int precision,

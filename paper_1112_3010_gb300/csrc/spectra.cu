@@ -151,8 +151,11 @@ __global__ void k_compress(const double2 *__restrict__ K, T *c, int D, int64_t M
     const int64_t total = H0 * H1 * H2;
     double worst = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t f0, f1, f2 = 0, dst;
-        if (D == 2) {
+        int64_t f0, f1 = 0, f2 = 0, dst;
+        if (D == 1) {
+            f0 = i;
+            dst = i;
+        } else if (D == 2) {
             f1 = i % H1;
             f0 = i / H1;
             dst = f0 * Hp + f1;

@@ -123,3 +123,19 @@ def test_tends_to_distance(D):
         errs.append(np.max(np.abs(green.evaluate(Y, X, tau, want=("S",))["S"] - R)))
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
     assert errs[-1] < 4 * 0.0003 * np.log(1 / 0.0003)
+
+
+def test_1d_green_is_exp_up_to_a_constant():
+    """In 1D the Green's function is (1/2tau) exp(-|x|/tau) (eq.
+    GreensFunction1D): with the tau^1/2 of eq. phiapproxSol the set differs
+    from exp(-r/tau) only by S_G = S - tau log(tau^-1/2 / 2), derivatives equal."""
+    import oracle
+    rng = np.random.default_rng(2)
+    Y = rng.uniform(0.2, 0.8, (30, 1))
+    X = rng.uniform(0.0, 1.0, (80, 1))
+    tau = 0.01
+    e = oracle.evaluate(Y, X, tau, want=("S", "dS", "d2S"))
+    g = green.evaluate(Y, X, tau)
+    np.testing.assert_allclose(g["S"], e["S"] - tau * np.log(tau ** -0.5 / 2), atol=1e-14)
+    np.testing.assert_allclose(g["dS"], e["dS"], atol=1e-13)
+    np.testing.assert_allclose(g["d2S"], e["d2S"], atol=1e-9 / tau)

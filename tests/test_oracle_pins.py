@@ -23,7 +23,7 @@ def _rng(seed):
 
 
 # ---------------------------------------------------------------- closed forms
-@pytest.mark.parametrize("D", [2, 3])
+@pytest.mark.parametrize("D", [1, 2, 3])
 def test_single_point_is_a_cone(D):
     """K = 1: S = r, grad S = n, Hessian = (I - n n^T)/r (textbook cone)."""
     rng = _rng(1)
@@ -65,7 +65,7 @@ def test_two_points_midpoint_gradient_vanishes():
 
 
 # ------------------------------------------------------------------- the bound
-@pytest.mark.parametrize("D", [2, 3])
+@pytest.mark.parametrize("D", [1, 2, 3])
 def test_error_bound_against_brute_force(D):
     """Sec. 2.4, eqs. Bound1 / errorBound: 0 <= R - S <= tau log K with R the
     brute-force nearest distance (eq. Rdef)."""
@@ -96,7 +96,7 @@ def test_monotone_in_tau():
 
 
 # ------------------------------------------------------------ finite differences
-@pytest.mark.parametrize("D", [2, 3])
+@pytest.mark.parametrize("D", [1, 2, 3])
 def test_gradient_matches_finite_differences(D):
     """eq. SxSy against central differences of eq. STilde."""
     rng = _rng(7 + D)
@@ -113,7 +113,7 @@ def test_gradient_matches_finite_differences(D):
         np.testing.assert_allclose(o["dS"][:, a], (Sp - Sm) / (2 * eps), atol=2e-8)
 
 
-@pytest.mark.parametrize("D", [2, 3])
+@pytest.mark.parametrize("D", [1, 2, 3])
 def test_hessian_matches_finite_differences(D):
     """eqs. Sxx, Syy, Sxy (and the 3D analogue) against central differences of
     the gradient."""
