@@ -119,6 +119,15 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// The two nodes of a thread are the two lanes of packed FP32x2 arithmetic
+// (sm_100+): lane j of an accumulator is node j's.
+__device__ __forceinline__ float lane(const float2 &v, int j) { return j ? v.y : v.x; }
+__device__ __forceinline__ void lane_scale(float2 &v, int j, float s) {
+    if (j) v.y *= s;
+    else v.x *= s;
+}
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
 // Index of the pair (a, b), a <= b, in the row-by-row upper triangle.
 template <int D> __device__ __forceinline__ constexpr int sym_index(int a, int b) {
     return a * D - a * (a - 1) / 2 + (b - a);
@@ -192,18 +201,15 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 6 : 
     // sB_ab = sum c e d_a d_b (1/r_w + 1/tau)/r^2 (r in grid units, r_w = h r
     // the distance, d = node - point); then H_ab = (delta_ab sA/h - sB_ab)/sE
     // + g_a g_b/tau (eqs. Sxx, Syy, Sxy) and grad S = sG/sE (eq. SxSy)
-    float mg[NPT], mk[NPT], sE[NPT], sA[NPT], sG[NPT][D], sB[NPT][NH];
+    static_assert(NPT == 2, "two nodes per thread: the two lanes of float2");
+    float mg[NPT];
+    float2 mk = dup2(INFINITY), sE = dup2(0.f), sA = dup2(0.f), sG[D], sB[NH];
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-        mg[j] = INFINITY;
-        mk[j] = INFINITY;
-        sE[j] = 0.f;
-        sA[j] = 0.f;
+    for (int j = 0; j < NPT; ++j) mg[j] = INFINITY;
 #pragma unroll
-        for (int a = 0; a < D; ++a) sG[j][a] = 0.f;
+    for (int a = 0; a < D; ++a) sG[a] = dup2(0.f);
 #pragma unroll
-        for (int a = 0; a < NH; ++a) sB[j][a] = 0.f;
-    }
+    for (int a = 0; a < NH; ++a) sB[a] = dup2(0.f);
     unsigned nterm = 0;
 
     // ring k: bins at Chebyshev distance k from the tile's block of bins
@@ -369,50 +375,52 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 6 : 
                         const float r = sqrtf(mn[j]);
                         if (r < mg[j]) {
                             const float sc = (mg[j] < INFINITY) ? ex2_approx((r - mg[j]) * l2e_th) : 0.f;
-                            sE[j] *= sc;
-                            sA[j] *= sc;
+                            lane_scale(sE, j, sc);
+                            lane_scale(sA, j, sc);
 #pragma unroll
-                            for (int a = 0; a < D; ++a) sG[j][a] *= sc;
+                            for (int a = 0; a < D; ++a) lane_scale(sG[a], j, sc);
 #pragma unroll
-                            for (int a = 0; a < NH; ++a) sB[j][a] *= sc;
+                            for (int a = 0; a < NH; ++a) lane_scale(sB[a], j, sc);
                             mg[j] = r;
-                            mk[j] = r * l2e_th;
+                            if (j) mk.y = r * l2e_th;
+                            else mk.x = r * l2e_th;
                         }
                     }
                 }
                 nterm += (unsigned)ncell * ((mine[0] ? 1u : 0u) + (mine[1] ? 1u : 0u));
+                const float2 nl2e = dup2(-l2e_th), ih2 = dup2(ih), itau2 = dup2(itau);
 #pragma unroll 2
                 for (int e = 0; e < ncell; ++e) {
                     const float4 q = cell[e];
                     const float d0 = xf - q.x, d1 = yf - q.y;
                     const float cl = (D == 2) ? d1 : zf - q.z;
                     const float base = (D == 2) ? d0 * d0 : fmaf(d0, d0, d1 * d1);
+                    // node offsets per axis, lanes = the two nodes (they differ along the last axis)
+                    float2 dv[D];
+                    dv[0] = dup2(d0);
+                    if (D == 3) dv[1] = dup2(d1);
+                    dv[D - 1] = make_float2(cl, cl + kOff);
+                    const float2 r2 = __ffma2_rn(dv[D - 1], dv[D - 1], dup2(base));
+                    // 1/r from one reciprocal square root; r2 is an integer,
+                    // and the point under the node itself (r2 = 0) gets
+                    // 1/r = 0: it adds to the sum only
+                    const float2 ir = make_float2(fminf(rsqrt_approx(r2.x), r2.x), fminf(rsqrt_approx(r2.y), r2.y));
+                    const float2 arg = __ffma2_rn(__fmul2_rn(r2, ir), nl2e, mk);
+                    const float2 E = __fmul2_rn(dup2(q.w), make_float2(ex2_approx(arg.x), ex2_approx(arg.y)));
+                    sE = __fadd2_rn(sE, E);
+                    if constexpr (LVL >= 1) {
+                        const float2 Eir = __fmul2_rn(E, ir);
 #pragma unroll
-                    for (int j = 0; j < NPT; ++j) {
-                        const float cj = cl + kOff * j;
-                        const float d[3] = {d0, (D == 2) ? cj : d1, cj};
-                        const float r2 = fmaf(cj, cj, base);
-                        // 1/r from one reciprocal square root; r2 is an integer,
-                        // and the point under the node itself (r2 = 0) gets
-                        // 1/r = 0: it adds to the sum only
-                        const float ir = fminf(rsqrt_approx(r2), r2);
-                        const float rg = r2 * ir;
-                        const float E = q.w * ex2_approx(fmaf(-rg, l2e_th, mk[j]));
-                        sE[j] += E;
-                        if constexpr (LVL >= 1) {
-                            const float Eir = E * ir;
+                        for (int a = 0; a < D; ++a) sG[a] = __ffma2_rn(Eir, dv[a], sG[a]);
+                        if constexpr (LVL >= 2) {
+                            const float2 F = __fmul2_rn(__fmul2_rn(Eir, ir), __ffma2_rn(ir, ih2, itau2));
+                            sA = __fadd2_rn(sA, Eir);
+                            int qh = 0;
 #pragma unroll
-                            for (int a = 0; a < D; ++a) sG[j][a] = fmaf(Eir, d[a], sG[j][a]);
-                            if constexpr (LVL >= 2) {
-                                const float F = Eir * ir * fmaf(ir, ih, itau);
-                                sA[j] += Eir;
-                                int qh = 0;
+                            for (int a = 0; a < D; ++a) {
+                                const float2 Fd = __fmul2_rn(F, dv[a]);
 #pragma unroll
-                                for (int a = 0; a < D; ++a) {
-                                    const float Fd = F * d[a];
-#pragma unroll
-                                    for (int bb = a; bb < D; ++bb, ++qh) sB[j][qh] = fmaf(Fd, d[bb], sB[j][qh]);
-                                }
+                                for (int bb = a; bb < D; ++bb, ++qh) sB[qh] = __ffma2_rn(Fd, dv[bb], sB[qh]);
                             }
                         }
                     }
@@ -441,7 +449,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 6 : 
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             if (!active[j]) continue;
-            const float A = (mg[j] < INFINITY) ? -mg[j] * h * itau + __logf(sE[j]) : -INFINITY;
+            const float A = (mg[j] < INFINITY) ? -mg[j] * h * itau + __logf(lane(sE, j)) : -INFINITY;
             // the rest adds less than 1e-5 of the sum: final
             if (tail0 <= A - 11.512925f) {
                 active[j] = false;
@@ -479,7 +487,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 6 : 
     for (int j = 0; j < NPT; ++j) {
         if (!mine[j]) continue;
         const int64_t nd = node[j];
-        const float S = fmaf(mg[j], h, -tau * logf(sE[j]));
+        const float S = fmaf(mg[j], h, -tau * logf(lane(sE, j)));
         const float sg = (P.sign && P.sign[nd] < 0) ? -1.f : 1.f;
         if (!P.full && (early_cap[j] || !(S <= scap))) {
             ++capped;
@@ -492,26 +500,26 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 6 : 
             P.flags[nd] = SDF_FLAG_FIXUP;
             continue;
         }
-        const float inv = 1.f / sE[j];
+        const float inv = 1.f / lane(sE, j);
         float g[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            g[a] = sG[j][a] * inv;
+            g[a] = lane(sG[a], j) * inv;
             if (dS) dS[a * P.nnodes + nd] = (TO)g[a];
         }
         if (LVL >= 2 && d2S) {
             // sB is stored row by row (xx, xy, [xz,] yy, ...); d2S is
             // diagonal first, then the pairs a < b
-            const float Ad = sA[j] * ih * inv;
+            const float Ad = lane(sA, j) * ih * inv;
             int q = 0;
 #pragma unroll
             for (int a = 0; a < D; ++a, ++q)
-                d2S[q * P.nnodes + nd] = (TO)(Ad - sB[j][sym_index<D>(a, a)] * inv + g[a] * g[a] * itau);
+                d2S[q * P.nnodes + nd] = (TO)(Ad - lane(sB[sym_index<D>(a, a)], j) * inv + g[a] * g[a] * itau);
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
                 for (int bb = a + 1; bb < D; ++bb, ++q)
-                    d2S[q * P.nnodes + nd] = (TO)(-sB[j][sym_index<D>(a, bb)] * inv + g[a] * g[bb] * itau);
+                    d2S[q * P.nnodes + nd] = (TO)(-lane(sB[sym_index<D>(a, bb)], j) * inv + g[a] * g[bb] * itau);
         }
         P.flags[nd] = SDF_FLAG_FIXUP;
     }
