@@ -50,8 +50,8 @@ __global__ void k_line1d(Line1dParams P) {
     extern __shared__ unsigned char smraw[];
     const int M = 1 << P.logM, TPL = M >> 4, N = P.N;
     V *sm = reinterpret_cast<V *>(smraw);
-    int *cnt = reinterpret_cast<int *>(smraw + sizeof(V) * pad16(M));
-    int *fix = cnt + N;
+    int *cnt = reinterpret_cast<int *>(smraw + sizeof(V) * pad16(M));  // node counts
+    int *fix = cnt + N;                                                 // nodes for the direct sum
     __shared__ int s_nfix, s_ncap;
     __shared__ unsigned long long s_c2;
     __shared__ int s_nu;
@@ -173,28 +173,60 @@ __global__ void k_line1d(Line1dParams P) {
         if (t == 0) P.dsc->n_capped = (unsigned long long)s_ncap;
         return;
     }
+    // the occupied nodes in order, as (position, count) pairs: each thread
+    // lists one contiguous chunk, thread 0 turns the chunk sizes into offsets
+    int2 *occ = reinterpret_cast<int2 *>(fix + N);
+    __shared__ int s_part[256];
+    const int chunk = (N + nt - 1) / nt, i0 = min(N, t * chunk), i1 = min(N, i0 + chunk);
+    int mine = 0;
+    for (int i = i0; i < i1; ++i) mine += cnt[i] > 0;
+    s_part[t] = mine;
+    __syncthreads();
+    if (t == 0) {
+        int acc = 0;
+        for (int w = 0; w < nt; ++w) {
+            const int c = s_part[w];
+            s_part[w] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    for (int i = i0, o = s_part[t]; i < i1; ++i)
+        if (cnt[i] > 0) occ[o++] = make_int2(i, cnt[i]);
+    __syncthreads();
+    const int nocc = s_nu;
     // direct sum, shifted by the distance R to the nearest occupied node
     // (eq. Bound1): phi e^{R/tau} = sum_j m_j e^{-(r_j - R)/tau}, in units of h
     const float hf = (float)P.h, itf = (float)(P.h / P.tau), tf = (float)P.tau;
     unsigned long long terms = 0;
     for (int i = t; i < nfix; i += nt) {
         const int x = fix[i];
+        // nearest occupied node: the first position >= x or the one before it
+        int lo = 0, hi = nocc;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (occ[mid].x < x) lo = mid + 1;
+            else hi = mid;
+        }
         int dmin = 1 << 30;
-        for (int j = 0; j < N; ++j)
-            if (cnt[j] > 0) dmin = min(dmin, abs(x - j));
+        if (lo < nocc) dmin = occ[lo].x - x;
+        if (lo > 0) dmin = min(dmin, x - occ[lo - 1].x);
+        // outward from there while a term can still matter: past 60 tau
+        // beyond the nearest node it is below e^-60 of the leading term
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int j = 0; j < N; ++j) {
-            const int c = cnt[j];
-            if (c == 0) continue;
-            ++terms;
-            const int d = x - j;
-            const float e = (float)c * __expf(-(float)(abs(d) - dmin) * itf);
+        auto add = [&](const int2 q) {
+            const int d = x - q.x;
+            const float e = (float)q.y * __expf(-(float)(abs(d) - dmin) * itf);
             s0 += e;
             if (d != 0) {
                 s1 += d > 0 ? e : -e;  // n E with n = sign(x - y)
                 s2 += e;               // the Hessian kernel is -E/tau off the origin
             }
-        }
+            ++terms;
+        };
+        const float cut = 60.f / itf;  // 60 tau in nodes
+        for (int j = lo; j < nocc && (float)(occ[j].x - x - dmin) <= cut; ++j) add(occ[j]);
+        for (int j = lo - 1; j >= 0 && (float)(x - occ[j].x - dmin) <= cut; --j) add(occ[j]);
         const float Sx = (float)dmin * hf - tf * logf(s0);
         if (!P.full_range && Sx > (float)scap) {  // phi below theta_64
             atomicAdd(&s_ncap, 1);
@@ -247,13 +279,13 @@ cudaError_t launch_line1d(sdf_plan_impl *p, int64_t K, const double *points, voi
     const int M = 1 << P.logM, nt = M >> 4;
     prof_begin(p, "line1d", st);
     if (p->prec == SDF_FP64) {
-        const size_t smem = sizeof(double2) * pad16(M) + sizeof(int) * 2 * P.N;
+        const size_t smem = sizeof(double2) * pad16(M) + (sizeof(int) * 2 + sizeof(int2)) * P.N;
         if ((e = cudaFuncSetAttribute(k_line1d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
             return e;
         k_line1d<double><<<1, nt, smem, st>>>(P);
     } else {
-        const size_t smem = sizeof(float2) * pad16(M) + sizeof(int) * 2 * P.N;
+        const size_t smem = sizeof(float2) * pad16(M) + (sizeof(int) * 2 + sizeof(int2)) * P.N;
         if ((e = cudaFuncSetAttribute(k_line1d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
             return e;
