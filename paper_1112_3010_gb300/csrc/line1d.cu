@@ -52,7 +52,7 @@ __global__ void k_line1d(Line1dParams P) {
     V *sm = reinterpret_cast<V *>(smraw);
     int *cnt = reinterpret_cast<int *>(smraw + sizeof(V) * pad16(M));  // node counts
     int *fix = cnt + N;                                                 // nodes for the direct sum
-    __shared__ int s_nfix, s_ncap;
+    __shared__ int s_nfix, s_ncap, s_ncapfix;
     __shared__ unsigned long long s_c2;
     __shared__ int s_nu;
     __shared__ double s_thr[3];  // theta64, theta32, S_cap
@@ -61,7 +61,7 @@ __global__ void k_line1d(Line1dParams P) {
 
     for (int i = t; i < N; i += nt) cnt[i] = 0;
     if (t == 0) {
-        s_nfix = s_ncap = s_nu = 0;
+        s_nfix = s_ncap = s_ncapfix = s_nu = 0;
         s_c2 = 0;
     }
     __syncthreads();
@@ -165,10 +165,7 @@ __global__ void k_line1d(Line1dParams P) {
     }
     __syncthreads();
     const int nfix = s_nfix;
-    if (t == 0) {
-        P.dsc->n_fixup_nodes = (unsigned long long)nfix;
-        P.dsc->n_fixup_tiles = nfix > 0 ? 1ull : 0ull;
-    }
+    if (t == 0) P.dsc->n_fixup_tiles = nfix > 0 ? 1ull : 0ull;
     if (nfix == 0) {
         if (t == 0) P.dsc->n_capped = (unsigned long long)s_ncap;
         return;
@@ -230,6 +227,7 @@ __global__ void k_line1d(Line1dParams P) {
         const float Sx = (float)dmin * hf - tf * logf(s0);
         if (!P.full_range && Sx > (float)scap) {  // phi below theta_64
             atomicAdd(&s_ncap, 1);
+            atomicAdd(&s_ncapfix, 1);
             if (Sout) Sout[x] = scap;
             if (dS) dS[x] = T(0);
             if (d2S) d2S[x] = T(0);
@@ -242,7 +240,11 @@ __global__ void k_line1d(Line1dParams P) {
         if (d2S) d2S[x] = T((g * g - s2 / s0) / tf);
     }
     __syncthreads();
-    if (t == 0) P.dsc->n_capped = (unsigned long long)s_ncap;
+    if (t == 0) {
+        // as in 2D: the nodes the direct sum wrote, and every capped node
+        P.dsc->n_fixup_nodes = (unsigned long long)(nfix - s_ncapfix);
+        P.dsc->n_capped = (unsigned long long)s_ncap;
+    }
     if (terms) atomicAdd(&P.dsc->n_fixup_terms, terms);
 }
 

@@ -69,7 +69,8 @@ def test_fp32_fixup_is_exercised():
     assert st.n_fixup_nodes > 0 and st.n_capped > 0
     fix = (res["flags"] & pkg.SDF_FLAG_FIXUP) != 0
     # recomputed nodes keep FIXUP unless the exact sum put them below theta_64
-    assert 0 < fix.sum() <= st.n_fixup_nodes
+    assert 0 < fix.sum() == st.n_fixup_nodes
+    assert ((res["flags"] & pkg.SDF_FLAG_CAPPED) != 0).sum() == st.n_capped
     check(s, res, ref_of(s), check_sign=False, label="1d-fixup")
 
 

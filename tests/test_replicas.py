@@ -57,3 +57,22 @@ def test_reference_arm_other_ranks_idle(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line(monkeypatch, capsys):
+    """`bench.py --impl reference` on rank 0: one JSON line with the contract's
+    keys, the oracle as the timed program (a tiny bounded sample here)."""
+    class Args:
+        gpus, steps, warmup = 1, 1, 3
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("SDF_REF_NODES", "512")
+    assert bench.run_reference(Args()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["workload"] == bench.WORKLOAD
