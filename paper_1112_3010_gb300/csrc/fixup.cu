@@ -136,7 +136,7 @@ template <int D> __device__ __forceinline__ constexpr int sym_index(int a, int b
 // LVL: 0 = S only, 1 = S and grad S, 2 = S, grad S and the Hessian (only the
 // sums the requested outputs need are accumulated).
 template <int D, typename TO, int LVL>
-__global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : (LVL == 2 ? 2 : 3)) k_fixup(FixParams P) {
+__global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : (LVL == 2 ? 2 : 4)) k_fixup(FixParams P) {
     constexpr int TB = (D == 2) ? kTB2 : 1;  // tile edge in bins
     constexpr int NT = (D == 2) ? 32 * kTB2 * kTB2 : 256;
     constexpr int NH = D * (D + 1) / 2;
