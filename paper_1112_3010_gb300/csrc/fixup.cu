@@ -9,7 +9,9 @@
 // but gives no mechanism; this one is ours.
 //
 // One CTA per flagged tile (2x2 bins of 8x8 nodes in 2D, one 8^3 bin in 3D),
-// two nodes per thread so that each staged point feeds two sums.  Candidate
+// two nodes per thread so that each staged point feeds two sums; the two
+// nodes are the two lanes of packed FP32x2 arithmetic (fma/mul/add.f32x2),
+// which halves the FMA-pipe instructions of the summing loop.  Candidate
 // bins are visited in rings of Chebyshev distance k = 0, 1, 2, ... around the
 // tile; every occupied node of ring k' lies at least (8(k'-1)+1)h from every
 // node of the tile, so after ring k the unvisited points add at most
