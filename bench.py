@@ -478,7 +478,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "kernels": per_kernel, "fft_passes": passes, "fp64_path": fp64,
             "fixup": [{"tau": s.tau, "tiles": st.n_fixup_tiles, "nodes": st.n_fixup_nodes,
-                       "capped_in_fixup": st.n_capped, "terms": st.n_fixup_terms, "theta32": st.theta32,
+                       "capped": st.n_capped, "terms": st.n_fixup_terms, "theta32": st.theta32,
                        "theta64": st.theta64,
                        "ms": pp.get("fixup", (1, 0.0))[1] / max(1, pp.get("fixup", (1, 0.0))[0]),
                        "terms_per_s": st.n_fixup_terms / max(1e-12, 1e-3 * pp.get("fixup", (1, 0.0))[1]

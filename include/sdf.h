@@ -111,8 +111,8 @@ typedef struct {
     double g_norm2;      /* ||g||_2 = sqrt(sum over nodes of count^2)          */
     int64_t n_unique;    /* distinct occupied nodes                            */
     int64_t n_fixup_tiles;  /* tiles the direct-sum fix-up visited             */
-    int64_t n_fixup_nodes;  /* nodes it recomputed                            */
-    int64_t n_capped;    /* nodes returned as S_cap                            */
+    int64_t n_fixup_nodes;  /* nodes whose values it wrote (flag FIXUP only)   */
+    int64_t n_capped;    /* nodes returned as S_cap (flag CAPPED)              */
     int64_t n_launches;  /* kernels the last execute launched                  */
     int64_t n_fixup_terms;  /* (node, occupied node) terms the fix-up summed   */
 } sdf_exec_stats;

@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
         if (kev < INT_MAX) atomicMin(&s_kev[(round + 1) & 1], kev);
         k0 = k1 + 1;
     }
-    int fixed = 0, capped = 0;
+    int fixed = 0;
     TO *So = reinterpret_cast<TO *>(P.S);
     TO *dS = reinterpret_cast<TO *>(P.dS);
     TO *d2S = reinterpret_cast<TO *>(P.d2S);
@@ -492,7 +492,6 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
         const float S = fmaf(mg[j], h, -tau * logf(lane(sE, j)));
         const float sg = (P.sign && P.sign[nd] < 0) ? -1.f : 1.f;
         if (!P.full && (early_cap[j] || !(S <= scap))) {
-            ++capped;
             P.flags[nd] = SDF_FLAG_CAPPED | SDF_FLAG_FIXUP;
             continue;
         }
@@ -526,16 +525,18 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
         P.flags[nd] = SDF_FLAG_FIXUP;
     }
     // statistics
-    unsigned fx = fixed, cp = capped;
+    unsigned fx = fixed;
     unsigned long long nt64 = nterm;
     for (int o = 16; o > 0; o >>= 1) {
         fx += __shfl_down_sync(0xffffffffu, fx, o);
-        cp += __shfl_down_sync(0xffffffffu, cp, o);
         nt64 += __shfl_down_sync(0xffffffffu, nt64, o);
     }
     if ((tid & 31) == 0) {
-        if (fx) atomicAdd(&P.dsc_w->n_fixup_nodes, (unsigned long long)fx);
-        if (cp) atomicAdd(&P.dsc_w->n_capped, (unsigned long long)cp);
+        if (fx) {
+            atomicAdd(&P.dsc_w->n_fixup_nodes, (unsigned long long)fx);
+            // the epilogue counted these as capped; they are not any more
+            atomicAdd(&P.dsc_w->n_capped, (unsigned long long)(-(long long)fx));
+        }
         if (nt64) atomicAdd(&P.dsc_w->n_fixup_terms, nt64);
     }
     if (tid == 0) atomicAdd(&P.dsc_w->n_fixup_tiles, 1ull);

@@ -533,6 +533,7 @@ struct EpiParams {
     uint8_t *flags;
     uint8_t *tile_flag;
     const DevScalars *dsc;
+    DevScalars *dsc_w;  // the same scalars, for the count of capped nodes
     double tau, coef64, coef32;
     int64_t nnodes;
     int N0, N1;
@@ -595,6 +596,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     T gs[D][8];
     unsigned sgn = 0xffu;   // bit m: +1 (no sign requested: all +1)
     unsigned trusted = 0;
+    unsigned ncap = 0;      // nodes of this thread flagged CAPPED
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         phi[m] = T(1);
@@ -640,6 +642,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
                         const T sv = ((sgn >> m) & 1) ? s : -s;
                         if (Sout) Sout[node] = sv;
                         if (P.flags) P.flags[node] = ok ? 0 : SDF_FLAG_CAPPED;
+                        ncap += ok ? 0u : 1u;
                         if (!ok && P.fixup && P.tile_flag) P.tile_flag[brow + (x >> 3)] = 1;
                         break;
                     }
@@ -678,6 +681,9 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
             }
         }
     }
+    // capped nodes (the FP32 fix-up takes back the ones it recomputes)
+    ncap = __reduce_add_sync(0xffffffffu, ncap);
+    if ((threadIdx.x & 31) == 0 && ncap) atomicAdd(&P.dsc_w->n_capped, (unsigned long long)ncap);
 }
 
 // ---------------------------------------------------------------- launch helpers

@@ -70,6 +70,7 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
     E.flags = flags;
     E.tile_flag = p->tile_flag;
     E.dsc = p->dsc;
+    E.dsc_w = p->dsc;
     E.tau = p->tau;
     {
         const double n = (double)p->M[0] * (double)p->M[1] * (D == 3 ? (double)p->M[2] : 1.0);

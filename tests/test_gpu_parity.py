@@ -150,3 +150,20 @@ def test_execute_host_fixup_outputs(pinned):
     plan.execute_host(torch.from_numpy(s.points), torch.from_numpy(s.weights), out)
     for k in out:
         assert torch.equal(out[k], dev[k].cpu()), k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_stats_match_flags(prec):
+    """n_capped counts the nodes flagged CAPPED and n_fixup_nodes those the
+    fix-up wrote (FIXUP without CAPPED), whichever kernel set the flag."""
+    s = wl.stars(N=256, K=3000, n_shapes=2, tau=0.004, seed=21)
+    res = run(s, prec, outputs=("S", "dS", "sign"))
+    fl = res["flags"]
+    st = res["stats"]
+    capped = (fl & pkg.SDF_FLAG_CAPPED) != 0
+    fixed = ((fl & pkg.SDF_FLAG_FIXUP) != 0) & ~capped
+    assert capped.sum() > 0
+    assert int(capped.sum()) == st.n_capped
+    assert int(fixed.sum()) == st.n_fixup_nodes
+    if prec == "fp32":
+        assert st.n_fixup_nodes > 0
