@@ -28,6 +28,20 @@ def test_largest_2d_grid_sampled():
     res["plan"].close()
 
 
+def test_largest_3d_grid_sampled():
+    # N = 512 per axis (padded 1024^3, ~70 GB at the plan-time peak), FP32
+    # with the fix-up, sign from the degree of a sampled sphere
+    s = wl.sphere(N=512, K=4000, radius=0.3, tau=2.0 / 512, seed=57)
+    res = run(s, "fp32", outputs=("S", "dS", "sign"))
+    rng = np.random.default_rng(58)
+    n = int(np.prod(s.dims))
+    sel = rng.choice(n, 1000, replace=False)
+    ref = oracle_ref(s, sel=sel, want=("S", "dS", "mu", "R"))
+    check(s, res, ref, sel=sel, check_hess=False, label="512^3-fp32")
+    assert res["stats"].n_fixup_nodes > 0
+    res["plan"].close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("D", [2, 3])
 def test_smallest_grids(D, prec):
