@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_
 #pragma unroll
         for (int m = 0; m < 8; ++m) my[pad16(t + m * TPL)] = mk<V>(T(0), T(0));
         __syncthreads();
+        bool hit = false;  // this thread placed a point on one of the CTA's lines
         if (valid) {
             for (int bx = t; bx < nb0; bx += TPL) {
                 const int64_t b = brow + bx;
@@ -101,10 +102,20 @@ __global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_
                     else if (f == 1) val = mk<V>(T(uw[3 * (int64_t)(s + i)]), T(uw[3 * (int64_t)(s + i) + 1]));
                     else val = mk<V>(T(uw[3 * (int64_t)(s + i) + 2]), T(0));
                     my[pad16(x)] = val;
+                    hit = true;
                 }
             }
         }
-        __syncthreads();
+        // lines without points (a quarter of the rows of a typical shape
+        // set) transform to zero: the CTA writes zeros and skips the FFT
+        if (!__syncthreads_or(hit)) {
+            if (valid) {
+                V *o = out + f * out_fs + line;
+#pragma unroll
+                for (int m = 0; m < 16; ++m) o[(int64_t)(t + m * TPL) * n_lines] = mk<V>(T(0), T(0));
+            }
+            continue;
+        }
         V v[16];
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = my[pad16(t + m * TPL)];
