@@ -173,6 +173,32 @@ sdf_status sdf_execute(sdf_plan plan, int64_t K, const double *points,
                        int8_t *sign, uint8_t *flags);
 
 /*
+ * sdf_execute_multi -- sdf_execute of n plans on the same points: a sweep of
+ * tau (the experiments of Sec. 6 vary tau on one point set), or the two
+ * kernel sets side by side.  The plans must agree in D, dims, h, precision
+ * and outputs (else SDF_ERR_INVALID_ARG) and be distinct; tau, the kernel set,
+ * noise constants, tuning and full-range mode may differ.
+ *   plans      host array of n plans.
+ *   K, points, weights   as sdf_execute, shared by all plans.
+ *   S, dS, d2S, sign, flags   host arrays of n device pointers (plan i's
+ *              outputs, as sdf_execute); a NULL array skips that output for
+ *              every plan, a NULL entry for that plan.
+ * The snapping, binning and the tau-independent forward transforms (the
+ * x-pass, and the y-pass in 3D: Table 1 step 3 up to the last axis) run once,
+ * on plans[0]'s stream.  Each plan then runs its spectrum multiply, inverse
+ * transforms, epilogue and fix-up on its own stream.  plans[0]'s stream waits
+ * for all of them before it returns, so later work on plans[0]'s stream is
+ * ordered after the whole call.  Results equal those of n separate
+ * sdf_execute calls bit for bit.  1D plans run one sdf_execute each.
+ * Errors as sdf_execute; device errors are reported by sdf_sync() of the plan
+ * that met them.
+ */
+sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K,
+                             const double *points, const double *weights,
+                             void *const *S, void *const *dS, void *const *d2S,
+                             int8_t *const *sign, uint8_t *const *flags);
+
+/*
  * sdf_execute_host -- sdf_execute with HOST buffers (same shapes and types):
  * copies points/weights to plan-owned device buffers, executes, brings the
  * requested outputs back, and waits for the stream.  S, dS and d2S in

@@ -34,7 +34,7 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_plan_set_noise_constants", "sdf_execute_noalloc", "sdf_batch_create",
             "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy",
             "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature", "sdf_plan_set_full_range",
-            "sdf_mesh_sources", "sdf_plan_set_kernel", "sdf_green_profile"]
+            "sdf_mesh_sources", "sdf_plan_set_kernel", "sdf_green_profile", "sdf_execute_multi"]
 
 
 class SDFError(RuntimeError):
@@ -94,6 +94,8 @@ def load_library(path: str | None = None):
         L.sdf_curvature.argtypes = [vp, vp, vp, vp, vp]
         L.sdf_plan_set_full_range.argtypes = [vp, ctypes.c_int]
         L.sdf_plan_set_kernel.argtypes = [vp, ctypes.c_int]
+        L.sdf_execute_multi.argtypes = [ctypes.c_int, ctypes.POINTER(vp), i64, vp, vp, ctypes.POINTER(vp),
+                                        ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
         L.sdf_green_profile.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp]
         L.sdf_mesh_sources.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
         L.sdf_sync.argtypes = [vp]
@@ -133,7 +135,7 @@ def load_library(path: str | None = None):
         L.sdf_profile_read.restype = ctypes.c_int
         for n in ("sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
                   "sdf_plan_get_info", "sdf_get_stats", "sdf_curvature", "sdf_plan_set_full_range", "sdf_mesh_sources",
-                  "sdf_plan_set_kernel", "sdf_green_profile"):
+                  "sdf_plan_set_kernel", "sdf_green_profile", "sdf_execute_multi"):
             getattr(L, n).restype = ctypes.c_int
         _LIBH = L
         return L
@@ -168,6 +170,20 @@ def sdf_plan_create(D, dims, h, tau, precision, outputs, stream):
 def sdf_execute(handle, K, points, weights, S, dS, d2S, sign, flags):
     _ck(_lib().sdf_execute(handle, int(K), _ptr(points), _ptr(weights), _ptr(S), _ptr(dS),
                            _ptr(d2S), _ptr(sign), _ptr(flags)), "sdf_execute")
+
+
+def sdf_execute_multi(handles, K, points, weights, S, dS, d2S, sign, flags):
+    """handles: list of plan handles; S ... flags: lists (one tensor or None
+    per plan) or None."""
+    n = len(handles)
+    hv = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+
+    def arr(lst):
+        if lst is None:
+            return None
+        return (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in lst])
+    _ck(_lib().sdf_execute_multi(n, hv, int(K), _ptr(points), _ptr(weights), arr(S), arr(dS), arr(d2S),
+                                 arr(sign), arr(flags)), "sdf_execute_multi")
 
 
 def sdf_execute_host(handle, K, points, weights, S, dS, d2S, sign, flags):
@@ -316,6 +332,27 @@ def sdf_plan_destroy(handle):
 # ---------------------------------------------------------------- convenience
 _OUTS = {"S": SDF_OUT_S, "dS": SDF_OUT_DS, "d2S": SDF_OUT_D2S, "sign": SDF_OUT_SIGN}
 _KERNELS = {"exp": SDF_KERNEL_EXP, "green": SDF_KERNEL_GREEN}
+
+
+def execute_multi(plans, points, weights=None, outs=None, check=True):
+    """sdf_execute_multi over Plan objects: one snapping and forward transform
+    for all of them (same D, dims, h, precision, outputs).  Returns one output
+    dict per plan."""
+    t = plans[0].torch
+    pts = points.to(device="cuda", dtype=t.float64).contiguous()
+    w = None if weights is None else weights.to(device="cuda", dtype=t.float64).contiguous()
+    if outs is None:
+        outs = []
+        for p in plans:
+            want = [k for k, v in _OUTS.items() if p.outputs & v] + ["flags"]
+            outs.append(p.alloc_outputs(want, signed=w is not None))
+    col = lambda k: [o.get(k) for o in outs] if any(k in o for o in outs) else None
+    sdf_execute_multi([p.handle for p in plans], pts.shape[0], pts, w, col("S"), col("dS"), col("d2S"),
+                      col("sign"), col("flags"))
+    if check:
+        for p in plans:
+            p.sync()
+    return outs
 
 
 class Plan:

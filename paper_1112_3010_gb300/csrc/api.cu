@@ -534,6 +534,105 @@ sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double
     return SDF_OK;
 }
 
+sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const double *points, const double *weights,
+                             void *const *S, void *const *dS, void *const *d2S, int8_t *const *sign,
+                             uint8_t *const *flags) {
+    if (n < 1 || !plans || !plans[0] || !points) return SDF_ERR_INVALID_ARG;
+    sdf_plan p0 = plans[0];
+    auto at = [](auto *const *arr, int i) { return arr ? arr[i] : nullptr; };
+    for (int i = 0; i < n; ++i) {
+        sdf_plan p = plans[i];
+        if (!p) return SDF_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == p) return SDF_ERR_INVALID_ARG;
+        bool same = p->D == p0->D && p->prec == p0->prec && p->outputs == p0->outputs && p->h == p0->h;
+        for (int a = 0; a < 3; ++a) same = same && p->N[a] == p0->N[a];
+        if (!same) {
+            set_last_error("sdf_execute_multi: the plans differ in D, dims, h, precision or outputs");
+            return SDF_ERR_INVALID_ARG;
+        }
+        sdf_status s = check_execute_args(p, K, points, weights, at(dS, i), at(d2S, i), at(sign, i));
+        if (s != SDF_OK) return s;
+    }
+    if (p0->D == 1) {
+        // one CTA per line: nothing worth sharing
+        for (int i = 0; i < n; ++i) {
+            sdf_status s = sdf_execute(plans[i], K, points, weights, at(S, i), at(dS, i), at(d2S, i), at(sign, i),
+                                       at(flags, i));
+            if (s != SDF_OK) return s;
+        }
+        return SDF_OK;
+    }
+    const bool ww = weights != nullptr;
+    for (int i = 0; i < n; ++i) {
+        CK(ensure_points(plans[i], K));
+        plans[i]->last_K = K;
+        plans[i]->nlaunch = 0;
+    }
+    // the points and the tau-independent forward transforms, once, on p0's stream
+    cudaStream_t st0 = p0->stream;
+    CK(launch_points(p0, K, points, weights));
+    CK(launch_forward_shared_part(p0, ww));
+    // the others' fix-up, Chebyshev map and source flags read the binned points:
+    // copied here, before p0's own later kernels update its scalars
+    for (int i = 1; i < n; ++i) {
+        sdf_plan p = plans[i];
+        CK(cudaMemcpyAsync(p->bin_start, p0->bin_start, sizeof(int) * (p0->nbins + 1), cudaMemcpyDeviceToDevice, st0));
+        CK(cudaMemcpyAsync(p->bin_nuniq, p0->bin_nuniq, sizeof(int) * p0->nbins, cudaMemcpyDeviceToDevice, st0));
+        CK(cudaMemcpyAsync(p->ucell, p0->ucell, sizeof(int) * K, cudaMemcpyDeviceToDevice, st0));
+        CK(cudaMemcpyAsync(p->ucount, p0->ucount, sizeof(int) * K, cudaMemcpyDeviceToDevice, st0));
+        const size_t o = offsetof(DevScalars, wmax);
+        CK(cudaMemcpyAsync(reinterpret_cast<char *>(p->dsc) + o, reinterpret_cast<const char *>(p0->dsc) + o,
+                           sizeof(DevScalars) - o, cudaMemcpyDeviceToDevice, st0));
+    }
+    std::vector<cudaEvent_t> ev(2 * n + 1, nullptr);
+    for (auto &x : ev) CK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+    auto cleanup = [&]() {
+        for (auto &x : ev) cudaEventDestroy(x);
+    };
+#define MCK(x)                       \
+    do {                             \
+        cudaError_t e_ = (x);        \
+        if (e_ != cudaSuccess) {     \
+            cleanup();               \
+            return cuda_fail(e_);    \
+        }                            \
+    } while (0)
+    MCK(cudaEventRecord(ev[2 * n], st0));
+    // per plan: Chebyshev map, the fused pass on p0's transforms
+    for (int i = 0; i < n; ++i) {
+        sdf_plan p = plans[i];
+        if (i > 0) MCK(cudaStreamWaitEvent(p->stream, ev[2 * n], 0));
+        if (p->prec == SDF_FP32) {
+            MCK(cudaMemsetAsync(p->tile_flag, 0, p->nbins, p->stream));
+            MCK(launch_cheb(p));
+        }
+        MCK(launch_forward_from(p, p0));
+        MCK(cudaEventRecord(ev[i], p->stream));
+    }
+    // 3D: p0's inverse y-pass overwrites the buffer the others' fused passes read
+    if (p0->D == 3)
+        for (int i = 1; i < n; ++i) MCK(cudaStreamWaitEvent(st0, ev[i], 0));
+    for (int i = 0; i < n; ++i) {
+        sdf_plan p = plans[i];
+        uint8_t *fl = at(flags, i);
+        int8_t *sg = at(sign, i);
+        if (p->prec == SDF_FP32) {
+            if (!fl) fl = p->flags_int;
+            if (ww && !sg) sg = p->sign_int;
+        }
+        MCK(launch_inverse_epilogue(p, ww, at(S, i), at(dS, i), at(d2S, i), sg, fl));
+        if (p->prec == SDF_FP32) MCK(launch_fixup(p, ww, at(S, i), at(dS, i), at(d2S, i), ww ? sg : nullptr, fl));
+        if (at(flags, i)) MCK(launch_source_flags(p, at(flags, i)));
+        MCK(cudaEventRecord(ev[n + i], p->stream));
+    }
+    // join: p0's next x-pass must not overwrite what the others still read
+    for (int i = 1; i < n; ++i) MCK(cudaStreamWaitEvent(st0, ev[n + i], 0));
+#undef MCK
+    cleanup();
+    return SDF_OK;
+}
+
 // Device address of a pinned, mapped host buffer (kernels can store there
 // directly over the CPU-GPU link), else nullptr.
 static void *mapped_host(void *ptr) {

@@ -25,8 +25,14 @@ template cudaError_t fwd_T_launch<double>(const double2 *, double2 *, int, int, 
 template cudaError_t fwd_T_launch<float>(const float2 *, float2 *, int, int, int64_t, int, int64_t, int64_t,
                                          const float2 *, cudaStream_t, sdf_plan_impl *);
 
+// The forward transforms up to the fused pass's input (x-pass, and the
+// y-pass in 3D): they depend on the points and the grid, not on tau or the
+// kernels.  With `shared` (another plan of the same shape and precision that
+// ran them for the same points), p skips them and its fused pass reads that
+// plan's buffer.
 template <typename T>
-static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void *dense_in, const uint8_t *flags_in) {
+static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void *dense_in, const uint8_t *flags_in,
+                                const sdf_plan_impl *shared = nullptr, bool shared_only = false) {
     using V = cx<T>;
     cudaStream_t st = p->stream;
     cudaError_t e;
@@ -36,6 +42,13 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
     V *B = reinterpret_cast<V *>(p->bufB);
     const int64_t N0 = p->N[0], N1 = p->N[1], N2 = p->N[2];
     const int64_t M0 = p->M[0], M1 = p->M[1];
+    if (shared) {
+        // 2D: the fused input is the x-pass output (bufA); 3D: the y-pass output (bufB)
+        const V *fin = reinterpret_cast<const V *>(D == 2 ? shared->bufA : shared->bufB);
+        V *fout = D == 2 ? B : A;
+        if (D == 2) return fused_step<T>(p, fin, fout, p->logM[1], (int)N1, M0, M0 * N1, false);
+        return fused_step<T>(p, fin, fout, p->logM[2], (int)N2, M1 * M0, M1 * M0 * N2, false);
+    }
     // ---- x-pass
     {
         const int logL = p->logM[0];
@@ -103,6 +116,7 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         fused_nin = (int)N2;
         in_fs = M1 * M0 * N2;
     }
+    if (shared_only) return cudaSuccess;
     // ---- fused: forward along the last axis, multiply, inverse
     return fused_step<T>(p, fin, fout, fused_logL, fused_nin, fused_lines, in_fs, dense_in != nullptr);
 }
@@ -111,6 +125,18 @@ cudaError_t launch_forward(sdf_plan_impl *p, bool with_weights, const void *dens
                            const uint8_t *flags_in) {
     if (p->prec == SDF_FP64) return forward_impl<double>(p, with_weights, dense_in, flags_in);
     return forward_impl<float>(p, with_weights, dense_in, flags_in);
+}
+
+// The tau-independent forward transforms only (x-pass, 3D y-pass) into p's buffers.
+cudaError_t launch_forward_shared_part(sdf_plan_impl *p, bool with_weights) {
+    if (p->prec == SDF_FP64) return forward_impl<double>(p, with_weights, nullptr, nullptr, nullptr, true);
+    return forward_impl<float>(p, with_weights, nullptr, nullptr, nullptr, true);
+}
+
+// The fused pass of p on the forward transforms `shared` computed.
+cudaError_t launch_forward_from(sdf_plan_impl *p, const sdf_plan_impl *shared) {
+    if (p->prec == SDF_FP64) return forward_impl<double>(p, true, nullptr, nullptr, shared);
+    return forward_impl<float>(p, true, nullptr, nullptr, shared);
 }
 
 

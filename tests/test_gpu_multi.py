@@ -1,0 +1,79 @@
+"""sdf_execute_multi: several plans (a sweep of tau, or both kernel sets) on
+one point set share the snapping and the tau-independent forward transforms.
+Each plan's outputs must equal a separate sdf_execute bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1112_3010_gb300 as pkg
+from paper_1112_3010_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    pkg.load_library()
+
+
+def _separate_and_multi(s, taus, prec, outputs, kernels=None):
+    kernels = kernels or ["exp"] * len(taus)
+    mk = lambda: [pkg.Plan(s.D, s.dims, s.h, t, precision=prec, outputs=outputs, kernel=k)
+                  for t, k in zip(taus, kernels)]
+    x = torch.from_numpy(s.points).cuda()
+    w = torch.from_numpy(s.weights).cuda() if ("sign" in outputs and s.weights is not None) else None
+    sep_plans = mk()
+    sep = [{k: v.clone() for k, v in p.execute(x, w).items()} for p in sep_plans]
+    sep_stats = [p.stats() for p in sep_plans]
+    plans = mk()
+    outs = pkg.execute_multi(plans, x, w)
+    torch.cuda.synchronize()
+    for i, (a, b) in enumerate(zip(sep, outs)):
+        assert set(a) == set(b)
+        for k in a:
+            assert torch.equal(a[k], b[k]), (i, k)
+        st = plans[i].stats()
+        for f in ("n_fixup_nodes", "n_capped", "n_fixup_terms", "n_unique"):
+            assert getattr(st, f) == getattr(sep_stats[i], f), (i, f)
+        assert st.theta64 == sep_stats[i].theta64
+    return plans, outs
+
+
+def test_2d_fp32_tau_sweep():
+    s = wl.stars(N=256, K=3000, n_shapes=3, tau=0.004, seed=31)
+    plans, _ = _separate_and_multi(s, [0.004, 0.002, 0.008], "fp32", ("S", "dS", "d2S", "sign"))
+    assert plans[1].stats().n_fixup_nodes > 0
+
+
+def test_2d_fp64_both_kernel_sets():
+    s = wl.stars(N=200, K=2000, n_shapes=2, tau=0.006, seed=32)
+    _separate_and_multi(s, [0.006, 0.006], "fp64", ("S", "dS", "sign"), kernels=["exp", "green"])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_3d_two_taus(prec):
+    s = wl.sphere(N=40, K=3000, radius=0.3, tau=0.03, seed=33)
+    _separate_and_multi(s, [0.03, 0.02], prec, ("S", "dS", "sign"))
+
+
+def test_single_plan_and_1d():
+    s = wl.stars(N=128, K=1000, n_shapes=2, tau=0.01, seed=34)
+    _separate_and_multi(s, [0.01], "fp32", ("S", "dS", "sign"))
+    rng = np.random.default_rng(35)
+    line = wl.Shape(1, (500,), 1 / 500, 2 / 500, rng.uniform(0.3, 0.7, (80, 1)), None)
+    _separate_and_multi(line, [2 / 500, 1 / 500], "fp32", ("S", "dS", "d2S"))
+
+
+def test_mismatched_plans_rejected():
+    s = wl.stars(N=128, K=1000, n_shapes=2, tau=0.01, seed=36)
+    x = torch.from_numpy(s.points).cuda()
+    a = pkg.Plan(2, s.dims, s.h, 0.01, precision="fp32", outputs=("S",))
+    b = pkg.Plan(2, (128, 120), s.h, 0.01, precision="fp32", outputs=("S",))
+    c = pkg.Plan(2, s.dims, s.h, 0.01, precision="fp64", outputs=("S",))
+    for plans in ([a, b], [a, c], [a, a]):
+        with pytest.raises(pkg.SDFError) as ei:
+            pkg.execute_multi(plans, x)
+        assert ei.value.code == 1
+    # the plans stay usable
+    out = pkg.execute_multi([a], x)[0]
+    assert torch.isfinite(out["S"]).all()
