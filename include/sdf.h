@@ -186,10 +186,14 @@ sdf_status sdf_execute(sdf_plan plan, int64_t K, const double *points,
  * The snapping, binning and the tau-independent forward transforms (the
  * x-pass, and the y-pass in 3D: Table 1 step 3 up to the last axis) run once,
  * on plans[0]'s stream.  Each plan then runs its spectrum multiply, inverse
- * transforms, epilogue and fix-up on its own stream.  plans[0]'s stream waits
- * for all of them before it returns, so later work on plans[0]'s stream is
- * ordered after the whole call.  Results equal those of n separate
- * sdf_execute calls bit for bit.  1D plans run one sdf_execute each.
+ * transforms, epilogue and fix-up on its own stream.  The sign (winding
+ * number or degree, eqs. kappdiscreteZ, normflux) depends on neither tau nor
+ * the kernel set: with weights, plans[0] computes it and the others copy it,
+ * skipping its transforms.  plans[0]'s stream waits for all of them before
+ * the call returns, so later work on plans[0]'s stream is ordered after the
+ * whole call.  For plans with the same tile schedule, the results equal
+ * those of n separate sdf_execute calls bit for bit.  1D plans run one
+ * sdf_execute each.
  * Errors as sdf_execute; device errors are reported by sdf_sync() of the plan
  * that met them.
  */

@@ -585,7 +585,15 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
         CK(cudaMemcpyAsync(reinterpret_cast<char *>(p->dsc) + o, reinterpret_cast<const char *>(p0->dsc) + o,
                            sizeof(DevScalars) - o, cudaMemcpyDeviceToDevice, st0));
     }
-    std::vector<cudaEvent_t> ev(2 * n + 1, nullptr);
+    // the sign does not depend on tau or the kernel set: plans[0] computes it,
+    // the others read it (their fused pass and epilogue skip the mu group)
+    const bool share_sign = ww && n > 1 && (p0->outputs & SDF_OUT_SIGN);
+    int8_t *sign0 = at(sign, 0);
+    if (share_sign && !sign0) {
+        if (!p0->sign_int) CK(alloc((void **)&p0->sign_int, p0->nnodes, &p0->workspace_bytes));
+        sign0 = p0->sign_int;
+    }
+    std::vector<cudaEvent_t> ev(2 * n + 2, nullptr);
     for (auto &x : ev) CK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
     auto cleanup = [&]() {
         for (auto &x : ev) cudaEventDestroy(x);
@@ -607,7 +615,7 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
             MCK(cudaMemsetAsync(p->tile_flag, 0, p->nbins, p->stream));
             MCK(launch_cheb(p));
         }
-        MCK(launch_forward_from(p, p0));
+        MCK(launch_forward_from(p, p0, share_sign && i > 0));
         MCK(cudaEventRecord(ev[i], p->stream));
     }
     // 3D: p0's inverse y-pass overwrites the buffer the others' fused passes read
@@ -617,12 +625,20 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
         sdf_plan p = plans[i];
         uint8_t *fl = at(flags, i);
         int8_t *sg = at(sign, i);
-        if (p->prec == SDF_FP32) {
-            if (!fl) fl = p->flags_int;
-            if (ww && !sg) sg = p->sign_int;
+        if (p->prec == SDF_FP32 && !fl) fl = p->flags_int;
+        const int8_t *sin = nullptr;
+        if (share_sign && i == 0) {
+            sg = sign0;
+        } else if (share_sign) {
+            MCK(cudaStreamWaitEvent(p->stream, ev[2 * n + 1], 0));  // plans[0]'s sign is written
+            sin = sign0;
+        } else if (p->prec == SDF_FP32 && ww && !sg) {
+            sg = p->sign_int;
         }
-        MCK(launch_inverse_epilogue(p, ww, at(S, i), at(dS, i), at(d2S, i), sg, fl));
-        if (p->prec == SDF_FP32) MCK(launch_fixup(p, ww, at(S, i), at(dS, i), at(d2S, i), ww ? sg : nullptr, fl));
+        MCK(launch_inverse_epilogue(p, ww, at(S, i), at(dS, i), at(d2S, i), sg, fl, sin));
+        if (share_sign && i == 0) MCK(cudaEventRecord(ev[2 * n + 1], p->stream));
+        const int8_t *sfix = ww ? (sg ? sg : sin) : nullptr;
+        if (p->prec == SDF_FP32) MCK(launch_fixup(p, ww, at(S, i), at(dS, i), at(d2S, i), sfix, fl));
         if (at(flags, i)) MCK(launch_source_flags(p, at(flags, i)));
         MCK(cudaEventRecord(ev[n + i], p->stream));
     }

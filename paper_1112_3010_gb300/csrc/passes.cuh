@@ -541,6 +541,7 @@ struct EpiParams {
     int64_t in_fs;
     void *S, *dS, *d2S;
     int8_t *sign;
+    const int8_t *sign_in;  // the sign from another plan on the same points (no mu group then)
     uint8_t *flags;
     uint8_t *tile_flag;
     const DevScalars *dsc;
@@ -617,6 +618,17 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     T *Sout = reinterpret_cast<T *>(P.S);
     T *dS = reinterpret_cast<T *>(P.dS);
     T *d2S = reinterpret_cast<T *>(P.d2S);
+    if (P.sign_in && valid) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int x = t + m * TPL;
+            if (x >= N0) continue;
+            const int64_t node = line * N0 + x;
+            const int8_t sv = P.sign_in[node];
+            if (sv < 0) sgn &= ~(1u << m);
+            if (P.sign) P.sign[node] = sv;
+        }
+    }
 
     for (int gi = 0; gi < P.ngroup; ++gi) {
         const int g = P.order[gi];
@@ -786,6 +798,6 @@ static inline FusedParams make_fused_params(const sdf_plan_impl *p, bool adj = f
 // the kernel spectra, inverse; dense: the adjoint programme.
 template <typename T>
 cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL, int n_in, int64_t n_lines,
-                       int64_t in_fs, bool dense);
+                       int64_t in_fs, bool dense, bool skip_mu = false);
 
 }  // namespace sdf

@@ -7,7 +7,7 @@ namespace sdf {
 
 template <typename T>
 cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL, int n_in, int64_t n_lines,
-                       int64_t in_fs, bool dense) {
+                       int64_t in_fs, bool dense, bool skip_mu) {
     using V = cx<T>;
     cudaStream_t st = p->stream;
     cudaError_t e;
@@ -27,6 +27,8 @@ cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL
         const size_t smem = line_smem(R, c.L, (int)sizeof(V));
         FusedParams F = make_fused_params(p, dense);
         if (dense) F.nfield = 1;
+        // the sign group (the last) left to another plan on the same points
+        if (skip_mu && !dense && F.ngroup > 0 && p->gch[F.ngroup - 1][0] == CH_MU) --F.ngroup;
         const int64_t n_out = (D == 2) ? N1 : N2;
         const int64_t out_fs = n_lines * n_out;
         const int64_t grid = (n_lines + R - 1) / R;
@@ -71,7 +73,9 @@ cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL
     return cudaSuccess;
 }
 
-template cudaError_t fused_step<float>(sdf_plan_impl *, const float2 *, float2 *, int, int, int64_t, int64_t, bool);
-template cudaError_t fused_step<double>(sdf_plan_impl *, const double2 *, double2 *, int, int, int64_t, int64_t, bool);
+template cudaError_t fused_step<float>(sdf_plan_impl *, const float2 *, float2 *, int, int, int64_t, int64_t, bool,
+                                       bool);
+template cudaError_t fused_step<double>(sdf_plan_impl *, const double2 *, double2 *, int, int, int64_t, int64_t,
+                                        bool, bool);
 
 }  // namespace sdf

@@ -32,7 +32,8 @@ template cudaError_t fwd_T_launch<float>(const float2 *, float2 *, int, int, int
 // plan's buffer.
 template <typename T>
 static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void *dense_in, const uint8_t *flags_in,
-                                const sdf_plan_impl *shared = nullptr, bool shared_only = false) {
+                                const sdf_plan_impl *shared = nullptr, bool shared_only = false,
+                                bool skip_mu = false) {
     using V = cx<T>;
     cudaStream_t st = p->stream;
     cudaError_t e;
@@ -46,8 +47,8 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         // 2D: the fused input is the x-pass output (bufA); 3D: the y-pass output (bufB)
         const V *fin = reinterpret_cast<const V *>(D == 2 ? shared->bufA : shared->bufB);
         V *fout = D == 2 ? B : A;
-        if (D == 2) return fused_step<T>(p, fin, fout, p->logM[1], (int)N1, M0, M0 * N1, false);
-        return fused_step<T>(p, fin, fout, p->logM[2], (int)N2, M1 * M0, M1 * M0 * N2, false);
+        if (D == 2) return fused_step<T>(p, fin, fout, p->logM[1], (int)N1, M0, M0 * N1, false, skip_mu);
+        return fused_step<T>(p, fin, fout, p->logM[2], (int)N2, M1 * M0, M1 * M0 * N2, false, skip_mu);
     }
     // ---- x-pass
     {
@@ -133,10 +134,11 @@ cudaError_t launch_forward_shared_part(sdf_plan_impl *p, bool with_weights) {
     return forward_impl<float>(p, with_weights, nullptr, nullptr, nullptr, true);
 }
 
-// The fused pass of p on the forward transforms `shared` computed.
-cudaError_t launch_forward_from(sdf_plan_impl *p, const sdf_plan_impl *shared) {
-    if (p->prec == SDF_FP64) return forward_impl<double>(p, true, nullptr, nullptr, shared);
-    return forward_impl<float>(p, true, nullptr, nullptr, shared);
+// The fused pass of p on the forward transforms `shared` computed (without
+// the sign group when skip_mu: another plan computes the same sign).
+cudaError_t launch_forward_from(sdf_plan_impl *p, const sdf_plan_impl *shared, bool skip_mu) {
+    if (p->prec == SDF_FP64) return forward_impl<double>(p, true, nullptr, nullptr, shared, false, skip_mu);
+    return forward_impl<float>(p, true, nullptr, nullptr, shared, false, skip_mu);
 }
 
 

@@ -37,12 +37,13 @@ static cudaError_t inverse_mid(sdf_plan_impl *p, int ngroup, const cx<T> **last_
 
 template <typename T>
 static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, void *S, void *dS, void *d2S,
-                                         int8_t *sign, uint8_t *flags) {
+                                         int8_t *sign, uint8_t *flags, const int8_t *sign_in) {
     using V = cx<T>;
     const int D = p->D;
-    // groups actually computed: the sign group only with weights
+    // groups actually computed: the sign group only with weights, and not
+    // when the sign comes from another plan
     int ng = p->ngroup;
-    if (!with_weights) {
+    if (!with_weights || sign_in) {
         while (ng > 0 && p->gch[ng - 1][0] == CH_MU) --ng;
     }
     const V *lin = nullptr;
@@ -67,6 +68,7 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
     E.dS = dS;
     E.d2S = d2S;
     E.sign = with_weights ? sign : nullptr;
+    E.sign_in = with_weights ? sign_in : nullptr;
     E.flags = flags;
     E.tile_flag = p->tile_flag;
     E.dsc = p->dsc;
@@ -114,9 +116,9 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
 }
 
 cudaError_t launch_inverse_epilogue(sdf_plan_impl *p, bool with_weights, void *S, void *dS, void *d2S, int8_t *sign,
-                                    uint8_t *flags) {
-    if (p->prec == SDF_FP64) return inverse_epilogue_impl<double>(p, with_weights, S, dS, d2S, sign, flags);
-    return inverse_epilogue_impl<float>(p, with_weights, S, dS, d2S, sign, flags);
+                                    uint8_t *flags, const int8_t *sign_in) {
+    if (p->prec == SDF_FP64) return inverse_epilogue_impl<double>(p, with_weights, S, dS, d2S, sign, flags, sign_in);
+    return inverse_epilogue_impl<float>(p, with_weights, S, dS, d2S, sign, flags, sign_in);
 }
 
 // ---------------------------------------------------------------- adjoint epilogue
