@@ -403,6 +403,12 @@ def main():
         pool = cf.ThreadPoolExecutor(len(plans))
 
         def host_step():
+            if shared_pts:
+                # one call for both tau: the points cross once, outputs come back per tau
+                col = lambda k: [o[k] for o in host_out]
+                pkg.sdf_execute_multi_host([p.handle for p in plans], hp[0].shape[0], hp[0], hw[0], col("S"),
+                                           col("dS"), col("d2S"), col("sign"), None)
+                return
             # the public call is synchronous: one host thread per problem
             # (ctypes releases the GIL) so the two run concurrently
             futs = [pool.submit(pkg.sdf_execute_host, p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"],
@@ -419,7 +425,7 @@ def main():
         for _ in range(n_e2e):
             host_step()
         el = max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
-        h2d = sum(2 * s.K * 2 * 8 for s in shapes)
+        h2d = (2 * shapes[0].K * 2 * 8) if shared_pts else sum(2 * s.K * 2 * 8 for s in shapes)
         d2h = sum(s.n_nodes * (4 * 6 + 1) for s in shapes)
         e2e = {"value": job_throughput(world, pts_per_step, n_e2e, el), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * el / n_e2e}

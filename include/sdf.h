@@ -203,6 +203,21 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K,
                              int8_t *const *sign, uint8_t *const *flags);
 
 /*
+ * sdf_execute_multi_host -- sdf_execute_multi with HOST buffers, as
+ * sdf_execute_host is to sdf_execute: the points and weights are copied once
+ * (to plans[0]'s staging buffer); S, dS and d2S in pinned host memory are
+ * written by the kernels directly, other outputs are staged on the plan's
+ * device and copied back.  Waits for every plan's stream and returns the
+ * first non-OK status of sdf_sync() over the plans.  Errors as
+ * sdf_execute_multi.
+ */
+sdf_status sdf_execute_multi_host(int n, const sdf_plan *plans, int64_t K,
+                                  const double *points, const double *weights,
+                                  void *const *S, void *const *dS,
+                                  void *const *d2S, int8_t *const *sign,
+                                  uint8_t *const *flags);
+
+/*
  * sdf_execute_host -- sdf_execute with HOST buffers (same shapes and types):
  * copies points/weights to plan-owned device buffers, executes, brings the
  * requested outputs back, and waits for the stream.  S, dS and d2S in

@@ -34,7 +34,8 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_plan_set_noise_constants", "sdf_execute_noalloc", "sdf_batch_create",
             "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy",
             "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature", "sdf_plan_set_full_range",
-            "sdf_mesh_sources", "sdf_plan_set_kernel", "sdf_green_profile", "sdf_execute_multi"]
+            "sdf_mesh_sources", "sdf_plan_set_kernel", "sdf_green_profile", "sdf_execute_multi",
+            "sdf_execute_multi_host"]
 
 
 class SDFError(RuntimeError):
@@ -96,6 +97,7 @@ def load_library(path: str | None = None):
         L.sdf_plan_set_kernel.argtypes = [vp, ctypes.c_int]
         L.sdf_execute_multi.argtypes = [ctypes.c_int, ctypes.POINTER(vp), i64, vp, vp, ctypes.POINTER(vp),
                                         ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.sdf_execute_multi_host.argtypes = L.sdf_execute_multi.argtypes
         L.sdf_green_profile.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp]
         L.sdf_mesh_sources.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
         L.sdf_sync.argtypes = [vp]
@@ -135,7 +137,8 @@ def load_library(path: str | None = None):
         L.sdf_profile_read.restype = ctypes.c_int
         for n in ("sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
                   "sdf_plan_get_info", "sdf_get_stats", "sdf_curvature", "sdf_plan_set_full_range", "sdf_mesh_sources",
-                  "sdf_plan_set_kernel", "sdf_green_profile", "sdf_execute_multi"):
+                  "sdf_plan_set_kernel", "sdf_green_profile", "sdf_execute_multi",
+                  "sdf_execute_multi_host"):
             getattr(L, n).restype = ctypes.c_int
         _LIBH = L
         return L
@@ -184,6 +187,20 @@ def sdf_execute_multi(handles, K, points, weights, S, dS, d2S, sign, flags):
         return (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in lst])
     _ck(_lib().sdf_execute_multi(n, hv, int(K), _ptr(points), _ptr(weights), arr(S), arr(dS), arr(d2S),
                                  arr(sign), arr(flags)), "sdf_execute_multi")
+
+
+def sdf_execute_multi_host(handles, K, points, weights, S, dS, d2S, sign, flags):
+    """As sdf_execute_multi with host tensors (pinned S/dS/d2S are written by
+    the kernels directly)."""
+    n = len(handles)
+    hv = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+
+    def arr(lst):
+        if lst is None:
+            return None
+        return (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in lst])
+    _ck(_lib().sdf_execute_multi_host(n, hv, int(K), _ptr(points), _ptr(weights), arr(S), arr(dS), arr(d2S),
+                                      arr(sign), arr(flags)), "sdf_execute_multi_host")
 
 
 def sdf_execute_host(handle, K, points, weights, S, dS, d2S, sign, flags):

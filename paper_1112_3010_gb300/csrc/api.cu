@@ -704,6 +704,78 @@ sdf_status sdf_execute_host(sdf_plan p, int64_t K, const double *points, const d
     return sdf_sync(p);
 }
 
+sdf_status sdf_execute_multi_host(int n, const sdf_plan *plans, int64_t K, const double *points,
+                                  const double *weights, void *const *S, void *const *dS, void *const *d2S,
+                                  int8_t *const *sign, uint8_t *const *flags) {
+    if (n < 1 || !plans || !points || K < 1) return SDF_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!plans[i]) return SDF_ERR_INVALID_ARG;
+    auto at = [](auto *const *arr, int i) { return arr ? arr[i] : nullptr; };
+    sdf_plan p0 = plans[0];
+    const int D = p0->D;
+    const int nh = D * (D + 1) / 2;
+    // device views of every plan's outputs: pinned host memory the kernels
+    // write directly, else the plan's staging buffer (copied back below)
+    std::vector<void *> dev_S(n), dev_dS(n), dev_d2(n), mS(n), mdS(n), md2(n);
+    std::vector<int8_t *> dev_sg(n);
+    std::vector<uint8_t *> dev_fl(n);
+    double *dpts = nullptr, *dw = nullptr;
+    for (int i = 0; i < n; ++i) {
+        sdf_plan p = plans[i];
+        const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
+        const int64_t nn = p->nnodes;
+        mS[i] = mapped_host(at(S, i));
+        mdS[i] = mapped_host(at(dS, i));
+        md2[i] = mapped_host(at(d2S, i));
+        const size_t need = (i == 0) ? sizeof(double) * K * D * (weights ? 2 : 1) : 0;
+        const size_t oS = need, odS = oS + ((at(S, i) && !mS[i]) ? esz * nn : 0),
+                     od2 = odS + ((at(dS, i) && !mdS[i]) ? esz * nn * D : 0),
+                     osg = od2 + ((at(d2S, i) && !md2[i]) ? esz * nn * nh : 0), ofl = osg + (at(sign, i) ? nn : 0),
+                     tot = ofl + (at(flags, i) ? nn : 0);
+        if (tot > p->staging_bytes) {
+            cudaStreamSynchronize(p->stream);
+            cudaFree(p->staging);
+            p->staging = nullptr;
+            p->staging_bytes = 0;
+            CK(cudaMalloc((void **)&p->staging, tot));
+            p->staging_bytes = tot;
+        }
+        char *base = reinterpret_cast<char *>(p->staging);
+        if (i == 0) {
+            dpts = reinterpret_cast<double *>(base);
+            dw = weights ? dpts + K * D : nullptr;
+        }
+        dev_S[i] = at(S, i) ? (mS[i] ? mS[i] : base + oS) : nullptr;
+        dev_dS[i] = at(dS, i) ? (mdS[i] ? mdS[i] : base + odS) : nullptr;
+        dev_d2[i] = at(d2S, i) ? (md2[i] ? md2[i] : base + od2) : nullptr;
+        dev_sg[i] = at(sign, i) ? reinterpret_cast<int8_t *>(base + osg) : nullptr;
+        dev_fl[i] = at(flags, i) ? reinterpret_cast<uint8_t *>(base + ofl) : nullptr;
+    }
+    CK(cudaMemcpyAsync(dpts, points, sizeof(double) * K * D, cudaMemcpyHostToDevice, p0->stream));
+    if (weights) CK(cudaMemcpyAsync(dw, weights, sizeof(double) * K * D, cudaMemcpyHostToDevice, p0->stream));
+    sdf_status s = sdf_execute_multi(n, plans, K, dpts, dw, dev_S.data(), dev_dS.data(), dev_d2.data(),
+                                     dev_sg.data(), dev_fl.data());
+    if (s != SDF_OK) return s;
+    for (int i = 0; i < n; ++i) {
+        sdf_plan p = plans[i];
+        const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
+        const int64_t nn = p->nnodes;
+        if (at(S, i) && !mS[i]) CK(cudaMemcpyAsync(at(S, i), dev_S[i], esz * nn, cudaMemcpyDeviceToHost, p->stream));
+        if (at(dS, i) && !mdS[i])
+            CK(cudaMemcpyAsync(at(dS, i), dev_dS[i], esz * nn * D, cudaMemcpyDeviceToHost, p->stream));
+        if (at(d2S, i) && !md2[i])
+            CK(cudaMemcpyAsync(at(d2S, i), dev_d2[i], esz * nn * nh, cudaMemcpyDeviceToHost, p->stream));
+        if (at(sign, i)) CK(cudaMemcpyAsync(at(sign, i), dev_sg[i], nn, cudaMemcpyDeviceToHost, p->stream));
+        if (at(flags, i)) CK(cudaMemcpyAsync(at(flags, i), dev_fl[i], nn, cudaMemcpyDeviceToHost, p->stream));
+    }
+    sdf_status first = SDF_OK;
+    for (int i = 0; i < n; ++i) {
+        const sdf_status si = sdf_sync(plans[i]);
+        if (first == SDF_OK) first = si;
+    }
+    return first;
+}
+
 sdf_status sdf_sync(sdf_plan p) {
     if (!p) return SDF_ERR_INVALID_ARG;
     CK(cudaStreamSynchronize(p->stream));

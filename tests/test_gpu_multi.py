@@ -77,3 +77,30 @@ def test_mismatched_plans_rejected():
     # the plans stay usable
     out = pkg.execute_multi([a], x)[0]
     assert torch.isfinite(out["S"]).all()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_multi_host_matches_device(pinned):
+    """sdf_execute_multi_host: host points and outputs (pinned: written by the
+    kernels directly; pageable: staged), equal to the device results."""
+    s = wl.stars(N=256, K=3000, n_shapes=2, tau=0.004, seed=37)
+    taus = [0.004, 0.002]
+    outputs = ("S", "dS", "d2S", "sign")
+    plans = [pkg.Plan(2, s.dims, s.h, t, precision="fp32", outputs=outputs) for t in taus]
+    dev = pkg.execute_multi(plans, torch.from_numpy(s.points).cuda(), torch.from_numpy(s.weights).cuda())
+    shp = (s.dims[1], s.dims[0])
+
+    def host(shape, dtype):
+        t = torch.empty(shape, dtype=dtype)
+        return t.pin_memory() if pinned else t
+
+    outs = [{"S": host(shp, torch.float32), "dS": host((2,) + shp, torch.float32),
+             "d2S": host((3,) + shp, torch.float32), "sign": host(shp, torch.int8),
+             "flags": host(shp, torch.uint8)} for _ in taus]
+    col = lambda k: [o[k] for o in outs]
+    pkg.sdf_execute_multi_host([p.handle for p in plans], s.K, torch.from_numpy(s.points),
+                               torch.from_numpy(s.weights), col("S"), col("dS"), col("d2S"), col("sign"),
+                               col("flags"))
+    for o, d in zip(outs, dev):
+        for k in o:
+            assert torch.equal(o[k], d[k].cpu()), k
