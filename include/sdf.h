@@ -33,8 +33,9 @@
  * (u the unit roundoff), so -tau log(phi) is noise where phi is tiny (the
  * paper's Sec. 3.3).  Both paths use the same FP64 trust threshold theta_64;
  * at nodes with phi < theta_64 they return S_cap = -tau log(theta_64) (a lower
- * bound on S), zero derivatives, and set SDF_FLAG_CAPPED.  The sign is valid
- * everywhere.
+ * bound on S), zero derivatives, and set SDF_FLAG_CAPPED (an SDF_FP32 plan in
+ * full-range mode, sdf_plan_set_full_range, recomputes those nodes too and
+ * caps nothing).  The sign is valid everywhere.
  *
  * Ownership and errors.  The caller owns every points/weights/output buffer;
  * the plan owns its workspace and kernel spectra.  All calls are asynchronous
@@ -276,8 +277,8 @@ sdf_status sdf_mesh_sources(sdf_plan plan, int64_t nf, int64_t nv, const double 
 
 /*
  * sdf_curvature -- curvature fields from the grad S and Hessian planes an
- * sdf_execute wrote (Sec. 5: the derivatives give "derived quantities such as
- * curvature (Gaussian, mean and principal curvatures)" of the surface S(X)).
+ * sdf_execute wrote (Sec. 5 names the Gaussian, mean and principal
+ * curvatures of S among the uses of its derivatives, without formulas).
  *   2D: the graph z = S(x, y) as a Monge patch, W = 1 + S_x^2 + S_y^2:
  *       K = (S_xx S_yy - S_xy^2)/W^2,
  *       H = ((1 + S_y^2) S_xx - 2 S_x S_y S_xy + (1 + S_x^2) S_yy)/(2 W^{3/2}).
@@ -290,7 +291,8 @@ sdf_status sdf_mesh_sources(sdf_plan plan, int64_t nf, int64_t nv, const double 
  *            SDF_FLAG_CAPPED get 0.
  *   curv     device, 4 planes of N^D (plan type): K, H, k1, k2.
  * Caller-owned buffers; enqueued on the plan's stream (asynchronous, errors
- * as for sdf_execute).  SDF_ERR_INVALID_ARG for a NULL plan or plane.
+ * as for sdf_execute).  SDF_ERR_INVALID_ARG for a NULL plan or plane;
+ * SDF_ERR_UNSUPPORTED for a 1D plan.
  */
 sdf_status sdf_curvature(sdf_plan plan, const void *dS, const void *d2S,
                          const uint8_t *flags, void *curv);

@@ -1,5 +1,5 @@
 // points.cu -- step A1: snap the points to their nearest nodes (Sec. 6,
-// Examples 3-4: "rounded ... to the nearest grid points") and form the
+// Examples 3-4 round the points to the grid) and form the
 // scattered fields of eq. function_g (counts) and of Secs. 4.1-4.2
 // (tangent- or normal-weighted sums), as a list of distinct occupied nodes
 // grouped by 8^D-node bins.
