@@ -207,6 +207,41 @@ template <bool INV, int S, typename V> __device__ __forceinline__ void dft8s(V *
     for (int q = 0; q < 8; ++q) a[q * S] = b[q];
 }
 
+// Float lines: the butterflies' complex adds as packed FP32x2 on the (re, im)
+// pair a register already holds (sm_100+); a product by -i or +i becomes a
+// component swap with a +-1 packed multiply-add.  Each lane rounds exactly as
+// the scalar add it replaces.
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+// a + (sx b.y, sy b.x)
+__device__ __forceinline__ float2 p2addsw(float2 a, float2 b, float sx, float sy) {
+    return __ffma2_rn(make_float2(b.y, b.x), make_float2(sx, sy), a);
+}
+template <> __device__ __forceinline__ void dft4<false, float2>(float2 &a, float2 &b, float2 &c, float2 &d) {
+    const float2 t0 = p2add(a, c), t1 = p2sub(a, c), t2 = p2add(b, d), t3 = p2sub(b, d);
+    a = p2add(t0, t2);
+    c = p2sub(t0, t2);
+    b = p2addsw(t1, t3, 1.f, -1.f);  // t1 + (-i) t3
+    d = p2addsw(t1, t3, -1.f, 1.f);  // t1 - (-i) t3
+}
+template <> __device__ __forceinline__ void dft4<true, float2>(float2 &a, float2 &b, float2 &c, float2 &d) {
+    const float2 t0 = p2add(a, c), t1 = p2sub(a, c), t2 = p2add(b, d), t3 = p2sub(b, d);
+    a = p2add(t0, t2);
+    c = p2sub(t0, t2);
+    b = p2addsw(t1, t3, -1.f, 1.f);  // t1 + i t3
+    d = p2addsw(t1, t3, 1.f, -1.f);  // t1 - i t3
+}
+template <> __device__ __forceinline__ void dft2<false, float2>(float2 &a, float2 &b) {
+    const float2 t = a;
+    a = p2add(t, b);
+    b = p2sub(t, b);
+}
+template <> __device__ __forceinline__ void dft2<true, float2>(float2 &a, float2 &b) {
+    const float2 t = a;
+    a = p2add(t, b);
+    b = p2sub(t, b);
+}
+
 template <typename V> __device__ __forceinline__ V ldtw(const V *tw, int i) { return tw[i]; }
 
 // Final stage of radix P (2, 4 or 8): Ns = L/P, thread t runs butterflies
