@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
                                : 0;
     constexpr int NH = D * (D + 1) / 2;
 
-    T phi[8];
+    T phi[8];  // 1/phi per node, once the phi group is done
     T gs[D][8];
     unsigned sgn = 0xffu;   // bit m: +1 (no sign requested: all +1)
     unsigned trusted = 0;
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
                         break;
                     }
                     case CH_PHI: {
-                        phi[m] = val;
+                        phi[m] = T(1) / val;  // kept as 1/phi: every other channel divides by it
                         const bool ok = val >= theta;
                         if (ok) trusted |= 1u << m;
                         const T s = ok ? -tau * log(val) : scap;
@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
                     case CH_GY:
                     case CH_GZ: {
                         const int a = ch - CH_GX;
-                        const T gv = tr ? val / phi[m] : T(0);
+                        const T gv = tr ? val * phi[m] : T(0);
                         if (a == 0) gs[0][m] = gv;
                         if (D > 1 && a == 1) gs[1][m] = gv;
                         if (D > 2 && a == 2) gs[D - 1][m] = gv;
@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
                         if (D > 2 && a == 2) ga = gs[D - 1][m];
                         if (b == 1) gb = gs[1][m];
                         if (D > 2 && b == 2) gb = gs[D - 1][m];
-                        const T hv = tr ? (val * hs_inv) / phi[m] + ga * gb * itau : T(0);
+                        const T hv = tr ? (val * hs_inv) * phi[m] + ga * gb * itau : T(0);
                         if (d2S && c < NH) d2S[c * P.nnodes + node] = hv;
                         break;
                     }
