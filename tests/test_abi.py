@@ -106,3 +106,15 @@ def test_green_profile_host_utility():
         pkg.sdf_green_profile(2, [-1.0])
     with pytest.raises(pkg.SDFError):
         pkg.sdf_green_profile(4, [1.0])
+
+
+def test_multi_execute_rejects_bad_arguments_on_host(lib):
+    """sdf_execute_multi / _host check their arguments before any CUDA call."""
+    for fn in (lib.sdf_execute_multi, lib.sdf_execute_multi_host):
+        fn.restype = ctypes.c_int
+        vp = ctypes.c_void_p
+        pts = (ctypes.c_double * 4)()
+        plans = (vp * 2)(None, None)
+        assert fn(0, plans, ctypes.c_int64(2), pts, None, None, None, None, None, None) == 1  # n < 1
+        assert fn(2, None, ctypes.c_int64(2), pts, None, None, None, None, None, None) == 1   # no plans
+        assert fn(2, plans, ctypes.c_int64(2), pts, None, None, None, None, None, None) == 1  # NULL plan
