@@ -118,3 +118,16 @@ def test_multi_execute_rejects_bad_arguments_on_host(lib):
         assert fn(0, plans, ctypes.c_int64(2), pts, None, None, None, None, None, None) == 1  # n < 1
         assert fn(2, None, ctypes.c_int64(2), pts, None, None, None, None, None, None) == 1   # no plans
         assert fn(2, plans, ctypes.c_int64(2), pts, None, None, None, None, None, None) == 1  # NULL plan
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without the built library the binding raises, and a
+    Plan cannot be made on a machine without a GPU."""
+    import paper_1112_3010_gb300 as pkg
+    monkeypatch.setattr(pkg, "_LIBH", None)
+    with pytest.raises(ImportError):
+        pkg.load_library(str(tmp_path / "absent.so"))
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError):
+            pkg.Plan(2, (16, 16), 1 / 16, 0.1)
