@@ -324,8 +324,8 @@ sdf_status sdf_plan_set_noise_constants(sdf_plan plan, double c_fp32, double c_f
  * 2 = up to 128 registers per thread, 3 = 2D float plans: one CTA per pair of
  * mirror columns with the spectrum rows staged in shared memory (falls back to
  * 2 when it does not fit).  0 (or an invalid value, rounded down to a valid
- * one) keeps the built-in rule (3 where it fits, else 2).  Results do not
- * depend on these.
+ * one) keeps the built-in rule (2).  Results agree across schedules to the
+ * rounding of the transforms (the order of a few float operations differs).
  */
 sdf_status sdf_plan_set_tuning(sdf_plan plan, int lines_T, int lines_F, int fused_variant);
 

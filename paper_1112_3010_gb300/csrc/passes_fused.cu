@@ -34,9 +34,10 @@ cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL
         const int64_t grid = (n_lines + R - 1) / R;
         const V *twl = reinterpret_cast<const V *>(p->tw[D - 1]);
         prof_begin(p, "fused", st);
-        // paired-column variant: the built-in choice for 2D float plans that fit
+        // paired-column variant (2D float plans that fit), on request: the
+        // per-line variant below measured faster on GB300 and is the default
         const size_t smem2p = (!dense && sizeof(T) == 4) ? fused2p_smem(p) : 0;
-        if (smem2p && (p->tune_FV == 0 || p->tune_FV == 3)) {
+        if (smem2p && p->tune_FV == 3) {
 #define SDF_F2P(LG)                                                                                        \
     do {                                                                                                   \
         if ((e = set_smem<T>((const void *)k_fused2p<T, LG>, smem2p)) != cudaSuccess) return e;            \
