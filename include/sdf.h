@@ -190,7 +190,9 @@ sdf_status sdf_execute(sdf_plan plan, int64_t K, const double *points,
  * transforms, epilogue and fix-up on its own stream.  The sign (winding
  * number or degree, eqs. kappdiscreteZ, normflux) depends on neither tau nor
  * the kernel set: with weights, plans[0] computes it and the others copy it,
- * skipping its transforms.  plans[0]'s stream waits for all of them before
+ * skipping its transforms.  With two plans, one fused launch on plans[0]'s
+ * stream does both plans' products and inverse transforms on a single
+ * forward transform of the counts.  plans[0]'s stream waits for all of them before
  * the call returns, so later work on plans[0]'s stream is ordered after the
  * whole call.  For plans with the same tile schedule, the results equal
  * those of n separate sdf_execute calls bit for bit.  1D plans run one

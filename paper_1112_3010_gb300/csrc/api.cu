@@ -607,6 +607,9 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
         }                            \
     } while (0)
     MCK(cudaEventRecord(ev[2 * n], st0));
+    // two plans: one fused launch does both (the second plan's products and
+    // inverses reuse the forward transform of field 0)
+    const bool pair = n == 2;
     // per plan: Chebyshev map, the fused pass on p0's transforms
     for (int i = 0; i < n; ++i) {
         sdf_plan p = plans[i];
@@ -615,7 +618,7 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
             MCK(cudaMemsetAsync(p->tile_flag, 0, p->nbins, p->stream));
             MCK(launch_cheb(p));
         }
-        MCK(launch_forward_from(p, p0, share_sign && i > 0));
+        if (!(pair && i == 1)) MCK(launch_forward_from(p, p0, share_sign && i > 0, (pair && i == 0) ? plans[1] : nullptr));
         MCK(cudaEventRecord(ev[i], p->stream));
     }
     // 3D: p0's inverse y-pass overwrites the buffer the others' fused passes read
@@ -635,6 +638,7 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
         } else if (p->prec == SDF_FP32 && ww && !sg) {
             sg = p->sign_int;
         }
+        if (pair && i == 1) MCK(cudaStreamWaitEvent(p->stream, ev[0], 0));  // its fused pass ran on st0
         MCK(launch_inverse_epilogue(p, ww, at(S, i), at(dS, i), at(d2S, i), sg, fl, sin));
         if (share_sign && i == 0) MCK(cudaEventRecord(ev[2 * n + 1], p->stream));
         const int8_t *sfix = ww ? (sg ? sg : sin) : nullptr;

@@ -301,10 +301,13 @@ __device__ __forceinline__ void term_coef(const FusedParams &P, int g, int k, bo
 
 // Forward along the last axis, multiply by the kernel spectra, inverse along the
 // same axis, keep the first n_out outputs.  Field spectra stay in registers.
+// P1 (P1.ngroup > 0): a second plan of the same shape on the same points (a
+// different tau or kernel set), whose groups all read field 0: its products
+// and inverses reuse this CTA's forward transform of field 0 and go to out1.
 template <typename T, int D, int FV, int LOGL = 0>
 __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T> *__restrict__ in, cx<T> *out, int logL, int n_in, int n_out,
                                                int R, int64_t n_lines, int64_t in_fs, int64_t out_fs, FusedParams P,
-                                               const cx<T> *__restrict__ tw) {
+                                               const cx<T> *__restrict__ tw, FusedParams P1, cx<T> *out1) {
     using V = cx<T>;
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
@@ -342,20 +345,20 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
         __syncthreads();
         fft_line<false, LOGL>(v, my, t, logL, tws);
     };
-    auto run_group = [&](int g, const V (&A)[16], const V (&B)[16], const V (&C)[16]) {
+    auto run_group = [&](const FusedParams &Q, V *qout, int g, const V (&A)[16], const V (&B)[16], const V (&C)[16]) {
         V v[16];
 #pragma unroll
         for (int m = 0; m < 16; ++m) v[m] = mk<V>(T(0), T(0));
-        for (int k = 0; k < P.nterm[g]; ++k) {
-            const int slot = P.tk[g][k];
-            const T *c = reinterpret_cast<const T *>(P.kc[slot]);
-            const int par = P.kpar[slot];
-            const int f = P.tf[g][k];
+        for (int k = 0; k < Q.nterm[g]; ++k) {
+            const int slot = Q.tk[g][k];
+            const T *c = reinterpret_cast<const T *>(Q.kc[slot]);
+            const int par = Q.kpar[slot];
+            const int f = Q.tf[g][k];
             const bool lflip = (__popc(par & flips) & 1) != 0;
             const bool wodd = (par >> waxis) & 1;
             T alo, ahi;
             bool imag;
-            term_coef<T>(P, g, k, lflip, wodd, alo, ahi, imag);
+            term_coef<T>(Q, g, k, lflip, wodd, alo, ahi, imag);
             if (f == 2) mac_term<true>(v, C, c + cb, t, TPL, L, alo, ahi, imag);
             else if (f == 1) mac_term<true>(v, B, c + cb, t, TPL, L, alo, ahi, imag);
             else mac_term<true>(v, A, c + cb, t, TPL, L, alo, ahi, imag);
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
         __syncthreads();
         fft_line<true, LOGL>(v, my, t, logL, tws);
         if (valid) {
-            V *o = out + g * out_fs + line * n_out;
+            V *o = qout + g * out_fs + line * n_out;
 #pragma unroll
             for (int m = 0; m < 16; ++m) {
                 const int e = t + m * TPL;
@@ -378,8 +381,10 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
         bool only0 = true;
         for (int k = 0; k < P.nterm[g]; ++k) only0 &= (P.tf[g][k] == 0);
         if (!only0) break;
-        run_group(g, F0, F0, F0);
+        run_group(P, out, g, F0, F0, F0);
     }
+    // the second plan's groups, while F0 is still live
+    for (int g1 = 0; g1 < P1.ngroup; ++g1) run_group(P1, out1, g1, F0, F0, F0);
     if (g < P.ngroup) {
         load_fwd(1, F1);
         if (P.nfield > 2) load_fwd(2, F2);
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
             for (int m = 0; m < 16; ++m) F2[m] = mk<V>(T(0), T(0));
         }
         // no sign-group term reads field 0, so F0 is dead here
-        for (; g < P.ngroup; ++g) run_group(g, F1, F1, F2);
+        for (; g < P.ngroup; ++g) run_group(P, out, g, F1, F1, F2);
     }
 }
 
@@ -798,6 +803,7 @@ static inline FusedParams make_fused_params(const sdf_plan_impl *p, bool adj = f
 // the kernel spectra, inverse; dense: the adjoint programme.
 template <typename T>
 cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL, int n_in, int64_t n_lines,
-                       int64_t in_fs, bool dense, bool skip_mu = false);
+                       int64_t in_fs, bool dense, bool skip_mu = false, const sdf_plan_impl *p1 = nullptr,
+                       cx<T> *fout1 = nullptr);
 
 }  // namespace sdf

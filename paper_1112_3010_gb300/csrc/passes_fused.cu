@@ -7,7 +7,7 @@ namespace sdf {
 
 template <typename T>
 cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL, int n_in, int64_t n_lines,
-                       int64_t in_fs, bool dense, bool skip_mu) {
+                       int64_t in_fs, bool dense, bool skip_mu, const sdf_plan_impl *p1, cx<T> *fout1) {
     using V = cx<T>;
     cudaStream_t st = p->stream;
     cudaError_t e;
@@ -29,6 +29,14 @@ cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL
         if (dense) F.nfield = 1;
         // the sign group (the last) left to another plan on the same points
         if (skip_mu && !dense && F.ngroup > 0 && p->gch[F.ngroup - 1][0] == CH_MU) --F.ngroup;
+        // a second plan on the same transforms (per-line kernel only): its
+        // groups without the sign group, which reads the other fields
+        FusedParams F1;
+        memset(&F1, 0, sizeof(F1));
+        if (p1) {
+            F1 = make_fused_params(p1, false);
+            if (F1.ngroup > 0 && p1->gch[F1.ngroup - 1][0] == CH_MU) --F1.ngroup;
+        }
         const int64_t n_out = (D == 2) ? N1 : N2;
         const int64_t out_fs = n_lines * n_out;
         const int64_t grid = (n_lines + R - 1) / R;
@@ -37,7 +45,7 @@ cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL
         // paired-column variant (2D float plans that fit), on request: the
         // per-line variant below measured faster on GB300 and is the default
         const size_t smem2p = (!dense && sizeof(T) == 4) ? fused2p_smem(p) : 0;
-        if (smem2p && p->tune_FV == 3) {
+        if (smem2p && p->tune_FV == 3 && !p1) {
 #define SDF_F2P(LG)                                                                                        \
     do {                                                                                                   \
         if ((e = set_smem<T>((const void *)k_fused2p<T, LG>, smem2p)) != cudaSuccess) return e;            \
@@ -53,7 +61,7 @@ cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL
     do {                                                                                                         \
         if ((e = set_smem<T>((const void *)k_fused<T, DD, FVV, LG>, smem)) != cudaSuccess) return e;            \
         k_fused<T, DD, FVV, LG><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, n_in, (int)n_out, R, \
-                                                                      n_lines, in_fs, out_fs, F, twl);          \
+                                                                      n_lines, in_fs, out_fs, F, twl, F1, fout1); \
     } while (0)
 #define SDF_FUSED2(LG) SDF_FUSED(2, 0, LG)
 #define SDF_FUSED3(LG) SDF_FUSED(3, 0, LG)
@@ -75,8 +83,8 @@ cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL
 }
 
 template cudaError_t fused_step<float>(sdf_plan_impl *, const float2 *, float2 *, int, int, int64_t, int64_t, bool,
-                                       bool);
+                                       bool, const sdf_plan_impl *, float2 *);
 template cudaError_t fused_step<double>(sdf_plan_impl *, const double2 *, double2 *, int, int, int64_t, int64_t,
-                                        bool, bool);
+                                        bool, bool, const sdf_plan_impl *, double2 *);
 
 }  // namespace sdf

@@ -33,7 +33,7 @@ template cudaError_t fwd_T_launch<float>(const float2 *, float2 *, int, int, int
 template <typename T>
 static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void *dense_in, const uint8_t *flags_in,
                                 const sdf_plan_impl *shared = nullptr, bool shared_only = false,
-                                bool skip_mu = false) {
+                                bool skip_mu = false, const sdf_plan_impl *pair = nullptr) {
     using V = cx<T>;
     cudaStream_t st = p->stream;
     cudaError_t e;
@@ -47,8 +47,9 @@ static cudaError_t forward_impl(sdf_plan_impl *p, bool with_weights, const void 
         // 2D: the fused input is the x-pass output (bufA); 3D: the y-pass output (bufB)
         const V *fin = reinterpret_cast<const V *>(D == 2 ? shared->bufA : shared->bufB);
         V *fout = D == 2 ? B : A;
-        if (D == 2) return fused_step<T>(p, fin, fout, p->logM[1], (int)N1, M0, M0 * N1, false, skip_mu);
-        return fused_step<T>(p, fin, fout, p->logM[2], (int)N2, M1 * M0, M1 * M0 * N2, false, skip_mu);
+        V *fout1 = pair ? reinterpret_cast<V *>(D == 2 ? pair->bufB : pair->bufA) : nullptr;
+        if (D == 2) return fused_step<T>(p, fin, fout, p->logM[1], (int)N1, M0, M0 * N1, false, skip_mu, pair, fout1);
+        return fused_step<T>(p, fin, fout, p->logM[2], (int)N2, M1 * M0, M1 * M0 * N2, false, skip_mu, pair, fout1);
     }
     // ---- x-pass
     {
@@ -135,10 +136,13 @@ cudaError_t launch_forward_shared_part(sdf_plan_impl *p, bool with_weights) {
 }
 
 // The fused pass of p on the forward transforms `shared` computed (without
-// the sign group when skip_mu: another plan computes the same sign).
-cudaError_t launch_forward_from(sdf_plan_impl *p, const sdf_plan_impl *shared, bool skip_mu) {
-    if (p->prec == SDF_FP64) return forward_impl<double>(p, true, nullptr, nullptr, shared, false, skip_mu);
-    return forward_impl<float>(p, true, nullptr, nullptr, shared, false, skip_mu);
+// the sign group when skip_mu: another plan computes the same sign); with
+// `pair`, the same launch also runs that plan's groups (sign group excepted)
+// on the same forward transform of field 0.
+cudaError_t launch_forward_from(sdf_plan_impl *p, const sdf_plan_impl *shared, bool skip_mu,
+                                const sdf_plan_impl *pair) {
+    if (p->prec == SDF_FP64) return forward_impl<double>(p, true, nullptr, nullptr, shared, false, skip_mu, pair);
+    return forward_impl<float>(p, true, nullptr, nullptr, shared, false, skip_mu, pair);
 }
 
 

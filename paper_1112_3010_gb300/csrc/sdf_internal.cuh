@@ -144,7 +144,8 @@ cudaError_t launch_cheb(sdf_plan_impl *p);
 cudaError_t launch_forward(sdf_plan_impl *p, bool with_weights, const void *dense_in, int dense_mode,
                            const uint8_t *flags_in);
 cudaError_t launch_forward_shared_part(sdf_plan_impl *p, bool with_weights);
-cudaError_t launch_forward_from(sdf_plan_impl *p, const sdf_plan_impl *shared, bool skip_mu = false);
+cudaError_t launch_forward_from(sdf_plan_impl *p, const sdf_plan_impl *shared, bool skip_mu = false,
+                                const sdf_plan_impl *pair = nullptr);
 cudaError_t launch_inverse_epilogue(sdf_plan_impl *p, bool with_weights, void *S, void *dS, void *d2S,
                                     int8_t *sign, uint8_t *flags, const int8_t *sign_in = nullptr);
 cudaError_t launch_fixup(sdf_plan_impl *p, bool with_sign, void *S, void *dS, void *d2S, const int8_t *sign,
