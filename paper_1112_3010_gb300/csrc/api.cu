@@ -569,34 +569,13 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
         plans[i]->last_K = K;
         plans[i]->nlaunch = 0;
     }
-    // the points and the tau-independent forward transforms, once, on p0's stream
     cudaStream_t st0 = p0->stream;
-    CK(launch_points(p0, K, points, weights));
-    CK(launch_forward_shared_part(p0, ww));
-    // the others' fix-up, Chebyshev map and source flags read the binned points:
-    // copied here, before p0's own later kernels update its scalars
-    for (int i = 1; i < n; ++i) {
-        sdf_plan p = plans[i];
-        CK(cudaMemcpyAsync(p->bin_start, p0->bin_start, sizeof(int) * (p0->nbins + 1), cudaMemcpyDeviceToDevice, st0));
-        CK(cudaMemcpyAsync(p->bin_nuniq, p0->bin_nuniq, sizeof(int) * p0->nbins, cudaMemcpyDeviceToDevice, st0));
-        CK(cudaMemcpyAsync(p->ucell, p0->ucell, sizeof(int) * K, cudaMemcpyDeviceToDevice, st0));
-        CK(cudaMemcpyAsync(p->ucount, p0->ucount, sizeof(int) * K, cudaMemcpyDeviceToDevice, st0));
-        const size_t o = offsetof(DevScalars, wmax);
-        CK(cudaMemcpyAsync(reinterpret_cast<char *>(p->dsc) + o, reinterpret_cast<const char *>(p0->dsc) + o,
-                           sizeof(DevScalars) - o, cudaMemcpyDeviceToDevice, st0));
-    }
-    // the sign does not depend on tau or the kernel set: plans[0] computes it,
-    // the others read it (their fused pass and epilogue skip the mu group)
-    const bool share_sign = ww && n > 1 && (p0->outputs & SDF_OUT_SIGN);
-    int8_t *sign0 = at(sign, 0);
-    if (share_sign && !sign0) {
-        if (!p0->sign_int) CK(alloc((void **)&p0->sign_int, p0->nnodes, &p0->workspace_bytes));
-        sign0 = p0->sign_int;
-    }
-    std::vector<cudaEvent_t> ev(2 * n + 2, nullptr);
-    for (auto &x : ev) CK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+    // events: entry (one per plan), after each fused pass, after each plan's
+    // work, after the shared part, after plans[0]'s sign
+    std::vector<cudaEvent_t> ev(3 * n + 2, nullptr);
     auto cleanup = [&]() {
-        for (auto &x : ev) cudaEventDestroy(x);
+        for (auto &x : ev)
+            if (x) cudaEventDestroy(x);
     };
 #define MCK(x)                       \
     do {                             \
@@ -606,6 +585,37 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
             return cuda_fail(e_);    \
         }                            \
     } while (0)
+    for (auto &x : ev) MCK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+    cudaEvent_t *ev_entry = ev.data() + 2 * n + 2;
+    // st0 writes into the other plans' buffers (binned points, fused outputs):
+    // it first waits for whatever their own streams already hold
+    for (int i = 1; i < n; ++i) {
+        MCK(cudaEventRecord(ev_entry[i], plans[i]->stream));
+        MCK(cudaStreamWaitEvent(st0, ev_entry[i], 0));
+    }
+    // the points and the tau-independent forward transforms, once, on p0's stream
+    MCK(launch_points(p0, K, points, weights));
+    MCK(launch_forward_shared_part(p0, ww));
+    // the others' fix-up, Chebyshev map and source flags read the binned points:
+    // copied here, before p0's own later kernels update its scalars
+    for (int i = 1; i < n; ++i) {
+        sdf_plan p = plans[i];
+        MCK(cudaMemcpyAsync(p->bin_start, p0->bin_start, sizeof(int) * (p0->nbins + 1), cudaMemcpyDeviceToDevice, st0));
+        MCK(cudaMemcpyAsync(p->bin_nuniq, p0->bin_nuniq, sizeof(int) * p0->nbins, cudaMemcpyDeviceToDevice, st0));
+        MCK(cudaMemcpyAsync(p->ucell, p0->ucell, sizeof(int) * K, cudaMemcpyDeviceToDevice, st0));
+        MCK(cudaMemcpyAsync(p->ucount, p0->ucount, sizeof(int) * K, cudaMemcpyDeviceToDevice, st0));
+        const size_t o = offsetof(DevScalars, wmax);
+        MCK(cudaMemcpyAsync(reinterpret_cast<char *>(p->dsc) + o, reinterpret_cast<const char *>(p0->dsc) + o,
+                            sizeof(DevScalars) - o, cudaMemcpyDeviceToDevice, st0));
+    }
+    // the sign does not depend on tau or the kernel set: plans[0] computes it,
+    // the others read it (their fused pass and epilogue skip the mu group)
+    const bool share_sign = ww && n > 1 && (p0->outputs & SDF_OUT_SIGN);
+    int8_t *sign0 = at(sign, 0);
+    if (share_sign && !sign0) {
+        if (!p0->sign_int) MCK(alloc((void **)&p0->sign_int, p0->nnodes, &p0->workspace_bytes));
+        sign0 = p0->sign_int;
+    }
     MCK(cudaEventRecord(ev[2 * n], st0));
     // two plans: one fused launch does both (the second plan's products and
     // inverses reuse the forward transform of field 0)

@@ -104,3 +104,29 @@ def test_multi_host_matches_device(pinned):
     for o, d in zip(outs, dev):
         for k in o:
             assert torch.equal(o[k], d[k].cpu()), k
+
+
+def test_multi_after_pending_work_on_other_streams():
+    """Plans on their own streams, with an execute still queued on the second
+    plan's stream when the multi-execute starts: the first plan's stream
+    waits for it before writing into the second plan's buffers."""
+    s = wl.stars(N=256, K=3000, n_shapes=2, tau=0.004, seed=38)
+    x = torch.from_numpy(s.points).cuda()
+    w = torch.from_numpy(s.weights).cuda()
+    outputs = ("S", "dS", "d2S", "sign")
+    ref = [{k: v.clone() for k, v in pkg.Plan(2, s.dims, s.h, t, precision="fp32", outputs=outputs)
+            .execute(x, w).items()} for t in (0.004, 0.002)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    plans = [pkg.Plan(2, s.dims, s.h, t, precision="fp32", outputs=outputs, stream=st)
+             for t, st in zip((0.004, 0.002), streams)]
+    for _ in range(3):
+        o1 = plans[1].alloc_outputs(["S", "dS", "d2S", "sign", "flags"])
+        # queued, not waited for
+        pkg.sdf_execute(plans[1].handle, x.shape[0], x, w, o1["S"], o1["dS"], o1["d2S"], o1["sign"], o1["flags"])
+        outs = pkg.execute_multi(plans, x, w, check=False)
+        torch.cuda.synchronize()
+        for a, b in zip(ref, outs):
+            for k in a:
+                assert torch.equal(a[k], b[k]), k
+        for k in ref[1]:
+            assert torch.equal(ref[1][k], o1[k]), k
