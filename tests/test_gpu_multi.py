@@ -130,3 +130,15 @@ def test_multi_after_pending_work_on_other_streams():
                 assert torch.equal(a[k], b[k]), k
         for k in ref[1]:
             assert torch.equal(ref[1][k], o1[k]), k
+
+
+def test_multi_reports_points_off_the_grid():
+    s = wl.stars(N=128, K=1000, n_shapes=2, tau=0.01, seed=39)
+    bad = torch.from_numpy(np.concatenate([s.points, [[1.5, 0.5]]])).cuda()
+    plans = [pkg.Plan(2, s.dims, s.h, t, precision="fp32", outputs=("S", "dS")) for t in (0.01, 0.005)]
+    with pytest.raises(pkg.SDFError) as ei:
+        pkg.execute_multi(plans, bad)
+    assert ei.value.code == 3
+    # the plans stay usable
+    outs = pkg.execute_multi(plans, torch.from_numpy(s.points).cuda())
+    assert all(torch.isfinite(o["S"]).all() for o in outs)
