@@ -571,8 +571,9 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
     }
     cudaStream_t st0 = p0->stream;
     // events: entry (one per plan), after each fused pass, after each plan's
-    // work, after the shared part, after plans[0]'s sign
-    std::vector<cudaEvent_t> ev(3 * n + 2, nullptr);
+    // work, after the shared part, after plans[0]'s sign, after plans[0]'s
+    // Chebyshev map
+    std::vector<cudaEvent_t> ev(3 * n + 3, nullptr);
     auto cleanup = [&]() {
         for (auto &x : ev)
             if (x) cudaEventDestroy(x);
@@ -625,8 +626,13 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
         sdf_plan p = plans[i];
         if (i > 0) MCK(cudaStreamWaitEvent(p->stream, ev[2 * n], 0));
         if (p->prec == SDF_FP32) {
-            MCK(cudaMemsetAsync(p->tile_flag, 0, p->nbins, p->stream));
-            MCK(launch_cheb(p));
+            // with two plans, plans[0]'s map goes on the second stream, beside
+            // the fused launch that occupies its own
+            cudaStream_t sc = (pair && i == 0) ? plans[1]->stream : p->stream;
+            if (sc != p->stream) MCK(cudaStreamWaitEvent(sc, ev[2 * n], 0));
+            MCK(cudaMemsetAsync(p->tile_flag, 0, p->nbins, sc));
+            MCK(launch_cheb(p, sc));
+            if (sc != p->stream) MCK(cudaEventRecord(ev[3 * n + 2], sc));
         }
         if (!(pair && i == 1)) MCK(launch_forward_from(p, p0, share_sign && i > 0, (pair && i == 0) ? plans[1] : nullptr));
         MCK(cudaEventRecord(ev[i], p->stream));
@@ -649,6 +655,8 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
             sg = p->sign_int;
         }
         if (pair && i == 1) MCK(cudaStreamWaitEvent(p->stream, ev[0], 0));  // its fused pass ran on st0
+        if (pair && i == 0 && p->prec == SDF_FP32 && plans[1]->stream != p->stream)
+            MCK(cudaStreamWaitEvent(p->stream, ev[3 * n + 2], 0));  // its map and cleared tile flags
         MCK(launch_inverse_epilogue(p, ww, at(S, i), at(dS, i), at(d2S, i), sg, fl, sin));
         if (share_sign && i == 0) MCK(cudaEventRecord(ev[2 * n + 1], p->stream));
         const int8_t *sfix = ww ? (sg ? sg : sin) : nullptr;

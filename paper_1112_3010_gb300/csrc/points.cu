@@ -478,8 +478,8 @@ __global__ void __launch_bounds__(1024) k_sat_axis(const int *__restrict__ bin_s
     }
 }
 
-cudaError_t launch_cheb(sdf_plan_impl *p) {
-    cudaStream_t st = p->stream;
+cudaError_t launch_cheb(sdf_plan_impl *p, cudaStream_t on) {
+    cudaStream_t st = on ? on : p->stream;
     const int64_t nb0 = p->nb[0], nb1 = p->nb[1], nb2 = p->nb[2];
     unsigned char *tmp = p->cheb + p->nbins;  // second half of the allocation
     const unsigned g = (unsigned)((p->nbins + 255) / 256);

@@ -140,7 +140,7 @@ void prof_end(sdf_plan_impl *p, cudaStream_t st);
 
 // ---- launchers (defined in the .cu files) ----
 cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, const double *weights);
-cudaError_t launch_cheb(sdf_plan_impl *p);
+cudaError_t launch_cheb(sdf_plan_impl *p, cudaStream_t on = nullptr);  // on: another stream than p's
 cudaError_t launch_forward(sdf_plan_impl *p, bool with_weights, const void *dense_in, int dense_mode,
                            const uint8_t *flags_in);
 cudaError_t launch_forward_shared_part(sdf_plan_impl *p, bool with_weights);
