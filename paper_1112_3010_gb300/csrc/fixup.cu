@@ -21,7 +21,11 @@
 // even its sum plus T is below theta_64 (it stays capped).  Rings go in batches
 // that end at the first ring where some node could meet one of these tests
 // (a bound from its sums so far), so there are few batches per tile and no
-// node sums past its own stopping ring.  The log-sum-exp shift
+// node sums past its own stopping ring.  In 3D a warp also skips a staged
+// bin when, for each of its active nodes, the bin's whole box lies so far out
+// that all the batch's points there would add under 1e-6 of the node's sum so
+// far (the cube of rings holds many points outside that sphere).  The
+// log-sum-exp shift
 // m is the nearest point found by a cheap pass over the first batch of points
 // (and over a later batch only if it could hold a point so much nearer that a
 // term would exceed 2^60), so the summing loop itself has no branch.  A
@@ -330,7 +334,12 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
                                       (float)(qz * 8 + (lc >> 6)), (float)P.ucount[src]);
             }
             __syncthreads();
-            if ((active[0] || active[1]) && ncell > 0) {
+            // 3D: every lane of a warp with an active node runs the loops
+            // below (the bin votes need the whole warp); lanes with none add
+            // terms that are never written
+            const bool me = active[0] || active[1];
+            const bool run = (D == 3) ? __any_sync(0xffffffffu, me) : me;
+            if (run && ncell > 0) {
                 // the shift m need not be the exact minimum, only keep every
                 // term in range: no shift yet, or a batch point that could
                 // be nearer than m by more than 60 tau ln 2 (term > 2^60),
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
                 // nearest point may then lie a bin diagonal (7 sqrt(D) nodes)
                 // beyond the box bound, its term 2^(-7 sqrt(D) l2e_th)
                 const bool by_bins = 7.f * ((D == 2) ? 1.4143f : 1.7321f) * l2e_th < 60.f;
-                if (mg[0] - lb_in > lim || mg[1] - lb_in > lim) {
+                if (me && (mg[0] - lb_in > lim || mg[1] - lb_in > lim)) {
                     float mn[NPT] = {INFINITY, INFINITY};
                     if (by_bins) {
                         // distance to the nearest occupied bin's box: a lower
@@ -389,10 +398,51 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
                         }
                     }
                 }
-                nterm += (unsigned)ncell * ((mine[0] ? 1u : 0u) + (mine[1] ? 1u : 0u));
+                const unsigned nmine = me ? (mine[0] ? 1u : 0u) + (mine[1] ? 1u : 0u) : 0u;
+                // 3D: a bin whose points all lie at least rho_j from node j adds
+                // at most n e^{-(rho_j - m_j)/tau} to its sum (relative to
+                // e^{-m_j/tau}), n <= the points in the box of rings <= k1.
+                // rho_j makes that at most 1e-6 of the sum so far (2^-19.93),
+                // so the batch's skipped terms stay below 1e-6 of the final
+                // sum; the warp skips the bin when none of its active nodes
+                // needs it.  No sum yet: nothing is skipped.  (The points of
+                // a 2D tile's bins are few, and the per-bin loop measured
+                // slower there: 2D sums every staged point in one loop.)
+                float rho2[NPT] = {INFINITY, INFINITY};
+                bool cull = false;
+                if constexpr (D == 3) {
+#pragma unroll
+                    for (int j = 0; j < NPT; ++j) {
+                        const float sj = j ? sE.y : sE.x;
+                        const float rho = mg[j] + (__log2f((float)s_cnt[0]) + 19.94f - __log2f(sj)) / l2e_th;
+                        rho2[j] = (active[j] && sj > 0.f && mg[j] < INFINITY) ? rho * rho : INFINITY;
+                    }
+                    cull = __any_sync(0xffffffffu, rho2[0] < INFINITY || rho2[1] < INFINITY);
+                }
                 const float2 nl2e = dup2(-l2e_th), ih2 = dup2(ih), itau2 = dup2(itau);
+                const int nloop = (D == 3) ? taken : 1;
+                for (int b = 0; b < nloop; ++b) {
+                    const int e0 = (D == 3) ? soff[b] : 0, e1 = (D == 3) ? soff[b + 1] : ncell;
+                    if (e0 == e1) continue;
+                    if (cull) {
+                        // squared distance from each node to the bin's box
+                        const float4 bq = sbox[b];
+                        const float ex = fmaxf(fmaxf(bq.x - xf, xf - (bq.x + 7.f)), 0.f);
+                        const float ey = (D == 2) ? 0.f : fmaxf(fmaxf(bq.y - yf, yf - (bq.y + 7.f)), 0.f);
+                        const float base = fmaf(ex, ex, ey * ey);
+                        bool skip = true;
+#pragma unroll
+                        for (int j = 0; j < NPT; ++j) {
+                            const float c = (D == 2) ? yf + kOff * j : zf + kOff * j;
+                            const float lo = (D == 2) ? bq.y : bq.z;
+                            const float ec = fmaxf(fmaxf(lo - c, c - (lo + 7.f)), 0.f);
+                            skip = skip && (!active[j] || fmaf(ec, ec, base) >= rho2[j]);
+                        }
+                        if (__all_sync(0xffffffffu, skip)) continue;
+                    }
+                    nterm += (unsigned)(e1 - e0) * nmine;
 #pragma unroll 2
-                for (int e = 0; e < ncell; ++e) {
+                for (int e = e0; e < e1; ++e) {
                     const float4 q = cell[e];
                     const float d0 = xf - q.x, d1 = yf - q.y;
                     const float cl = (D == 2) ? d1 : zf - q.z;
@@ -426,6 +476,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
                             }
                         }
                     }
+                }
                 }
             }
             __syncthreads();
