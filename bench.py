@@ -3,17 +3,20 @@
 Workload (the 2D mixed-precision configuration): a 2048^2 grid (h = 1/2048,
 padded to 4096^2), K = 40000 points sampled along 8 seeded non-intersecting
 star polygons with chord tangents, tau in {0.002, 0.0005}; outputs S (signed),
-grad S, Hessian and sign.  One step = one execute per tau value.  Inputs are
-resident in HBM before the timed region; L2 is flushed (256 MiB write) between
-timed steps, outside the CUDA-event brackets.  The two problems of a step are
-independent: each plan has its own stream, forked from and joined back to the
-timing stream, so they run concurrently (the FP64 path the same way).
+grad S, Hessian and sign.  One step = every output at both tau values, through
+one sdf_execute_multi (the points and the tau-independent transforms once,
+each tau's passes on its own stream).  Inputs are resident in HBM before the
+timed region; L2 is flushed (256 MiB write) between timed steps, outside the
+CUDA-event brackets.
 
-Also reported: the same metric through sdf_execute_host (host buffers, copies
-inside the timed region), the plain FP64 GPU path with max|S - S_FP64| over its
-trust region, the dominant kernel's roofline from live CUDA events, the FP64
-oracle's throughput on the host cores (bounded sample), and SM clocks sampled
-during the timed region.
+Also reported: the same metric through sdf_execute_multi_host (host buffers,
+copies inside the timed region), the plain FP64 GPU path with max|S - S_FP64|
+over its trust region beside the library's own error report, the dominant
+kernel's roofline from live CUDA events, the FP64 oracle's throughput on the
+host cores (bounded sample), SM clocks sampled during the timed region, and
+the other configurations under the same clock: the 3D mixed workload (c3), the
+96-shape batch (c4), the 3D adjoint (c5), and the 2D workload in full-range
+mode (every node from the paper's S, none capped).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -119,9 +122,12 @@ def workloads():
     return [wl.config_c2(tau=t) for t in TAUS]
 
 
-def cpu_baseline(shapes, n_nodes=12288, seed=0):
+def cpu_baseline(shapes, n_nodes=12288, seed=0, keep=None):
     """The FP64 oracle (as it stands) on a seeded random sample of nodes of
-    each tau's grid: S, grad S, Hessian and mu.  Returns grid pts/s."""
+    each tau's grid: S, grad S, Hessian and mu.  Returns grid pts/s.  With
+    `keep` (a list), the sampled node indices and the oracle's values there
+    are appended to it, one (sel, values) pair per shape: the full-range leg
+    compares its outputs with them."""
     import oracle
     rng = np.random.default_rng(seed)
     total_t, total_n = 0.0, 0
@@ -132,9 +138,11 @@ def cpu_baseline(shapes, n_nodes=12288, seed=0):
         sel = rng.choice(s.n_nodes, n_nodes // len(shapes), replace=False)
         X = oracle.grid_nodes(s.dims, s.h, sel)
         t0 = time.perf_counter()
-        oracle.evaluate(Y, X, s.tau, weights=W, want=("S", "dS", "d2S", "mu"))
+        ref = oracle.evaluate(Y, X, s.tau, weights=W, want=("S", "dS", "d2S", "mu"))
         total_t += time.perf_counter() - t0
         total_n += len(sel)
+        if keep is not None:
+            keep.append((sel, ref))
     rate = total_n / total_t
     # every node costs the oracle the same (a sum over all points), so a
     # uniform sample gives the full grid's time by proportion
@@ -218,6 +226,244 @@ def measured_traffic(kernel, n_launch_terms=None):
     return d["bytes_per_launch"]
 
 
+def fork_join(torch, run, main, streams):
+    """run() enqueues on `streams` after everything already on `main`;
+    `main` then waits for all of them."""
+    fork = torch.cuda.Event()
+    fork.record(main)
+    for st in streams:
+        st.wait_event(fork)
+    run()
+    for st in streams:
+        main.wait_stream(st)
+
+
+class C2Problem:
+    """The benchmarked configuration, set up and stepped exactly as the
+    headline number is measured: one FP32 plan per tau, each on its own
+    stream, outputs S, grad S, Hessian, sign and flags; the tile schedule
+    chosen by sdf_plan_autotune on the workload itself; a step is one
+    sdf_execute_multi over both plans (the one point set snapped and
+    transformed once), forked from and joined back to `self.stream`."""
+
+    def __init__(self, torch, pkg, tune=True, reps=2, full_range=False, tuning=None):
+        self.torch, self.pkg = torch, pkg
+        self.shapes = workloads()
+        self.stream = torch.cuda.Stream()
+        self.pstreams = [torch.cuda.Stream() for _ in self.shapes]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(self.stream):
+            self.plans = [pkg.Plan(2, s.dims, s.h, s.tau, precision="fp32", outputs=("S", "dS", "d2S", "sign"),
+                                   stream=ps, full_range=full_range) for s, ps in zip(self.shapes, self.pstreams)]
+            self.pts = [torch.from_numpy(s.points).cuda() for s in self.shapes]
+            self.wts = [torch.from_numpy(s.weights).cuda() for s in self.shapes]
+            self.outs = [p.alloc_outputs(["S", "dS", "d2S", "sign", "flags"]) for p in self.plans]
+        torch.cuda.synchronize()
+        self.tuning = []
+        if tuning is not None:
+            for p, t in zip(self.plans, tuning):
+                pkg.sdf_plan_set_tuning(p.handle, *t)
+            self.tuning = list(tuning)
+        elif tune:
+            # plan-time work, untimed
+            for p, x, w in zip(self.plans, self.pts, self.wts):
+                self.tuning.append(pkg.sdf_plan_autotune(p.handle, x.shape[0], x, w, reps))
+        self.shared_pts = all(np.array_equal(s.points, self.shapes[0].points) and
+                              np.array_equal(s.weights, self.shapes[0].weights) for s in self.shapes)
+
+    def step(self, serial=False):
+        pkg, torch = self.pkg, self.torch
+        plans, pts, wts, outs = self.plans, self.pts, self.wts, self.outs
+
+        def run():
+            if self.shared_pts:
+                col = lambda k: [o[k] for o in outs]
+                pkg.sdf_execute_multi([p.handle for p in plans], pts[0].shape[0], pts[0], wts[0], col("S"),
+                                      col("dS"), col("d2S"), col("sign"), col("flags"))
+                return
+            for p, x, w, o in zip(plans, pts, wts, outs):
+                pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], o["flags"])
+        if not serial:
+            fork_join(torch, run, self.stream, self.pstreams)
+            return
+        # one problem at a time (the kernel-timing pass)
+        for p, x, w, o, ps in zip(plans, pts, wts, outs, self.pstreams):
+            fork_join(torch, lambda: pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"],
+                                                     o["sign"], o["flags"]), self.stream, [ps])
+
+    def close(self):
+        for p in self.plans:
+            p.close()
+
+
+def _timed(torch, stream, flush, steps, fn):
+    """Device time of fn() per call (ms, mean over `steps`), CUDA events on
+    `stream`, L2 flushed before each call outside the events."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def _dominant(prof_items):
+    tot = sum(t for _, (n, t) in prof_items) or 1e-12
+    name, (n, t) = max(prof_items, key=lambda kv: kv[1][1])
+    return {"kernel": name, "share": t / tot, "avg_ms": t / max(1, n)}
+
+
+def bench_c3(torch, pkg, flush, steps):
+    """3D mixed precision: 256^3 grid padded to 512^3, K = 200000 on a torus
+    plus a sphere, tau = 0.004, outputs S, grad S, sign; against the FP64 path."""
+    from paper_1112_3010_gb300 import workloads as wl
+    s = wl.config_c3()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        pts = torch.from_numpy(s.points).cuda()
+        w = torch.from_numpy(s.weights).cuda()
+    res = {"workload": "3D mixed: 256^3 grid padded to 512^3, K=200000 on a torus + sphere, tau=0.004, "
+                       "outputs S, grad S, sign"}
+    outs = {}
+    for prec in ("fp32", "fp64"):
+        with torch.cuda.stream(st):
+            p = pkg.Plan(3, s.dims, s.h, s.tau, precision=prec, outputs=("S", "dS", "sign"), stream=st)
+            o = p.alloc_outputs(["S", "dS", "sign", "flags"])
+        run = lambda: pkg.sdf_execute(p.handle, s.K, pts, w, o["S"], o["dS"], None, o["sign"], o["flags"])
+        with torch.cuda.stream(st):
+            run()
+        p.sync()
+        ms = _timed(torch, st, flush, steps if prec == "fp32" else max(2, steps // 2), run)
+        p.profile(True)
+        p.profile_read()
+        _timed(torch, st, flush, 1, run)
+        prof = p.profile_read()
+        p.profile(False)
+        stt = p.stats()
+        res[prec] = {"ms_per_execute": ms, "grid_pts_per_s": s.n_nodes / (ms * 1e-3),
+                     "dominant_kernel": _dominant(list(prof.items())),
+                     "err_bound_S_over_tau": stt.err_bound_S / s.tau, "err_bound_dS": stt.err_bound_dS,
+                     "trusted_frac": stt.trusted_frac}
+        if prec == "fp32":
+            res[prec]["fixup_terms"] = stt.n_fixup_terms
+            res[prec]["fixup_nodes"] = stt.n_fixup_nodes
+        outs[prec] = (o, stt)
+        p.close()
+    (o32, b32), (o64, b64) = outs["fp32"], outs["fp64"]
+    ok = ((o32["flags"] & pkg.SDF_FLAG_CAPPED) == 0) & ((o64["flags"] & pkg.SDF_FLAG_CAPPED) == 0)
+    u32 = o32["S"].double() * o32["sign"].double()
+    u64 = o64["S"].double() * o64["sign"].double()
+    res["max_abs_S_minus_S64_over_tau"] = (u32 - u64)[ok].abs().max().item() / s.tau
+    res["bound_S_32_plus_64_over_tau"] = (b32.err_bound_S + b64.err_bound_S) / s.tau
+    res["sign_diff_in_trust_region"] = int(((o32["sign"] != o64["sign"]) & ok).sum().item())
+    res["speedup_mixed_over_fp64"] = res["fp64"]["ms_per_execute"] / res["fp32"]["ms_per_execute"]
+    return res
+
+
+def bench_c4(torch, pkg, flush, steps):
+    """The batch: 96 independent 2D shapes (sides 256-1024, K 500-20000,
+    tau = 2h), outputs S and sign, FP32, one graph launch per step."""
+    from paper_1112_3010_gb300 import workloads as wl
+    shapes = wl.batch_stars(n=96, seed=4)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        b = pkg.Batch(2, [x.dims for x in shapes], [x.h for x in shapes], [x.tau for x in shapes],
+                      precision="fp32", outputs=("S", "sign"), n_streams=8, stream=st)
+        pts = [torch.from_numpy(x.points).cuda() for x in shapes]
+        wts = [torch.from_numpy(x.weights).cuda() for x in shapes]
+        outs = b.alloc_outputs()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        b.execute(pts, wts, outs)   # plain run + graph capture
+        b.execute(pts, wts, outs)
+    b.sync()
+    ms = _timed(torch, st, flush, steps, lambda: b.execute(pts, wts, outs))
+    b.sync()
+    n_pts = sum(x.n_nodes for x in shapes)
+    padded = []
+    for i in range(len(shapes)):
+        inf = pkg.sdf_plan_get_info(pkg.sdf_batch_plan(b.handle, i))
+        padded.append(int(inf.padded[0]))
+    b.close()
+    sides = sorted(set(x.dims[0] for x in shapes))
+    return {"workload": "96 2D shapes (seed 4): sides uniform over {256,384,512,768,1024}, K 500-20000, "
+                        "tau=2h, outputs S, sign; one CUDA-graph launch",
+            "ms_per_batch": ms, "grid_pts": n_pts, "grid_pts_per_s": n_pts / (ms * 1e-3),
+            "padded_by_side": {str(sd): sorted(set(m for x, m in zip(shapes, padded) if x.dims[0] == sd))
+                               for sd in sides}}
+
+
+def bench_c5(torch, pkg, flush, steps):
+    """Differentiation: 128^3 grid, K = 20000 jittered sphere points (the
+    library snaps them), tau = 0.01, FP32; forward (S, grad S) and the
+    adjoint of L = sum w S, with w ~ N(0, 1) on a band of half-width tau
+    around the sphere (0 elsewhere)."""
+    from paper_1112_3010_gb300 import workloads as wl
+    s = wl.config_c5()
+    Y = np.ascontiguousarray(s.points)
+    n = s.dims[0]
+    g = np.arange(n) * s.h - 0.5
+    zz, yy, xx = np.meshgrid(g, g, g, indexing="ij")   # x fastest, as the grid arrays
+    d = np.abs(np.sqrt(xx * xx + yy * yy + zz * zz).ravel() - 0.3)
+    wv = wl.loss_weights(s.n_nodes, seed=50)
+    wv[d > s.tau] = 0.0
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        p = pkg.Plan(3, s.dims, s.h, s.tau, precision="fp32", outputs=("S", "dS"), stream=st)
+        pts = torch.from_numpy(Y).cuda()
+        o = p.alloc_outputs(["S", "dS", "flags"])
+        wt = torch.from_numpy(wv).float().cuda().reshape(o["S"].shape)
+        dY = torch.empty_like(pts)
+        dtau = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fwd = lambda: pkg.sdf_execute(p.handle, pts.shape[0], pts, None, o["S"], o["dS"], None, None, o["flags"])
+    bwd = lambda: pkg.sdf_backward(p.handle, pts.shape[0], pts, wt, o["S"], o["flags"], dY, dtau)
+    with torch.cuda.stream(st):
+        fwd()
+        bwd()
+    p.sync()
+    ms_f = _timed(torch, st, flush, steps, fwd)
+    ms_b = _timed(torch, st, flush, steps, bwd)
+    p.sync()
+    p.close()
+    return {"workload": "3D adjoint: 128^3 grid padded to 256^3, K=20000 jittered sphere points (snapped), "
+                        "tau=0.01, FP32; dL/dY and dL/dtau of L = sum w S",
+            "forward_ms": ms_f, "backward_ms": ms_b, "grid_pts_per_s_forward_plus_backward":
+                s.n_nodes / ((ms_f + ms_b) * 1e-3)}
+
+
+def bench_full_range(torch, pkg, flush, steps, tuning, samples=None):
+    """The 2D workload in full-range mode: every node from the paper's S
+    (the fix-up sums whatever the float transform does not trust, nothing is
+    capped).  Accuracy against the oracle values the cpu_baseline leg
+    computed on its sampled nodes (`samples`, when that leg ran)."""
+    prob = C2Problem(torch, pkg, tune=False, full_range=True, tuning=tuning or None)
+    with torch.cuda.stream(prob.stream):
+        prob.step()
+    torch.cuda.synchronize()
+    ms = _timed(torch, prob.stream, flush, steps, prob.step)
+    stats = [p.stats() for p in prob.plans]
+    acc = []
+    for i, (s, o, st) in enumerate(zip(prob.shapes, prob.outs, stats)):
+        a = {"tau": s.tau, "capped": st.n_capped, "fixup_nodes": st.n_fixup_nodes,
+             "fixup_terms": st.n_fixup_terms, "err_bound_S_over_tau": st.err_bound_S / s.tau,
+             "err_bound_dS": st.err_bound_dS}
+        if samples is not None and i < len(samples):
+            sel, ref = samples[i]
+            S = (o["S"].double() * o["sign"].double()).cpu().numpy().ravel()[sel]
+            G = o["dS"].double().cpu().numpy().reshape(2, -1)[:, sel].T
+            a["sampled_nodes"] = int(len(sel))
+            a["max_abs_S_minus_oracle_over_tau"] = float(np.abs(S - ref["S"]).max() / s.tau)
+            a["max_abs_dS_minus_oracle"] = float(np.abs(G - ref["dS"]).max())
+        acc.append(a)
+    n_pts = sum(s.n_nodes for s in prob.shapes)
+    prob.close()
+    return {"ms_per_step": ms, "grid_pts_per_s": n_pts / (ms * 1e-3),
+            "sample": "the cpu_baseline leg's random nodes, against its FP64 oracle values", "accuracy": acc}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,6 +474,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the c3/c4/c5/full-range legs")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -245,59 +492,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     pkg.load_library()
-    stream = torch.cuda.Stream()
-    shapes = workloads()
-    # one stream per problem: the two executes of a step run concurrently (one
-    # problem's ALU-bound fix-up overlaps the other's memory-bound passes)
-    pstreams = [torch.cuda.Stream() for _ in shapes]
-    torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        plans = [pkg.Plan(2, s.dims, s.h, s.tau, precision="fp32", outputs=("S", "dS", "d2S", "sign"),
-                          stream=ps) for s, ps in zip(shapes, pstreams)]
-        pts = [torch.from_numpy(s.points).cuda() for s in shapes]
-        wts = [torch.from_numpy(s.weights).cuda() for s in shapes]
-        outs = [p.alloc_outputs(["S", "dS", "d2S", "sign", "flags"]) for p in plans]
-    # tile schedule chosen by the library's autotuner (plan-time work, untimed)
-    tuning = []
-    if not args.no_tune:
-        for p, x, w in zip(plans, pts, wts):
-            tuning.append(pkg.sdf_plan_autotune(p.handle, x.shape[0], x, w, 2))
+    prob = C2Problem(torch, pkg, tune=not args.no_tune)
+    stream, pstreams, shapes, plans = prob.stream, prob.pstreams, prob.shapes, prob.plans
+    pts, wts, outs, tuning, shared_pts = prob.pts, prob.wts, prob.outs, prob.tuning, prob.shared_pts
+    step = prob.step
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
-
-    def fork_join(run, main, streams):
-        """run() enqueues on `streams` after everything already on `main`;
-        `main` then waits for all of them."""
-        fork = torch.cuda.Event()
-        fork.record(main)
-        for st in streams:
-            st.wait_event(fork)
-        run()
-        for st in streams:
-            main.wait_stream(st)
-
-    # the problems of a step are one point set at several tau: one
-    # sdf_execute_multi snaps the points and runs the tau-independent
-    # transforms once, then each tau's passes on its own stream
-    shared_pts = all(np.array_equal(s.points, shapes[0].points) and np.array_equal(s.weights, shapes[0].weights)
-                     for s in shapes)
-
-    def step(serial=False):
-        def run():
-            if shared_pts:
-                col = lambda k: [o[k] for o in outs]
-                pkg.sdf_execute_multi([p.handle for p in plans], pts[0].shape[0], pts[0], wts[0], col("S"),
-                                      col("dS"), col("d2S"), col("sign"), col("flags"))
-                return
-            for p, x, w, o in zip(plans, pts, wts, outs):
-                pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], o["flags"])
-        if not serial:
-            fork_join(run, stream, pstreams)
-            return
-        # one problem at a time (the kernel-timing pass)
-        for p, x, w, o, ps in zip(plans, pts, wts, outs, pstreams):
-            fork_join(lambda: pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"],
-                                              o["flags"]), stream, [ps])
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -448,7 +648,7 @@ def main():
                     return
                 for p, x, w, o in zip(p64, pts, wts, o64):
                     pkg.sdf_execute(p.handle, x.shape[0], x, w, o["S"], o["dS"], o["d2S"], o["sign"], o["flags"])
-            fork_join(run, stream, pstreams)
+            fork_join(torch, run, stream, pstreams)
 
         with torch.cuda.stream(stream):
             step64()
@@ -477,9 +677,14 @@ def main():
             dG = (o32["dS"].double() - o_64["dS"].double()).abs()[:, m].max().item() if m.any() else 0.0
             dH = (o32["d2S"].double() - o_64["d2S"].double()).abs()[:, m].max().item() if m.any() else 0.0
             sgn_mis = int(((o32["sign"] != o_64["sign"]) & m).sum().item())
+            st32 = next(st for st, s2 in zip(stats, shapes) if s2 is s)
             acc.append({"tau": s.tau, "max_abs_S_minus_S64_over_tau": dS / s.tau, "max_abs_dS": dG,
                         "max_abs_d2S_times_tau": dH * s.tau, "trusted_frac": m.float().mean().item(),
-                        "sign_diff_in_trust_region": sgn_mis})
+                        "sign_diff_in_trust_region": sgn_mis,
+                        # the library's own error report: |S_32 - S_64| <= bound_32 + bound_64
+                        "reported_bound_S_over_tau": (st32.err_bound_S + st64.err_bound_S) / s.tau,
+                        "reported_bound_dS": st32.err_bound_dS + st64.err_bound_dS,
+                        "reported_bound_d2S_times_tau": (st32.err_bound_d2S + st64.err_bound_d2S) * s.tau})
         fp64 = {"ms_per_step": ms64, "value": pts_per_step / (ms64 * 1e-3), "unit": UNIT,
                 "speedup_mixed_over_fp64": (value / world) / (pts_per_step / (ms64 * 1e-3)),
                 "accuracy": acc}
@@ -487,8 +692,20 @@ def main():
             p.close()
 
     cpu = None
+    samples = []
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(shapes)
+        cpu = cpu_baseline(shapes, keep=samples)
+
+    # the other configurations under the same clock (one GPU, rank 0 alone)
+    extra = {}
+    if world == 1 and not args.no_extra:
+        for p in plans:
+            p.sync()
+        ext_steps = max(3, min(args.steps, 10))
+        extra["full_range"] = bench_full_range(torch, pkg, flush, max(2, ext_steps // 2), tuning, samples or None)
+        extra["c3"] = bench_c3(torch, pkg, flush, ext_steps)
+        extra["c4"] = bench_c4(torch, pkg, flush, ext_steps)
+        extra["c5"] = bench_c5(torch, pkg, flush, ext_steps)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -506,6 +723,9 @@ def main():
                        "tile_schedule": [{"lines_T": a, "lines_F": b, "fused_variant": c} for a, b, c in tuning]},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "kernels": per_kernel, "fft_passes": passes, "fp64_path": fp64,
+            "error_report": [{"tau": s.tau, "err_bound_S_over_tau": st.err_bound_S / s.tau,
+                              "err_bound_dS": st.err_bound_dS, "err_bound_d2S_times_tau": st.err_bound_d2S * s.tau,
+                              "trusted_frac": st.trusted_frac} for s, st in zip(shapes, stats)],
             "fixup": [{"tau": s.tau, "tiles": st.n_fixup_tiles, "nodes": st.n_fixup_nodes,
                        "capped": st.n_capped, "terms": st.n_fixup_terms, "theta32": st.theta32,
                        "theta64": st.theta64,
@@ -513,6 +733,7 @@ def main():
                        "terms_per_s": st.n_fixup_terms / max(1e-12, 1e-3 * pp.get("fixup", (1, 0.0))[1]
                                                              / max(1, pp.get("fixup", (1, 0.0))[0]))}
                       for s, st, pp in zip(shapes, stats, per_plan)]}
+    line.update(extra)
     if rank == 0:
         print(json.dumps(line))
     for p in plans:

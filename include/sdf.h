@@ -96,7 +96,8 @@ typedef struct {
     int64_t dims[3];          /* N_a                                       */
     int64_t padded[3];        /* M_a                                       */
     double h, tau;
-    double kernel_l1[16];     /* l1 norm of each sampled kernel (see sdf.cu) */
+    double kernel_l1[16];     /* l1 norm of each sampled kernel on the     */
+                              /* padded grid, in plan order (unscaled)     */
     int n_kernels;
     double noise_const_fp32;  /* C in the noise model, float transforms    */
     double noise_const_fp64;  /* C in the noise model, double transforms   */
@@ -116,6 +117,23 @@ typedef struct {
     int64_t n_capped;    /* nodes returned as S_cap (flag CAPPED)              */
     int64_t n_launches;  /* kernels the last execute launched                  */
     int64_t n_fixup_terms;  /* (node, occupied node) terms the fix-up summed   */
+    /* Error report of the last execute, over the nodes NOT flagged CAPPED: a
+     * priori bounds on |S - S_exact|, on each component of |grad S - exact|
+     * and of |Hessian - exact| (0 when not requested), S_exact being the
+     * paper's S (eq. STilde, in the shifted form of eq. Bound1) of the snapped
+     * points in exact arithmetic.  They combine the transform error model of
+     * the trust region (relative error of phi at most
+     * (eps f/Q)/(1 - eps f/Q) where phi >= theta, eps = 2.5e-4, f and Q the
+     * l1-norm terms of the model), the fix-up's tail, term and summation
+     * errors (SDF_FP32 plans), and the rounding of the outputs.  For an
+     * SDF_FP32 plan and an SDF_FP64 plan of the same problem,
+     * |S_32 - S_64| <= err_bound_S(32) + err_bound_S(64) wherever neither is
+     * capped.  Like the trust region, the transform part is a bound under the
+     * calibrated noise model, not a proof. */
+    double err_bound_S;
+    double err_bound_dS;
+    double err_bound_d2S;
+    double trusted_frac; /* fraction of the N^D nodes not flagged CAPPED        */
 } sdf_exec_stats;
 
 /* Per-kernel device time, filled by sdf_profile_read(). */
@@ -472,9 +490,10 @@ void sdf_batch_destroy(sdf_batch batch);
  * inside this library; every GPU that loads the library holds it until the
  * process exits.  The caller still owns points, weights and outputs.
  *
- *   D, dims, h, tau, precision, outputs   as sdf_plan_create
- *   K, points, weights, S, dS, d2S, sign, flags   as sdf_execute
- *   stream     cudaStream_t (as void*) for the work
+ *   D, dims, h, tau, precision, outputs   as sdf_plan_create (D = 2 or 3)
+ *   K, points, weights, S, dS, d2S, sign, flags   as sdf_execute (K >= 1)
+ *   stream     cudaStream_t (as void*) for the work; it must belong to the
+ *              current device (else SDF_ERR_INVALID_ARG, nothing enqueued)
  *
  * Limits: problems whose scratch exceeds 32 MiB are rejected with
  * SDF_ERR_CAPACITY before any device work (sdf_last_error() gives the size
@@ -484,7 +503,10 @@ void sdf_batch_destroy(sdf_batch batch);
  * The first call on a device looks up the array's device address with that
  * device current; make that first call before any stream capture.  The call
  * is synchronous (it waits for its stream and returns the device status, as
- * sdf_sync).  All calls share the one array, which keeps the last call's
+ * sdf_sync), on success and on every error return after work was enqueued,
+ * so no kernel of a finished call still uses the array.  Host-to-device
+ * copies (twiddle tables) are ordered on `stream`, not the legacy default
+ * stream.  All calls share the one array, which keeps the last call's
  * contents; every counter that must start at zero is cleared by each call.
  * Calls from this process are serialised by a lock; calls that overlap on the
  * GPU from elsewhere (another process using the same library image cannot)

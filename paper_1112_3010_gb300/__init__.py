@@ -65,7 +65,9 @@ class ExecStats(ctypes.Structure):
                 ("g_norm2", ctypes.c_double), ("n_unique", ctypes.c_int64),
                 ("n_fixup_tiles", ctypes.c_int64), ("n_fixup_nodes", ctypes.c_int64),
                 ("n_capped", ctypes.c_int64), ("n_launches", ctypes.c_int64),
-                ("n_fixup_terms", ctypes.c_int64)]
+                ("n_fixup_terms", ctypes.c_int64), ("err_bound_S", ctypes.c_double),
+                ("err_bound_dS", ctypes.c_double), ("err_bound_d2S", ctypes.c_double),
+                ("trusted_frac", ctypes.c_double)]
 
 
 class KernelTime(ctypes.Structure):

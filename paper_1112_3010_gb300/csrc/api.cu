@@ -298,6 +298,9 @@ void plan_programme(sdf_plan_impl *p) {
     if (ds) q = std::max(q, f + gmax);
     if (d2) q = std::max(q, tau * hmax + 2 * gmax + 2 * f);
     p->q_factor = q;
+    p->q_f = f;
+    p->q_g = gmax;
+    p->q_h = hmax;
 }
 
 // Sizes of the two transform buffers (bytesA, bytesB).
@@ -828,6 +831,68 @@ sdf_status sdf_plan_get_info(sdf_plan p, sdf_plan_info *info) {
     return SDF_OK;
 }
 
+// A-priori bounds on the error of the last execute over the nodes not
+// flagged CAPPED, against the exact S (eq. STilde via eq. Bound1), grad S and
+// Hessian of the snapped points, from three sources:
+//  * Transform noise.  Under the error model behind the trust threshold
+//    (include/sdf.h, "Trust region"), the computed phi_p of precision p errs by
+//    at most F = C_p u_p sqrt(log2 n) ||g||_2/sqrt(n) times the channel's l1
+//    norm, and theta_p = F_phi Q/(eps f) (eps = kTrustEps, f the phi channel's
+//    norm).  A node the transform keeps has phi_p >= theta_p, so the relative
+//    error of phi there is at most d = (eps f/Q)/(1 - eps f/Q): S = -tau log phi
+//    errs by tau d; grad S = num/phi by (F_grad + F_phi)/phi, i.e.
+//    eps (f + g)/Q/(1 - ...) since |grad S| <= 1; the Hessian, in units of
+//    1/tau, by eps (tau h + 2 g + 2 f)/Q (g, h: the gradient and Hessian
+//    channels' norms) -- the same combination Q weighs.
+//  * The fix-up's direct sum (SDF_FP32 plans), relative error of the sum:
+//    the tail left out when a node stops (below 1e-5 of its sum by the stop
+//    test; in 3D plus 1e-6 per ring batch for the bins a warp skips), each
+//    term's error (1/r and 2^x by rsqrt.approx / ex2.approx, both within
+//    2^-21 relative; the exponent's absolute error is (r/tau) log2(e) times
+//    that, and the terms that matter have r/tau log2(e) <= L + 64 with
+//    L = log2(e) R_max/tau, R_max the largest distance to the nearest point
+//    of an uncapped node: S_cap + tau log K, or the grid diagonal in full-range
+//    mode), and float summation of at most n_max positive terms (n_max u).
+//    S errs by tau times that relative error, grad S by twice it, and the
+//    Hessian, whose moments carry 1/r <= 1/h, by (2 tau/h + 4) times it (in
+//    units of 1/tau).
+//  * Rounding of the outputs (float: 2^-24 relative to S <= R_max).
+// The noise part rests on the calibrated constants C_p: a bound under the
+// model, as the trust region itself is.
+static void error_bounds(const sdf_plan_impl *p, const DevScalars &d, sdf_exec_stats *st) {
+    const double eps = kTrustEps, tau = p->tau, h = p->h;
+    const double Q = p->q_factor > 0 ? p->q_factor : 1.0;
+    const double f = p->q_f, g = p->q_g, hh = p->q_h;
+    const double den = 1.0 - eps * f / Q;
+    const double dS_rel = eps * f / Q / den;
+    const double dG = eps * (f + g) / Q / den;
+    const double dH_tau = eps * (tau * hh + 2 * g + 2 * f) / Q / den;
+    const double logK = log((double)std::max<int64_t>(1, p->last_K));
+    double diag = 0;
+    for (int a = 0; a < p->D; ++a) diag += (double)p->N[a] * (double)p->N[a];
+    diag = h * sqrt(diag);
+    const double rmax = (p->prec == SDF_FP32 && p->full_range) ? diag : std::min(diag, st->s_cap + tau * logK);
+    const double u = (p->prec == SDF_FP64) ? ldexp(1.0, -53) : ldexp(1.0, -24);
+    const bool ds = p->outputs & SDF_OUT_DS, d2 = p->outputs & SDF_OUT_D2S;
+    // transform part (the FP64 path, and the nodes an FP32 plan keeps)
+    double bS = tau * dS_rel + 2 * u * rmax;
+    double bG = ds ? dG + 2 * u : 0.0;
+    double bH = d2 ? (dH_tau + 4 * u * (tau / h + 2)) / tau : 0.0;
+    if (p->prec == SDF_FP32 && (d.n_fixup_nodes > 0 || p->D == 1)) {
+        const double L = 1.4426950408889634 * rmax / tau;
+        const double e_term = log(2.0) * (L + 64.0 + 1.0) * ldexp(1.0, -21) + ldexp(1.0, -23);
+        const double e_sum = (double)(d.fix_nmax + d.fix_rounds + 1) * ldexp(1.0, -24);
+        const double e_tail = 1e-5 + (p->D == 3 ? 1e-6 * (double)d.fix_rounds : 0.0);
+        const double e = e_term + e_sum + e_tail;
+        bS = std::max(bS, tau * e + 2 * u * rmax);
+        if (ds) bG = std::max(bG, 2 * e + 2 * u);
+        if (d2) bH = std::max(bH, ((2 * tau / h + 4) * e + 4 * u * (tau / h + 2)) / tau);
+    }
+    st->err_bound_S = bS;
+    st->err_bound_dS = bG;
+    st->err_bound_d2S = bH;
+}
+
 sdf_status sdf_get_stats(sdf_plan p, sdf_exec_stats *st) {
     if (!p || !st) return SDF_ERR_INVALID_ARG;
     CK(cudaStreamSynchronize(p->stream));
@@ -848,6 +913,8 @@ sdf_status sdf_get_stats(sdf_plan p, sdf_exec_stats *st) {
     st->n_capped = (int64_t)d.n_capped;
     st->n_launches = p->nlaunch;
     st->n_fixup_terms = (int64_t)d.n_fixup_terms;
+    st->trusted_frac = 1.0 - (double)(int64_t)d.n_capped / (double)p->nnodes;
+    error_bounds(p, d, st);
     return SDF_OK;
 }
 

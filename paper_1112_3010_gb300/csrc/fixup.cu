@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
     };
     if (tid == 0) s_kev[0] = s_kev[1] = INT_MAX;
     int round = 0;
+    unsigned cells_seen = 0;  // staged cells of every batch: no node sums more terms
     for (int k0 = 0; k0 <= kmax; ++round) {
         if (!__syncthreads_or(active[0] || active[1])) break;
         const int k1 = (k0 == 0) ? min(kmax, 2) : min(kmax, max(k0, s_kev[round & 1]));
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
             if (tid == taken - 1) soff[taken] = off + nb;
             __syncthreads();
             const int ncell = (taken > 0) ? soff[taken] : 0;
+            cells_seen += (unsigned)ncell;
             // all threads copy: staged cell j belongs to the last taken bin
             // whose first cell is <= j (empty bins share their successor's)
             for (int j = tid; j < ncell; j += NT) {
@@ -590,7 +592,12 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
         }
         if (nt64) atomicAdd(&P.dsc_w->n_fixup_terms, nt64);
     }
-    if (tid == 0) atomicAdd(&P.dsc_w->n_fixup_tiles, 1ull);
+    if (tid == 0) {
+        atomicAdd(&P.dsc_w->n_fixup_tiles, 1ull);
+        // for the error report: a bound on any node's term count, and batches
+        atomicMax(&P.dsc_w->fix_nmax, (unsigned long long)cells_seen);
+        atomicMax(&P.dsc_w->fix_rounds, (unsigned long long)round);
+    }
 }
 
 cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS, void *d2S, const int8_t *sign,

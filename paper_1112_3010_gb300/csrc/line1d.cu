@@ -222,8 +222,10 @@ __global__ void k_line1d(Line1dParams P) {
             ++terms;
         };
         const float cut = 60.f / itf;  // 60 tau in nodes
+        const unsigned long long terms0 = terms;
         for (int j = lo; j < nocc && (float)(occ[j].x - x - dmin) <= cut; ++j) add(occ[j]);
         for (int j = lo - 1; j >= 0 && (float)(x - occ[j].x - dmin) <= cut; --j) add(occ[j]);
+        atomicMax(&P.dsc->fix_nmax, terms - terms0);  // for the error report
         const float Sx = (float)dmin * hf - tf * logf(s0);
         if (!P.full_range && Sx > (float)scap) {  // phi below theta_64
             atomicAdd(&s_ncap, 1);

@@ -68,12 +68,16 @@ struct Carver {
     }
 };
 
+// The twiddle table goes to the scratch with a copy ordered on the caller's
+// stream (not the legacy default stream, which would serialise with every
+// other stream of the device).  The source is pageable: the copy has been
+// staged by the time cudaMemcpyAsync returns, so h may go out of scope.
 template <typename T>
-cudaError_t fill_twiddles(void *dst, int64_t L) {
+cudaError_t fill_twiddles(void *dst, int64_t L, cudaStream_t st) {
     using V = typename cplx_t<T>::type;
     std::vector<V> h(L);
     fill_twiddle_table(ilog2(L), h.data());
-    return cudaMemcpy(dst, h.data(), sizeof(V) * L, cudaMemcpyHostToDevice);
+    return cudaMemcpyAsync(dst, h.data(), sizeof(V) * L, cudaMemcpyHostToDevice, st);
 }
 
 // Lay out every buffer of plan p in the scratch; returns the bytes needed.
@@ -123,17 +127,22 @@ size_t layout(sdf_plan_impl *p, int64_t K, unsigned char *base, double2 **tw64, 
     return c.off;
 }
 
-sdf_status fail(cudaError_t e) {
+// An error return: first wait for whatever this call already queued on the
+// stream, so that no kernel of a failed call still reads or writes the
+// scratch when the lock is released and the next call rewrites it.
+sdf_status fail(cudaError_t e, cudaStream_t st) {
     set_last_error(cudaGetErrorString(e));
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? SDF_ERR_OOM : SDF_ERR_CUDA;
 }
 
 }  // namespace
 
-#define NCK(x)                              \
-    do {                                    \
-        cudaError_t e_ = (x);               \
-        if (e_ != cudaSuccess) return fail(e_); \
+#define NCK(x)                                           \
+    do {                                                 \
+        cudaError_t e_ = (x);                            \
+        if (e_ != cudaSuccess) return fail(e_, p->stream); \
     } while (0)
 
 extern "C" sdf_status sdf_execute_noalloc(int D, const int64_t *dims, double h, double tau, int precision,
@@ -180,13 +189,30 @@ extern "C" sdf_status sdf_execute_noalloc(int D, const int64_t *dims, double h, 
         set_last_error(msg);
         return SDF_ERR_CAPACITY;
     }
+    // the scratch address belongs to the current device: the stream must be
+    // one of that device's (else the kernels would address another GPU's
+    // copy of the array, or fail to launch)
+    {
+        int dev = 0, sdev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaStreamGetDevice(p->stream, &sdev);
+        if (e != cudaSuccess) {
+            set_last_error(cudaGetErrorString(e));
+            cudaGetLastError();
+            return SDF_ERR_INVALID_ARG;
+        }
+        if (sdev != dev) {
+            set_last_error("sdf_execute_noalloc: the stream belongs to another device than the current one");
+            return SDF_ERR_INVALID_ARG;
+        }
+    }
     unsigned char *base = nullptr;
     NCK(scratch_address(&base));
     layout(p, K, base, tw64, &part, &bufX, &bufY);
     for (int a = 0; a < D; ++a) {
-        if (precision == SDF_FP64) NCK(fill_twiddles<double>(p->tw[a], p->M[a]));
-        else NCK(fill_twiddles<float>(p->tw[a], p->M[a]));
-        NCK(fill_twiddles<double>(tw64[a], p->M[a]));
+        if (precision == SDF_FP64) NCK(fill_twiddles<double>(p->tw[a], p->M[a], p->stream));
+        else NCK(fill_twiddles<float>(p->tw[a], p->M[a], p->stream));
+        NCK(fill_twiddles<double>(tw64[a], p->M[a], p->stream));
     }
     std::vector<double> host_part(kSpectraParts);
     NCK(build_spectra_into(p, bufX, bufY, part, host_part.data(), tw64));
@@ -208,9 +234,9 @@ extern "C" sdf_status sdf_execute_noalloc(int D, const int64_t *dims, double h, 
     NCK(launch_inverse_epilogue(p, ww, S, dS, d2S, sg, fl));
     if (p->prec == SDF_FP32) NCK(launch_fixup(p, ww, S, dS, d2S, ww ? sg : nullptr, fl));
     if (flags) NCK(launch_source_flags(p, flags));
-    NCK(cudaStreamSynchronize(p->stream));
     DevScalars hs;
-    NCK(cudaMemcpy(&hs, p->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    NCK(cudaMemcpyAsync(&hs, p->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
+    NCK(cudaStreamSynchronize(p->stream));
     return (sdf_status)hs.status;
 }
 

@@ -60,6 +60,9 @@ struct DevScalars {
     unsigned long long n_fixup_tiles, n_fixup_nodes, n_capped, n_fixup_terms;
     int64_t n_unique;
     double dl_dtau_acc;         // adjoint partial sum (deterministic order not required)
+    // fix-up facts behind the error report (sdf_get_stats): the most terms any
+    // node summed, and the most ring batches any tile took
+    unsigned long long fix_nmax, fix_rounds;
 };
 
 // Kernel-level event timing (sdf_profile_enable) and the launch counter.
@@ -81,6 +84,7 @@ struct sdf_plan_impl {
     double plan_ms = 0;
     double noise_c32 = 0, noise_c64 = 0;
     double q_factor = 0;     // combination of kernel l1 norms entering theta
+    double q_f = 0, q_g = 0, q_h = 0;  // its parts: l1 noise norms of the phi, gradient, Hessian channels
     double q_factor_adj = 0;
 
     void *tw[3] = {nullptr, nullptr, nullptr};  // per-axis twiddle tables (plan precision)

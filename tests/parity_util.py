@@ -48,6 +48,27 @@ def oracle_ref(shape, sel=None, with_weights=True, want=("S", "dS", "d2S", "mu",
     return ref
 
 
+def sample_nodes(s, n_uniform=1000, n_near=2000, seed=7, reach=40.0):
+    """Seeded node sample of a workload, from its input geometry only:
+    uniform random nodes plus nodes at random distances 0..reach*tau from
+    random points, so the near band, the fix-up band and the capped far field
+    are all represented.  Returns sorted unique flat node indices."""
+    rng = np.random.default_rng(seed)
+    D = s.D
+    uni = rng.integers(0, s.n_nodes, n_uniform)
+    k = rng.integers(0, s.K, n_near)
+    d = rng.uniform(0.0, reach * s.tau, n_near)
+    v = rng.normal(size=(n_near, D))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    P = s.points[k] + d[:, None] * v
+    idx = np.floor(P / s.h + 0.5).astype(np.int64)
+    dims = np.asarray(s.dims)
+    ok = np.all((idx >= 0) & (idx < dims), axis=1)
+    idx = idx[ok]
+    flat_idx = idx[:, 0] + dims[0] * (idx[:, 1] + (dims[1] * idx[:, 2] if D == 3 else 0))
+    return np.unique(np.concatenate([uni, flat_idx]))
+
+
 def flat(a, D, planes=False):
     if planes:
         return a.reshape(a.shape[0], -1)

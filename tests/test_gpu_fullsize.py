@@ -10,26 +10,13 @@ import oracle
 import paper_1112_3010_gb300 as pkg
 from paper_1112_3010_gb300 import workloads as wl
 
-from parity_util import check, oracle_ref, run
+from parity_util import check, oracle_ref, run, sample_nodes
 
 pytestmark = pytest.mark.gpu
 
 
 def _sample(s, n_uniform=1000, n_near=2000, seed=7):
-    rng = np.random.default_rng(seed)
-    D = s.D
-    uni = rng.integers(0, s.n_nodes, n_uniform)
-    k = rng.integers(0, s.K, n_near)
-    d = rng.uniform(0.0, 40.0 * s.tau, n_near)
-    v = rng.normal(size=(n_near, D))
-    v /= np.linalg.norm(v, axis=1, keepdims=True)
-    P = s.points[k] + d[:, None] * v
-    idx = np.floor(P / s.h + 0.5).astype(np.int64)
-    dims = np.asarray(s.dims)
-    ok = np.all((idx >= 0) & (idx < dims), axis=1)
-    idx = idx[ok]
-    flat = idx[:, 0] + dims[0] * (idx[:, 1] + (dims[1] * idx[:, 2] if D == 3 else 0))
-    return np.unique(np.concatenate([uni, flat]))
+    return sample_nodes(s, n_uniform=n_uniform, n_near=n_near, seed=seed)
 
 
 @pytest.mark.parametrize("tau", [0.002, 0.0005])

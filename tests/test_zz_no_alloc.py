@@ -62,15 +62,32 @@ def test_noalloc_matches_plan_execute(case, prec):
         mask |= {"S": 1, "dS": 2, "d2S": 4, "sign": 8}[o]
     p = pkg.SDF_FP64 if prec == "fp64" else pkg.SDF_FP32
     stream = torch.cuda.current_stream().cuda_stream
-    for call in range(2):
-        got = _outputs(s.dims, s.D, dtype, hess)
+    gots = [_outputs(s.dims, s.D, dtype, hess) for _ in range(2)]
+    for call, got in enumerate(gots):
         for t in got.values():
             t.fill_(0x5A if t.dtype in (torch.int8, torch.uint8) else 7.0)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         pkg.sdf_execute_noalloc(s.D, s.dims, s.h, s.tau, p, mask, s.K, pts, w, got["S"], got["dS"],
                                 got.get("d2S"), got["sign"], got["flags"], stream)
         torch.cuda.synchronize()
+        if call > 0:
+            # no device memory was taken by the call (the first call may still
+            # load the library's kernels; the array itself exists from load)
+            assert torch.cuda.mem_get_info()[0] == free0
         _compare(got, ref, s.tau)
     plan.close()
+
+
+def test_noalloc_stream_of_the_current_device_only():
+    """A stream handle is checked against the current device; the default
+    stream passes."""
+    pts = torch.tensor([[0.5, 0.5]], dtype=torch.float64, device="cuda")
+    S = torch.empty((16, 16), dtype=torch.float32, device="cuda")
+    pkg.sdf_execute_noalloc(2, (16, 16), 1.0 / 16, 0.1, pkg.SDF_FP32, 1, 1, pts, None, S, None, None, None,
+                            None, 0)
+    torch.cuda.synchronize()
+    assert torch.isfinite(S).all()
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
