@@ -347,6 +347,9 @@ static void free_plan(sdf_plan_impl *p) {
     cudaFree(p->ucount);
     cudaFree(p->uw);
     cudaFree(p->cheb);
+    cudaFree(p->occ_start);
+    cudaFree(p->occ_x);
+    cudaFree(p->occ_tmp);
     cudaFree(p->tile_flag);
     cudaFree(p->flags_int);
     cudaFree(p->sign_int);
@@ -462,6 +465,9 @@ sdf_status sdf::plan_create_shared(sdf_plan *out, int D, const int64_t *dims, do
         if (precision == SDF_FP32) {
             PCK(alloc((void **)&p->flags_int, p->nnodes, &p->workspace_bytes));
             PCK(alloc((void **)&p->sign_int, p->nnodes, &p->workspace_bytes));
+            PCK(alloc((void **)&p->occ_start, sizeof(int) * (bin_rows(p) + 1), &p->workspace_bytes));
+            PCK(alloc((void **)&p->occ_x, sizeof(int) * nb, &p->workspace_bytes));
+            PCK(alloc((void **)&p->occ_tmp, sizeof(int) * occ_tmp_len(p), &p->workspace_bytes));
         }
     }
     PCK(cudaDeviceSynchronize());
@@ -854,8 +860,10 @@ sdf_status sdf_plan_get_info(sdf_plan p, sdf_plan_info *info) {
 //    of an uncapped node: S_cap + tau log K, or the grid diagonal in full-range
 //    mode), and float summation of at most n_max positive terms (n_max u).
 //    S errs by tau times that relative error, grad S by twice it, and the
-//    Hessian, whose moments carry 1/r <= 1/h, by (2 tau/h + 4) times it (in
-//    units of 1/tau).
+//    Hessian -- a weighted mean of (delta - n n)/r - n n/tau, each term at
+//    most 1/r_min + 1/tau, plus g g/tau -- by (2 tau/r_min + 6) times it in
+//    units of 1/tau, with r_min >= h the smallest distance from a written
+//    node to its nearest point (recorded by the fix-up kernel).
 //  * Rounding of the outputs (float: 2^-24 relative to S <= R_max).
 // The noise part rests on the calibrated constants C_p: a bound under the
 // model, as the trust region itself is.
@@ -886,7 +894,10 @@ static void error_bounds(const sdf_plan_impl *p, const DevScalars &d, sdf_exec_s
         const double e = e_term + e_sum + e_tail;
         bS = std::max(bS, tau * e + 2 * u * rmax);
         if (ds) bG = std::max(bG, 2 * e + 2 * u);
-        if (d2) bH = std::max(bH, ((2 * tau / h + 4) * e + 4 * u * (tau / h + 2)) / tau);
+        float rinv_f;  // the largest h/r_min over written nodes (at most 1)
+        memcpy(&rinv_f, &d.fix_rinv_bits, sizeof rinv_f);
+        const double rinv = std::min(1.0, (double)rinv_f);
+        if (d2) bH = std::max(bH, ((2 * tau * rinv / h + 6) * e + 4 * u * (tau / h + 2)) / tau);
     }
     st->err_bound_S = bS;
     st->err_bound_dS = bG;

@@ -13,19 +13,22 @@
 // nodes are the two lanes of packed FP32x2 arithmetic (fma/mul/add.f32x2),
 // which halves the FMA-pipe instructions of the summing loop.  Candidate
 // bins are visited in rings of Chebyshev distance k = 0, 1, 2, ... around the
-// tile; every occupied node of ring k' lies at least (8(k'-1)+1)h from every
+// tile (a batch of rings is listed row by row from per-row lists of the
+// occupied bins, so empty bins cost nothing); every occupied node of ring k'
+// lies at least (8(k'-1)+1)h from every
 // node of the tile, so after ring k the unvisited points add at most
 // T = sum_{k'>k} n_k' exp(-(8(k'-1)+1)h/tau), with the ring counts n_k' read
 // from the bins' prefix sums for a few rings ahead (the rest all at the next
 // distance).  A node stops summing once T is below 1e-5 of its sum, or once
-// even its sum plus T is below theta_64 (it stays capped).  Rings go in batches
-// that end at the first ring where some node could meet one of these tests
-// (a bound from its sums so far), so there are few batches per tile and no
-// node sums past its own stopping ring.  In 3D a warp also skips a staged
-// bin when, for each of its active nodes, the bin's whole box lies so far out
-// that all the batch's points there would add under 1e-6 of the node's sum so
-// far (the cube of rings holds many points outside that sphere).  The
-// log-sum-exp shift
+// even its sum plus T is below theta_64 (it stays capped).  Rings go in
+// batches that end at the first ring where every node of some warp could meet
+// one of these tests (a bound from its sums so far): the summing loop is
+// warp-uniform, so a finished warp is what saves work, and batches stay few.
+// In 3D a warp also skips a staged bin when, for each of its active nodes,
+// the bin's whole box lies so far out that all the batch's points there add
+// under 1e-6 of the node's sum so far (the cube of rings holds many points
+// outside that sphere); over a node's batches that leaves out at most 1e-6
+// per batch of its final sum.  The log-sum-exp shift
 // m is the nearest point found by a cheap pass over the first batch of points
 // (and over a later batch only if it could hold a point so much nearer that a
 // term would exceed 2^60), so the summing loop itself has no branch.  A
@@ -45,6 +48,7 @@ namespace sdf {
 
 struct FixParams {
     const int *bin_start, *bin_nuniq, *ucell, *ucount;
+    const int *occ_start, *occ_x;  // occupied bins per bin row, x ascending
     const int *sat;  // summed-area table of the points per bin
     const unsigned char *cheb, *tile_flag;
     const DevScalars *dsc;
@@ -62,55 +66,19 @@ struct FixParams {
 };
 
 constexpr int kFixCap = 1024;  // cells staged in shared memory at once
+// bin rows listed per pass (a batch's rows are those of the box of its last ring)
+template <int D> constexpr int kRowCap = (D == 2) ? 256 : 1024;
+
+// First index in occ_x[a, b) (ascending) that is >= v.
+__device__ __forceinline__ int occ_lower(const int *__restrict__ occ_x, int a, int b, int v) {
+    while (a < b) {
+        const int m = (a + b) >> 1;
+        if (occ_x[m] < v) a = m + 1;
+        else b = m;
+    }
+    return a;
+}
 constexpr int kTB2 = 2;       // 2D tile: kTB2 x kTB2 bins (16 x 16 nodes)
-
-// Bin offset of ring element i (ring k > 0) in 2D: walk the square's border.
-__device__ __forceinline__ void ring2(int k, int i, int &dx, int &dy) {
-    const int side = 2 * k;
-    const int s = i / side, o = i % side;
-    switch (s) {
-        case 0: dx = -k + o; dy = -k; break;
-        case 1: dx = k; dy = -k + o; break;
-        case 2: dx = k - o; dy = k; break;
-        default: dx = -k; dy = k - o; break;
-    }
-}
-
-// 3D ring element i: enumerate the (2k+1)^3 cube and skip the interior by
-// index arithmetic: layers z = -k and z = k are full squares, the others are
-// square borders.
-__device__ __forceinline__ void ring3(int k, int i, int &dx, int &dy, int &dz) {
-    const int w = 2 * k + 1, full = w * w, border = 8 * k;
-    if (i < full) {
-        dz = -k;
-        dx = i % w - k;
-        dy = i / w - k;
-        return;
-    }
-    i -= full;
-    const int nmid = 2 * k - 1;
-    if (i < nmid * border) {
-        dz = -k + 1 + i / border;
-        ring2(k, i % border, dx, dy);
-        return;
-    }
-    i -= nmid * border;
-    dz = k;
-    dx = i % w - k;
-    dy = i / w - k;
-}
-
-// Border of a square of side s (s >= 2): element i of 4(s-1), as offsets
-// from its corner.
-__device__ __forceinline__ void square_border(int s, int i, int &dx, int &dy) {
-    const int side = i / (s - 1), o = i % (s - 1);
-    switch (side) {
-        case 0: dx = o; dy = 0; break;
-        case 1: dx = s - 1; dy = o; break;
-        case 2: dx = s - 1 - o; dy = s - 1; break;
-        default: dx = 0; dy = s - 1 - o; break;
-    }
-}
 
 // Hardware approximations (PTX ex2.approx / rsqrt.approx, relative error
 // about 2^-22): arguments here are never denormal (exponents lie in
@@ -142,7 +110,7 @@ template <int D> __device__ __forceinline__ constexpr int sym_index(int a, int b
 // LVL: 0 = S only, 1 = S and grad S, 2 = S, grad S and the Hessian (only the
 // sums the requested outputs need are accumulated).
 template <int D, typename TO, int LVL>
-__global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : (LVL == 2 ? 2 : 4)) k_fixup(FixParams P) {
+__global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : (LVL == 2 ? 2 : 3)) k_fixup(FixParams P) {
     constexpr int TB = (D == 2) ? kTB2 : 1;  // tile edge in bins
     constexpr int NT = (D == 2) ? 32 * kTB2 * kTB2 : 256;
     constexpr int NH = D * (D + 1) / 2;
@@ -154,6 +122,8 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
     __shared__ int sbin[NT];          // the bin's index
     __shared__ float4 sbox[NT];       // the bin's first node (x, y, z) and whether it holds points
     __shared__ int wtot[32];
+    __shared__ int4 s_row[kRowCap<D>];  // per listed row: (first, count) of up to two runs in occ_x
+    __shared__ int s_rpre[kRowCap<D>];  // per listed row: its first bin in the pass's list
     const int tid = threadIdx.x;
     const int nt0 = (P.nb0 + TB - 1) / TB, nt1 = (P.nb1 + TB - 1) / TB;
     const int64_t tile = blockIdx.x;
@@ -218,16 +188,10 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
     for (int a = 0; a < NH; ++a) sB[a] = dup2(0.f);
     unsigned nterm = 0;
 
-    // ring k: bins at Chebyshev distance k from the tile's block of bins
-    auto nring_of = [&](int k) {
-        return (D == 2) ? 4 * (TB + 2 * k - 1)
-                        : ((k == 0) ? 1 : (2 * k + 1) * (2 * k + 1) * (2 * k + 1) - (2 * k - 1) * (2 * k - 1) * (2 * k - 1));
-    };
     const int kmax = max(max(P.nb0, P.nb1), (D == 3) ? P.nb2 : 0);
     // Rings are visited in batches: {0,1,2}, then up to the first ring at
-    // whose end some active node could stop or be capped (a lower bound
-    // worked out from its sums after the previous batch, s_kev), so no node
-    // sums past its own stopping point and the batches stay few.
+    // whose end every active node of some warp could stop or be capped (a
+    // lower bound worked out from its sums after the previous batch, s_kev).
     __shared__ int s_kev[2];
     // points in the box of rings <= k1 + j (j <= kLook) and the log of the
     // bound on what lies beyond ring k1 + i (i < kLook): ring k' holds
@@ -250,7 +214,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
     };
     if (tid == 0) s_kev[0] = s_kev[1] = INT_MAX;
     int round = 0;
-    unsigned cells_seen = 0;  // staged cells of every batch: no node sums more terms
+    unsigned nsum = 0;  // cells this thread's loop ran over: no node of it summed more terms
     for (int k0 = 0; k0 <= kmax; ++round) {
         if (!__syncthreads_or(active[0] || active[1])) break;
         const int k1 = (k0 == 0) ? min(kmax, 2) : min(kmax, max(k0, s_kev[round & 1]));
@@ -258,35 +222,93 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
         if (tid <= kLook) s_cnt[tid] = box_count(min(k1 + tid, kmax));
         // every node of ring k0 or beyond lies at least 8(k0-1)+1 from the tile
         const float lb_in = (k0 == 0) ? 0.f : 8.f * (k0 - 1) + 1.f;
-        int nring = 0;
-        for (int k = k0; k <= k1; ++k) nring += nring_of(k);
-        for (int i0 = 0; i0 < nring;) {
-            // one candidate bin per thread
+        // The batch's bins are those of rings k0..k1: the occupied bins of the
+        // rows (y[, z]) of ring k1's box, whole x runs for rows at ring
+        // distance >= k0 in (y, z), else the two x runs at distance k0..k1.
+        // Rows go in passes of at most kRowCap; each thread lists a run of
+        // consecutive rows, so the bins come in row order (deterministic).
+        const int ylo = max(by - k1, 0), yhi = min(by + TB - 1 + k1, P.nb1 - 1);
+        const int zlo = (D == 3) ? max(bz - k1, 0) : 0, zhi = (D == 3) ? min(bz + k1, P.nb2 - 1) : 0;
+        const int ny = yhi - ylo + 1, nrow_all = ny * (zhi - zlo + 1);
+        for (int r0 = 0; r0 < nrow_all; r0 += kRowCap<D>) {
+        const int npass = min(kRowCap<D>, nrow_all - r0);
+        const int rpt = (npass + NT - 1) / NT;
+        int cnt_t = 0;
+        for (int q = 0; q < rpt; ++q) {
+            const int lr = tid * rpt + q;
+            if (lr >= npass) break;
+            const int r = r0 + lr;
+            const int qy = ylo + r % ny, qz = zlo + r / ny;
+            const int row = qy + P.nb1 * qz;
+            int dyz = max(max(by - qy, qy - (by + TB - 1)), 0);
+            if (D == 3) dyz = max(dyz, max(bz - qz, qz - bz));
+            const int a = P.occ_start[row], b = P.occ_start[row + 1];
+            int4 rg = make_int4(a, 0, a, 0);
+            if (a < b) {
+                if (dyz >= k0) {
+                    const int lo = occ_lower(P.occ_x, a, b, bx - k1);
+                    rg.x = lo;
+                    rg.y = occ_lower(P.occ_x, lo, b, bx + TB + k1) - lo;
+                } else {
+                    const int lo = occ_lower(P.occ_x, a, b, bx - k1);
+                    rg.x = lo;
+                    rg.y = occ_lower(P.occ_x, lo, b, bx - k0 + 1) - lo;
+                    const int lo2 = occ_lower(P.occ_x, lo + rg.y, b, bx + TB - 1 + k0);
+                    rg.z = lo2;
+                    rg.w = occ_lower(P.occ_x, lo2, b, bx + TB + k1) - lo2;
+                }
+            }
+            s_row[lr] = rg;
+            s_rpre[lr] = cnt_t;
+            cnt_t += rg.y + rg.w;
+        }
+        int nlist = 0;
+        {
+            // block exclusive scan of the threads' bin counts
+            const int lane = tid & 31, wid = tid >> 5;
+            int incl = cnt_t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            __syncthreads();  // wtot is free (its last readers are past a barrier)
+            if (lane == 31) wtot[wid] = incl;
+            __syncthreads();
+            int woff = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                const int t = wtot[w];
+                if (w < wid) woff += t;
+                nlist += t;
+            }
+            const int off = woff + incl - cnt_t;
+            for (int q = 0; q < rpt; ++q) {
+                const int lr = tid * rpt + q;
+                if (lr >= npass) break;
+                s_rpre[lr] += off;
+            }
+            __syncthreads();
+        }
+        for (int i0 = 0; i0 < nlist;) {
+            // one listed bin per thread: the last row whose first bin is <= i
             const int i = i0 + tid;
             int nb = 0, gb = -1, s0 = 0, cx = 0, cy = 0, cz = 0;
-            if (i < nring) {
-                int k = k0, ii = i;
-                while (ii >= nring_of(k)) {
-                    ii -= nring_of(k);
-                    ++k;
+            if (i < nlist) {
+                int lo = 0, hi = npass - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_rpre[mid] <= i) lo = mid;
+                    else hi = mid - 1;
                 }
-                int dx = 0, dy = 0, dz = 0;
-                if (D == 2) {
-                    square_border(TB + 2 * k, ii, dx, dy);
-                    dx -= k;
-                    dy -= k;
-                } else if (k > 0) {
-                    ring3(k, ii, dx, dy, dz);
-                }
-                const int qx = bx + dx, qy = by + dy, qz = bz + dz;
-                cx = qx;
-                cy = qy;
-                cz = qz;
-                if (qx >= 0 && qx < P.nb0 && qy >= 0 && qy < P.nb1 && (D == 2 || (qz >= 0 && qz < P.nb2))) {
-                    gb = qx + P.nb0 * (qy + P.nb1 * qz);
-                    nb = P.bin_nuniq[gb];
-                    s0 = P.bin_start[gb];
-                }
+                const int4 rg = s_row[lo];
+                const int kk = i - s_rpre[lo];
+                const int idx = (kk < rg.y) ? rg.x + kk : rg.z + (kk - rg.y);
+                const int r = r0 + lo;
+                cx = P.occ_x[idx];
+                cy = ylo + r % ny;
+                cz = zlo + r / ny;
+                gb = cx + P.nb0 * (cy + P.nb1 * cz);
+                nb = P.bin_nuniq[gb];
+                s0 = P.bin_start[gb];
             }
             // block exclusive scan of nb
             const int lane = tid & 31, wid = tid >> 5;
@@ -308,7 +330,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
             }
             __syncthreads();
             const int off = wtot[wid] + incl - nb;
-            const bool take = (i < nring) && (off + nb <= kFixCap);
+            const bool take = (i < nlist) && (off + nb <= kFixCap);
             const int taken = __syncthreads_count(take);  // taken bins form a prefix
             if (take) {
                 soff[tid] = off;
@@ -319,7 +341,6 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
             if (tid == taken - 1) soff[taken] = off + nb;
             __syncthreads();
             const int ncell = (taken > 0) ? soff[taken] : 0;
-            cells_seen += (unsigned)ncell;
             // all threads copy: staged cell j belongs to the last taken bin
             // whose first cell is <= j (empty bins share their successor's)
             for (int j = tid; j < ncell; j += NT) {
@@ -336,11 +357,13 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
                                       (float)(qz * 8 + (lc >> 6)), (float)P.ucount[src]);
             }
             __syncthreads();
-            // 3D: every lane of a warp with an active node runs the loops
-            // below (the bin votes need the whole warp); lanes with none add
-            // terms that are never written
+            // every lane of a warp with an active node runs the loops below
+            // (warp-uniform control flow; in 3D the bin votes need the whole
+            // warp).  A lane whose nodes stopped keeps adding terms beyond its
+            // stopping ring: they are positive and only make its sums more
+            // complete (the term count below leaves them out)
             const bool me = active[0] || active[1];
-            const bool run = (D == 3) ? __any_sync(0xffffffffu, me) : me;
+            const bool run = __any_sync(0xffffffffu, me);
             if (run && ncell > 0) {
                 // the shift m need not be the exact minimum, only keep every
                 // term in range: no shift yet, or a batch point that could
@@ -404,10 +427,11 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
                 // 3D: a bin whose points all lie at least rho_j from node j adds
                 // at most n e^{-(rho_j - m_j)/tau} to its sum (relative to
                 // e^{-m_j/tau}), n <= the points in the box of rings <= k1.
-                // rho_j makes that at most 1e-6 of the sum so far (2^-19.93),
-                // so the batch's skipped terms stay below 1e-6 of the final
-                // sum; the warp skips the bin when none of its active nodes
-                // needs it.  No sum yet: nothing is skipped.  (The points of
+                // rho_j makes all the batch's skipped points together add at
+                // most 1e-6 of the sum so far (2^-19.93), so over a node's
+                // batches the skipped terms stay below (batches) x 1e-6 of
+                // its final sum; the warp skips the bin when none of its
+                // active nodes needs it.  No sum yet: nothing is skipped.  (The points of
                 // a 2D tile's bins are few, and the per-bin loop measured
                 // slower there: 2D sums every staged point in one loop.)
                 float rho2[NPT] = {INFINITY, INFINITY};
@@ -443,7 +467,8 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
                         if (__all_sync(0xffffffffu, skip)) continue;
                     }
                     nterm += (unsigned)(e1 - e0) * nmine;
-#pragma unroll 2
+                    nsum += (unsigned)(e1 - e0);
+#pragma unroll 4
                 for (int e = e0; e < e1; ++e) {
                     const float4 q = cell[e];
                     const float d0 = xf - q.x, d1 = yf - q.y;
@@ -484,6 +509,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
             __syncthreads();
             i0 += max(taken, 1);
         }
+        }  // row passes
         if (tid < kLook) {
             // log T_i, T_i = sum_{k'=k1+i+1}^{k1+kLook} n_k' e^{-lb(k'-1)/tau}
             //                + (points beyond ring k1+kLook) e^{-lb(k1+kLook)/tau},
@@ -500,7 +526,11 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
         __syncthreads();
         // phi = e^{-m/tau} sE + (rest), rest <= T_0; in logs A = log(e^{-m/tau} sE)
         const float tail0 = s_logT[0];
-        int kev = INT_MAX;
+        // The next batch ends where some whole warp could be done: the
+        // summing loop is warp-uniform, so a node that stops early saves
+        // nothing while its warp runs on; per warp the latest ring at which
+        // its nodes could stop (or be capped), then the earliest over warps.
+        int kev = -1;
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             if (!active[j]) continue;
@@ -528,12 +558,14 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
                     break;
                 }
             }
-            kev = min(kev, min(k1 + ev, kmax));
+            kev = max(kev, min(k1 + ev, kmax));
         }
-        if (kev < INT_MAX) atomicMin(&s_kev[(round + 1) & 1], kev);
+        kev = __reduce_max_sync(0xffffffffu, kev);
+        if ((tid & 31) == 0 && kev >= 0) atomicMin(&s_kev[(round + 1) & 1], kev);
         k0 = k1 + 1;
     }
     int fixed = 0;
+    float rinv = 0.f;  // largest 1/max(m, 1) over the nodes written here
     TO *So = reinterpret_cast<TO *>(P.S);
     TO *dS = reinterpret_cast<TO *>(P.dS);
     TO *d2S = reinterpret_cast<TO *>(P.d2S);
@@ -549,6 +581,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
             continue;
         }
         ++fixed;
+        rinv = fmaxf(rinv, 1.f / fmaxf(mg[j], 1.f));
         if (So) So[nd] = (TO)(sg * S);
         if constexpr (LVL == 0) {
             P.flags[nd] = SDF_FLAG_FIXUP;
@@ -584,7 +617,12 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
         fx += __shfl_down_sync(0xffffffffu, fx, o);
         nt64 += __shfl_down_sync(0xffffffffu, nt64, o);
     }
+    // for the error report: the most terms a written node summed, its 1/r bound
+    const unsigned nmx = __reduce_max_sync(0xffffffffu, fixed ? nsum : 0u);
+    const unsigned rmx = __reduce_max_sync(0xffffffffu, __float_as_uint(rinv));
     if ((tid & 31) == 0) {
+        if (nmx) atomicMax(&P.dsc_w->fix_nmax, (unsigned long long)nmx);
+        if (rmx) atomicMax(&P.dsc_w->fix_rinv_bits, rmx);
         if (fx) {
             atomicAdd(&P.dsc_w->n_fixup_nodes, (unsigned long long)fx);
             // the epilogue counted these as capped; they are not any more
@@ -594,9 +632,7 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
     }
     if (tid == 0) {
         atomicAdd(&P.dsc_w->n_fixup_tiles, 1ull);
-        // for the error report: a bound on any node's term count, and batches
-        atomicMax(&P.dsc_w->fix_nmax, (unsigned long long)cells_seen);
-        atomicMax(&P.dsc_w->fix_rounds, (unsigned long long)round);
+        atomicMax(&P.dsc_w->fix_rounds, (unsigned long long)round);  // for the error report
     }
 }
 
@@ -604,6 +640,8 @@ cudaError_t launch_fixup(sdf_plan_impl *p, bool /*with_sign*/, void *S, void *dS
                          uint8_t *flags) {
     FixParams F;
     F.bin_start = p->bin_start;
+    F.occ_start = p->occ_start;
+    F.occ_x = p->occ_x;
     F.sat = p->bin_count;  // launch_cheb wrote the table there
     F.bin_nuniq = p->bin_nuniq;
     F.ucell = p->ucell;

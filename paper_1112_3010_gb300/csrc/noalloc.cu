@@ -105,6 +105,9 @@ size_t layout(sdf_plan_impl *p, int64_t K, unsigned char *base, double2 **tw64, 
     if (p->prec == SDF_FP32) {
         c.take(&p->flags_int, p->nnodes);
         c.take(&p->sign_int, p->nnodes);
+        c.take(&p->occ_start, sizeof(int) * (bin_rows(p) + 1));
+        c.take(&p->occ_x, sizeof(int) * nb);
+        c.take(&p->occ_tmp, sizeof(int) * occ_tmp_len(p));
     }
     c.take(&p->pt_key, sizeof(int) * K);
     c.take(&p->pt_lc, sizeof(int) * K);

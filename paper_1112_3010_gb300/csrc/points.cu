@@ -478,6 +478,26 @@ __global__ void __launch_bounds__(1024) k_sat_axis(const int *__restrict__ bin_s
     }
 }
 
+// The occupied bins of each bin row (row = by + nb1 bz), x ascending: one
+// warp per row counts them (ballots over 32 bins at a time), the counts are
+// scanned, and the same warps write the x indices.
+template <bool FILL>
+__global__ void k_occ_rows(const int *__restrict__ nuniq, int nb0, int64_t nrows, int *cnt_or_start, int *occ_x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= nrows) return;
+    const int *nu = nuniq + row * nb0;
+    int at = FILL ? cnt_or_start[row] : 0;
+    for (int x0 = 0; x0 < nb0; x0 += 32) {
+        const int x = x0 + lane;
+        const bool occ = x < nb0 && nu[x] > 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, occ);
+        if (FILL && occ) occ_x[at + __popc(bal & ((1u << lane) - 1u))] = x;
+        at += __popc(bal);
+    }
+    if (!FILL && lane == 0) cnt_or_start[row] = at;
+}
+
 cudaError_t launch_cheb(sdf_plan_impl *p, cudaStream_t on) {
     cudaStream_t st = on ? on : p->stream;
     const int64_t nb0 = p->nb[0], nb1 = p->nb[1], nb2 = p->nb[2];
@@ -499,6 +519,19 @@ cudaError_t launch_cheb(sdf_plan_impl *p, cudaStream_t on) {
     k_sat_axis<0><<<(unsigned)(nb0 * nz), threads(nb1), 0, st>>>(p->bin_start, p->bin_count, (int)nb0, (int)nb1, nz);
     if (p->D == 3)
         k_sat_axis<1><<<(unsigned)(nb0 * nb1), threads(nz), 0, st>>>(p->bin_start, p->bin_count, (int)nb0, (int)nb1, nz);
+    if (p->occ_start) {
+        // occupied-bin lists per bin row (the fix-up enumerates its rings from them)
+        const int64_t nrows = bin_rows(p);
+        const unsigned gw = (unsigned)((nrows * 32 + 255) / 256);
+        int *cnt = p->occ_tmp, *tsum = p->occ_tmp + nrows;
+        k_occ_rows<false><<<gw, 256, 0, st>>>(p->bin_nuniq, (int)nb0, nrows, cnt, nullptr);
+        const int64_t ntiles = (nrows + kScanTile - 1) / kScanTile;
+        k_scan_tiles<<<(unsigned)ntiles, 1024, 0, st>>>(cnt, p->occ_start, tsum, nrows);
+        k_scan_sums<<<1, 1024, 0, st>>>(tsum, (int)ntiles, p->occ_start, nrows);
+        if (ntiles > 1)
+            k_scan_add<<<(unsigned)((nrows + 255) / 256), 256, 0, st>>>(p->occ_start, tsum, nrows);
+        k_occ_rows<true><<<gw, 256, 0, st>>>(p->bin_nuniq, (int)nb0, nrows, p->occ_start, p->occ_x);
+    }
     prof_end(p, st);
     return cudaGetLastError();
 }

@@ -61,8 +61,11 @@ struct DevScalars {
     int64_t n_unique;
     double dl_dtau_acc;         // adjoint partial sum (deterministic order not required)
     // fix-up facts behind the error report (sdf_get_stats): the most terms any
-    // node summed, and the most ring batches any tile took
+    // written node summed, the most ring batches any tile took, and the bits
+    // of the largest 1/max(m, 1) over written nodes (m: distance to the
+    // nearest point in nodes; positive floats order as their bits)
     unsigned long long fix_nmax, fix_rounds;
+    unsigned fix_rinv_bits, pad1;
 };
 
 // Kernel-level event timing (sdf_profile_enable) and the launch counter.
@@ -108,6 +111,10 @@ struct sdf_plan_impl {
     int *ucell = nullptr, *ucount = nullptr;
     double *uw = nullptr;
     unsigned char *cheb = nullptr;   // Chebyshev bin distance to an occupied bin (capped)
+    // FP32 plans: the occupied bins of each bin row (row = by + nb1 bz), x
+    // ascending: occ_x[occ_start[row] .. occ_start[row + 1]); occ_tmp holds
+    // the per-row counts and scan partials while the lists are built
+    int *occ_start = nullptr, *occ_x = nullptr, *occ_tmp = nullptr;
     unsigned char *tile_flag = nullptr;
     uint8_t *flags_int = nullptr;    // FP32 plans: flags when the caller passes none
     int8_t *sign_int = nullptr;      // FP32 plans: sign when the caller passes none
@@ -167,6 +174,10 @@ double green_origin_integral(int D);  // A_D of the exact Green's function set (
 // Compressed spectrum of one kernel: one row per folded line-axis frequency
 // (2D: f0; 3D: (f1, f0)), each row the folded last-axis frequencies padded to
 // a multiple of 4 values (16-byte aligned rows).
+// Rows of bins (x fixed to the row) and the scratch the occupied-bin lists need.
+inline int64_t bin_rows(const sdf_plan_impl *p) { return p->nb[1] * p->nb[2]; }
+inline int64_t occ_tmp_len(const sdf_plan_impl *p) { return bin_rows(p) + (bin_rows(p) + 4095) / 4096 + 1; }
+
 inline int64_t spec_row_len(const sdf_plan_impl *p) { return ((p->M[p->D - 1] / 2 + 1) + 3) & ~int64_t(3); }
 inline int64_t spec_rows(const sdf_plan_impl *p) {
     return p->D == 1 ? 1 : (p->D == 2 ? p->M[0] / 2 + 1 : (p->M[0] / 2 + 1) * (p->M[1] / 2 + 1));
