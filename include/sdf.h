@@ -20,8 +20,9 @@
  * Grids.  dims[a] = N_a nodes on axis a (x first); node i sits at i*h (origin
  * 0).  Every grid array is C-order with x fastest: element (x, y[, z]) at
  * x + N_0*(y + N_1*z).  The padded FFT size per axis is the smallest power of
- * two M_a >= max(2*N_a - 1, 16), so the circular convolution equals the linear
- * one on the N^D output nodes.
+ * two M_a >= max(2*N_a - 1, 16) (sdf_plan_set_padding may choose 3 * 2^k
+ * instead), so the circular convolution equals the linear one on the N^D
+ * output nodes.
  *
  * Precision.  SDF_FP64: every FFT pass, product and epilogue in double; grid
  * outputs are double.  SDF_FP32 (the mixed path): FFT passes and products in
@@ -153,7 +154,8 @@ typedef struct {
  *              batches or autotuning.
  *   dims       host array of D node counts, x first, each in [2, 2048] (1D),
  *              [2, 4096] (2D) or [2, 512] (3D); M_a (above) must fit the
- *              device (else SDF_ERR_UNSUPPORTED).
+ *              device (else SDF_ERR_UNSUPPORTED).  sdf_plan_set_padding and
+ *              sdf_plan_autotune may change M_a to 3 * 2^k.
  *   h          grid spacing (> 0).  tau: the paper's tau (> 0).
  *   precision  SDF_FP64 or SDF_FP32.
  *   outputs    mask of SDF_OUT_* bits.  SDF_OUT_S is implied.
@@ -350,15 +352,45 @@ sdf_status sdf_plan_set_noise_constants(sdf_plan plan, double c_fp32, double c_f
 sdf_status sdf_plan_set_tuning(sdf_plan plan, int lines_T, int lines_F, int fused_variant);
 
 /*
- * sdf_plan_autotune -- time candidate tile schedules on the plan's stream with
- * the given inputs (as sdf_execute; outputs are not written), keep the
- * fastest, and report it in *lines_T, *lines_F, *fused_variant (host, may be
- * NULL).  Each candidate runs `reps` executes after one warm-up; the passes
- * each knob affects are timed with CUDA events.  Synchronous.
+ * sdf_plan_autotune -- choose the padded sizes and the tile schedule by
+ * timing them on the plan's stream with the given inputs (as sdf_execute;
+ * outputs are not written), keep the fastest, and report the schedule in
+ * *lines_T, *lines_F, *fused_variant (host, may be NULL; the sizes are in
+ * sdf_plan_get_info's `padded`).
+ *   1. Padded sizes: per axis the power of two of sdf_plan_create and, where
+ *      it is smaller, the least 3 * 2^k >= 2 N_a - 1 (sdf_plan_set_padding);
+ *      every combination is timed over the whole execute.  A plan of a batch
+ *      that borrows another plan's spectra keeps its sizes.
+ *   2. The tile schedule (sdf_plan_set_tuning) on those sizes: the passes
+ *      each knob affects are timed.
+ * Each candidate runs `reps` executes after one warm-up, timed with CUDA
+ * events.  The choice is kept in a cache keyed by the GPU's name and
+ * architecture, D, dims, precision, outputs and kernel set: a later call on
+ * a problem of the same key applies the cached choice without timing.  The
+ * cache is the text file $SDF_AUTOTUNE_CACHE (an empty value disables it),
+ * else $XDG_CACHE_HOME/sdf_gb300/autotune.tsv, else
+ * $HOME/.cache/sdf_gb300/autotune.tsv; it is optional (unreadable or
+ * unwritable: no cache).  Synchronous; may rebuild the plan's spectra.
+ * The paper chooses no transform sizes or schedules; this is the library's.
  */
 sdf_status sdf_plan_autotune(sdf_plan plan, int64_t K, const double *points,
                              const double *weights, int reps, int *lines_T,
                              int *lines_F, int *fused_variant);
+
+/*
+ * sdf_plan_set_padding -- set the padded transform size of each axis:
+ * padded[a] (host, D values) must be a power of two or 3 * 2^k (>= 48), at
+ * least max(2 N_a - 1, 16) so that the circular convolution still equals
+ * the linear one on the N^D nodes, and at most 8192 (2D) or 1024 (3D); else
+ * SDF_ERR_INVALID_ARG.  Lines of 3 * 2^k points are transformed with a
+ * radix-3 stage ahead of the radix-16 ones.  Rebuilds the plan's twiddles,
+ * kernel spectra and transform buffers (synchronous, allocates); on a CUDA
+ * error the plan must be destroyed.  SDF_ERR_UNSUPPORTED for 1D plans and
+ * for a plan of a batch that borrows another plan's spectra.  Results agree
+ * with the power-of-two padding to the rounding of the transforms (the trust
+ * threshold follows n = prod M_a).
+ */
+sdf_status sdf_plan_set_padding(sdf_plan plan, const int64_t *padded);
 
 /*
  * sdf_plan_set_full_range -- SDF_FP32 plans: when enable != 0, the fix-up
@@ -468,6 +500,18 @@ sdf_status sdf_batch_execute(sdf_batch batch, const int64_t *K,
                              const double *const *weights, void *const *S,
                              void *const *dS, void *const *d2S,
                              int8_t *const *sign, uint8_t *const *flags);
+
+/*
+ * sdf_batch_autotune -- sdf_plan_autotune for a batch: each problem that owns
+ * a set of kernel spectra (the first of its geometry) is tuned on its own
+ * inputs (K, points, weights: host arrays of n entries, as
+ * sdf_batch_execute), and the problems sharing its spectra take its padded
+ * sizes, spectra and tile schedule.  The next sdf_batch_execute captures a
+ * new graph.  Synchronous.
+ */
+sdf_status sdf_batch_autotune(sdf_batch batch, const int64_t *K,
+                              const double *const *points,
+                              const double *const *weights, int reps);
 
 /* Wait for the batch; return the first device-side error of any problem. */
 sdf_status sdf_batch_sync(sdf_batch batch);

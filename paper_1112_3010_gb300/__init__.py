@@ -35,7 +35,7 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_batch_execute", "sdf_batch_sync", "sdf_batch_plan", "sdf_batch_destroy",
             "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature", "sdf_plan_set_full_range",
             "sdf_mesh_sources", "sdf_plan_set_kernel", "sdf_green_profile", "sdf_execute_multi",
-            "sdf_execute_multi_host"]
+            "sdf_execute_multi_host", "sdf_plan_set_padding", "sdf_batch_autotune"]
 
 
 class SDFError(RuntimeError):
@@ -131,6 +131,10 @@ def load_library(path: str | None = None):
         ip = ctypes.POINTER(ctypes.c_int)
         L.sdf_plan_autotune.argtypes = [vp, i64, vp, vp, ctypes.c_int, ip, ip, ip]
         L.sdf_plan_autotune.restype = ctypes.c_int
+        L.sdf_plan_set_padding.argtypes = [vp, ctypes.POINTER(i64)]
+        L.sdf_plan_set_padding.restype = ctypes.c_int
+        L.sdf_batch_autotune.argtypes = [vp, ctypes.POINTER(i64), pp, pp, ctypes.c_int]
+        L.sdf_batch_autotune.restype = ctypes.c_int
         L.sdf_plan_set_noise_constants.argtypes = [vp, d, d]
         L.sdf_plan_set_noise_constants.restype = ctypes.c_int
         L.sdf_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -319,6 +323,19 @@ def sdf_batch_execute(handle, K, points, weights, S, dS, d2S, sign, flags):
         "sdf_batch_execute")
 
 
+def sdf_plan_set_padding(handle, padded):
+    """Padded transform size per axis (2^k or 3*2^k, >= 2N-1)."""
+    arr = (ctypes.c_int64 * len(padded))(*[int(x) for x in padded])
+    _ck(_lib().sdf_plan_set_padding(handle, arr), "sdf_plan_set_padding")
+
+
+def sdf_batch_autotune(handle, K, points, weights, reps):
+    n = len(K)
+    kv = (ctypes.c_int64 * n)(*[int(k) for k in K])
+    _ck(_lib().sdf_batch_autotune(handle, kv, _ptr_array(points), _ptr_array(weights), int(reps)),
+        "sdf_batch_autotune")
+
+
 def sdf_batch_sync(handle):
     return int(_lib().sdf_batch_sync(handle))
 
@@ -402,6 +419,10 @@ class Plan:
             sdf_plan_set_full_range(self.handle, True)
         if kernel != "exp":
             self.set_kernel(kernel)
+
+    def set_padding(self, padded):
+        """Padded transform size per axis (sdf_plan_set_padding)."""
+        sdf_plan_set_padding(self.handle, padded)
 
     def set_kernel(self, kernel):
         """'exp' (the paper's G~, default) or 'green' (the exact Green's
@@ -552,6 +573,10 @@ class Batch:
         col = lambda k: [o.get(k) for o in outs] if any(k in o for o in outs) else None
         sdf_batch_execute(self.handle, K, points, weights, col("S"), col("dS"), col("d2S"), col("sign"),
                           col("flags"))
+
+    def autotune(self, points, weights, reps=2):
+        """sdf_batch_autotune on device tensors (padded sizes and tile schedules)."""
+        sdf_batch_autotune(self.handle, [int(p.shape[0]) for p in points], points, weights, reps)
 
     def sync(self):
         _ck(sdf_batch_sync(self.handle), "sdf_batch_sync")

@@ -11,8 +11,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsdf_gb300.so")
-SOURCES = ["api.cu", "points.cu", "passes_fwd.cu", "passes_fused.cu", "passes_inv.cu", "spectra.cu", "fixup.cu",
-           "adjoint.cu", "noalloc.cu", "batch.cu", "curvature.cu", "mesh.cu", "line1d.cu"]
+SOURCES = ["passes_fused_f2.cu", "passes_fused_f3.cu", "passes_inv.cu", "passes_fwd.cu", "passes_fused_d.cu",
+           "passes_fused.cu", "api.cu", "points.cu", "spectra.cu", "fixup.cu", "adjoint.cu", "noalloc.cu", "batch.cu",
+           "curvature.cu", "mesh.cu", "line1d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

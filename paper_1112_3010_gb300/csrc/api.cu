@@ -5,9 +5,15 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+#include <sys/stat.h>
+
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "green.cuh"
@@ -193,9 +199,7 @@ void plan_geometry(sdf_plan_impl *p, int D, const int64_t *dims, double h, doubl
     for (int a = 0; a < 3; ++a) {
         p->N[a] = (a < D) ? dims[a] : 1;
         p->M[a] = (a < D) ? std::max<int64_t>(16, next_pow2(2 * p->N[a] - 1)) : 1;
-        int l = 0;
-        while ((int64_t(1) << l) < p->M[a]) ++l;
-        p->logM[a] = l;
+        p->logM[a] = line_code(p->M[a]);
         p->nb[a] = (p->N[a] + kBin - 1) / kBin;
         p->nnodes *= p->N[a];
         p->nbins *= p->nb[a];
@@ -369,11 +373,91 @@ template <typename T>
 static cudaError_t upload_twiddles(void **dst, int64_t L, size_t *acc) {
     using V = typename cplx_t<T>::type;
     std::vector<V> h(L);
-    fill_twiddle_table(ilog2(L), h.data());
+    fill_twiddle_table(line_code(L), h.data());
     cudaError_t e = alloc(dst, sizeof(V) * L, acc);
     if (e != cudaSuccess) return e;
     return cudaMemcpy(*dst, h.data(), sizeof(V) * L, cudaMemcpyHostToDevice);
 }
+
+// Largest padded line the transforms take per dimension (the FFT core runs
+// up to 8192-point lines; 3D buffers are kept to 1024^3).
+static int64_t max_padded(int D) { return D == 3 ? 1024 : 8192; }
+
+// Smallest 3 * 2^k >= v (k >= 4), or 0 when it is not below the power of two.
+static int64_t r3_padding(int64_t v) {
+    int64_t m = 48;
+    while (m < v) m *= 2;
+    return m < next_pow2(v) ? m : 0;
+}
+
+namespace sdf {
+// Rebuild what depends on the padded sizes (twiddles, kernel spectra,
+// transform buffers, the adjoint's programme) for padded sizes M; with
+// share_from, take that plan's spectra (same geometry and M).  On error the
+// plan is left without buffers and must be destroyed.
+sdf_status plan_repad(sdf_plan_impl *p, const int64_t *M, const sdf_plan_impl *share_from) {
+    CK(cudaStreamSynchronize(p->stream));
+    const size_t vb = vbytes(p);
+    const int64_t esz = (p->prec == SDF_FP64) ? 8 : 4;
+    for (int a = 0; a < p->D; ++a) {
+        cudaFree(p->tw[a]);
+        p->tw[a] = nullptr;
+        p->workspace_bytes -= vb * p->M[a];
+    }
+    if (!p->shares_spectra) {
+        for (auto &k : p->kernels) {
+            cudaFree(k.c);
+            p->workspace_bytes -= esz * spec_rows(p) * spec_row_len(p);
+        }
+    }
+    p->kernels.clear();
+    for (int i = 0; i < KER_COUNT; ++i) p->kslot[i] = -1;
+    if (p->adj_ngroup > 0) {
+        cudaFree(p->adj_planes);
+        cudaFree(p->adj_part);
+        p->adj_planes = nullptr;
+        p->adj_part = nullptr;
+        p->workspace_bytes -= esz * (p->D + 1) * p->nnodes + sizeof(double) * 2 * kAdjParts;
+        p->adj_ngroup = 0;
+    }
+    cudaFree(p->bufA);
+    cudaFree(p->bufB);
+    p->bufA = p->bufB = nullptr;
+    p->workspace_bytes -= p->bytesA + p->bytesB;
+    for (int a = 0; a < p->D; ++a) {
+        p->M[a] = M[a];
+        p->logM[a] = line_code(M[a]);
+    }
+    for (int a = 0; a < p->D; ++a) {
+        if (p->prec == SDF_FP64) CK(upload_twiddles<double>(&p->tw[a], p->M[a], &p->workspace_bytes));
+        else CK(upload_twiddles<float>(&p->tw[a], p->M[a], &p->workspace_bytes));
+    }
+    if (share_from) {
+        p->kernels = share_from->kernels;
+        for (int i = 0; i < KER_COUNT; ++i) p->kslot[i] = share_from->kslot[i];
+        p->shares_spectra = true;
+    } else {
+        p->shares_spectra = false;
+        CK(build_kernel_list(p, plan_kernel_ids(p)));
+    }
+    plan_programme(p);
+    plan_buffer_sizes(p);
+    CK(alloc(&p->bufA, p->bytesA, &p->workspace_bytes));
+    CK(alloc(&p->bufB, p->bytesB, &p->workspace_bytes));
+    CK(cudaDeviceSynchronize());
+    return SDF_OK;
+}
+
+// Padded-size choices of a plan (sdf_plan_set_padding rules).
+bool padding_ok(const sdf_plan_impl *p, const int64_t *M) {
+    for (int a = 0; a < p->D; ++a) {
+        const int64_t need = std::max<int64_t>(16, 2 * p->N[a] - 1);
+        if (M[a] < need || M[a] > max_padded(p->D) || line_code(M[a]) < 0) return false;
+        if (line_r3(line_code(M[a])) && M[a] < 48) return false;
+    }
+    return true;
+}
+}  // namespace sdf
 
 extern "C" {
 
@@ -555,9 +639,9 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
         for (int j = 0; j < i; ++j)
             if (plans[j] == p) return SDF_ERR_INVALID_ARG;
         bool same = p->D == p0->D && p->prec == p0->prec && p->outputs == p0->outputs && p->h == p0->h;
-        for (int a = 0; a < 3; ++a) same = same && p->N[a] == p0->N[a];
+        for (int a = 0; a < 3; ++a) same = same && p->N[a] == p0->N[a] && p->M[a] == p0->M[a];
         if (!same) {
-            set_last_error("sdf_execute_multi: the plans differ in D, dims, h, precision or outputs");
+            set_last_error("sdf_execute_multi: the plans differ in D, dims, padded sizes, h, precision or outputs");
             return SDF_ERR_INVALID_ARG;
         }
         sdf_status s = check_execute_args(p, K, points, weights, at(dS, i), at(d2S, i), at(sign, i));
@@ -954,6 +1038,27 @@ sdf_status sdf_plan_set_full_range(sdf_plan p, int enable) {
     return SDF_OK;
 }
 
+sdf_status sdf_plan_set_padding(sdf_plan p, const int64_t *padded) {
+    if (!p || !padded) return SDF_ERR_INVALID_ARG;
+    if (p->D == 1) {
+        set_last_error("sdf_plan_set_padding: 1D plans keep their power-of-two line");
+        return SDF_ERR_UNSUPPORTED;
+    }
+    if (p->shares_spectra) {
+        set_last_error("sdf_plan_set_padding: the plan uses spectra owned by another plan of its batch");
+        return SDF_ERR_UNSUPPORTED;
+    }
+    if (!padding_ok(p, padded)) {
+        set_last_error("sdf_plan_set_padding: each M_a must be 2^k or 3*2^k (>= 48), >= max(2 N_a - 1, 16), "
+                       "and within the transform limit");
+        return SDF_ERR_INVALID_ARG;
+    }
+    bool same = true;
+    for (int a = 0; a < p->D; ++a) same = same && padded[a] == p->M[a];
+    if (same) return SDF_OK;
+    return plan_repad(p, padded, nullptr);
+}
+
 sdf_status sdf_plan_set_kernel(sdf_plan p, int kernel_set) {
     if (!p || (kernel_set != SDF_KERNEL_EXP && kernel_set != SDF_KERNEL_GREEN)) return SDF_ERR_INVALID_ARG;
     if (kernel_set == p->kernel_set) return SDF_OK;
@@ -1003,7 +1108,8 @@ sdf_status sdf_green_profile(int D, int64_t n, const double *z, double *g, doubl
     return SDF_OK;
 }
 
-// Device time of the named kernels over `reps` executes (after one warm-up).
+// Device time of the named kernels (every kernel when nnames = 0) over `reps`
+// executes (after one warm-up).
 static sdf_status time_kernels(sdf_plan p, int64_t K, const double *points, const double *weights, int reps,
                                const char *const *names, int nnames, double *ms) {
     sdf_status s = sdf_execute(p, K, points, weights, nullptr, nullptr, nullptr, nullptr, nullptr);
@@ -1021,10 +1127,99 @@ static sdf_status time_kernels(sdf_plan p, int64_t K, const double *points, cons
     if (s != SDF_OK) return s;
     if (n < 0) return SDF_ERR_CUDA;
     *ms = 0;
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
+        if (nnames == 0) *ms += kt[i].total_ms;
         for (int j = 0; j < nnames; ++j)
             if (strcmp(kt[i].name, names[j]) == 0) *ms += kt[i].total_ms;
+    }
     return SDF_OK;
+}
+
+// ---- the autotuner's cache: one line per tuned problem,
+// "<key>\t<M0> <M1> <M2> <lines_T> <lines_F> <fused_variant>", the last line
+// of a key wins.  Path: $SDF_AUTOTUNE_CACHE (empty: no cache), else
+// $XDG_CACHE_HOME/sdf_gb300/autotune.tsv, else $HOME/.cache/sdf_gb300/autotune.tsv.
+static std::mutex g_tune_mutex;
+
+static std::string tune_cache_path() {
+    const char *e = getenv("SDF_AUTOTUNE_CACHE");
+    if (e) return std::string(e);
+    std::string base;
+    const char *x = getenv("XDG_CACHE_HOME");
+    if (x && *x) {
+        base = x;
+    } else {
+        const char *h = getenv("HOME");
+        if (!h || !*h) return std::string();
+        base = std::string(h) + "/.cache";
+    }
+    return base + "/sdf_gb300/autotune.tsv";
+}
+
+// GPU name and architecture, D, node counts, precision, outputs, kernel set.
+static std::string tune_key(const sdf_plan_impl *p) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    std::string gpu = "unknown";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+        gpu = prop.name;
+        gpu += " sm_" + std::to_string(prop.major) + std::to_string(prop.minor);
+    }
+    cudaGetLastError();
+    for (auto &c : gpu)
+        if (c == '\t' || c == '\n' || c == '|') c = ' ';
+    char buf[256];
+    snprintf(buf, sizeof buf, "|D%d|%lldx%lldx%lld|%s|out%u|kernel%d", p->D, (long long)p->N[0], (long long)p->N[1],
+             (long long)p->N[2], p->prec == SDF_FP64 ? "fp64" : "fp32", p->outputs, p->kernel_set);
+    return gpu + buf;
+}
+
+struct TuneRec {
+    int64_t M[3];
+    int RT, RF, FV;
+};
+
+static bool tune_lookup(const std::string &key, TuneRec *out) {
+    const std::string path = tune_cache_path();
+    if (path.empty()) return false;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return false;
+    bool found = false;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        char *tab = strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        if (key != line) continue;
+        long long m0, m1, m2;
+        int rt, rf, fv;
+        if (sscanf(tab + 1, "%lld %lld %lld %d %d %d", &m0, &m1, &m2, &rt, &rf, &fv) == 6) {
+            out->M[0] = m0;
+            out->M[1] = m1;
+            out->M[2] = m2;
+            out->RT = rt;
+            out->RF = rf;
+            out->FV = fv;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void tune_store(const std::string &key, const TuneRec &r) {
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    // create the directories on the way (ignore failures: the cache is optional)
+    for (size_t i = 1; i < path.size(); ++i)
+        if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "%s\t%lld %lld %lld %d %d %d\n", key.c_str(), (long long)r.M[0], (long long)r.M[1], (long long)r.M[2],
+            r.RT, r.RF, r.FV);
+    fclose(f);
 }
 
 sdf_status sdf_plan_autotune(sdf_plan p, int64_t K, const double *points, const double *weights, int reps,
@@ -1034,10 +1229,69 @@ sdf_status sdf_plan_autotune(sdf_plan p, int64_t K, const double *points, const 
         set_last_error("sdf_plan_autotune: a 1D plan has no tile schedule");
         return SDF_ERR_UNSUPPORTED;
     }
+    auto report = [&]() {
+        if (lines_T) *lines_T = p->tune_RT;
+        if (lines_F) *lines_F = p->tune_RF;
+        if (fused_variant) *fused_variant = p->tune_FV;
+    };
+    const std::string key = tune_key(p);
+    TuneRec rec;
+    if (tune_lookup(key, &rec)) {
+        bool sameM = true;
+        for (int a = 0; a < p->D; ++a) sameM = sameM && rec.M[a] == p->M[a];
+        if (!sameM && !p->shares_spectra && padding_ok(p, rec.M)) {
+            sdf_status s = plan_repad(p, rec.M, nullptr);
+            if (s != SDF_OK) return s;
+        }
+        p->tune_RT = rec.RT;
+        p->tune_RF = rec.RF;
+        p->tune_FV = rec.FV;
+        report();
+        return SDF_OK;
+    }
+    // 1. padded sizes: per axis the power of two, or 3 * 2^k where that is
+    // smaller; every combination timed over the whole execute (default tile
+    // schedule).  A plan of a batch that borrows its spectra keeps its sizes.
+    p->tune_RT = p->tune_RF = p->tune_FV = 0;
+    if (!p->shares_spectra) {
+        std::vector<std::vector<int64_t>> opts(p->D);
+        size_t ncomb = 1;
+        for (int a = 0; a < p->D; ++a) {
+            const int64_t need = std::max<int64_t>(16, 2 * p->N[a] - 1);
+            opts[a].push_back(std::max<int64_t>(16, next_pow2(need)));
+            const int64_t r3 = r3_padding(need);
+            if (r3 && r3 <= max_padded(p->D)) opts[a].push_back(r3);
+            ncomb *= opts[a].size();
+        }
+        if (ncomb > 1) {
+            double best = 1e300;
+            int64_t bestM[3] = {p->M[0], p->M[1], p->M[2]};
+            for (size_t c = 0; c < ncomb; ++c) {
+                int64_t M[3] = {1, 1, 1};
+                size_t r = c;
+                for (int a = 0; a < p->D; ++a) {
+                    M[a] = opts[a][r % opts[a].size()];
+                    r /= opts[a].size();
+                }
+                sdf_status s = sdf_plan_set_padding(p, M);
+                if (s != SDF_OK) return s;
+                double ms;
+                s = time_kernels(p, K, points, weights, reps, nullptr, 0, &ms);
+                if (s != SDF_OK) return s;
+                if (ms < best) {
+                    best = ms;
+                    for (int a = 0; a < 3; ++a) bestM[a] = M[a];
+                }
+            }
+            sdf_status s = sdf_plan_set_padding(p, bestM);
+            if (s != SDF_OK) return s;
+        }
+    }
+    // 2. the tile schedule on those sizes
     const char *tnames[] = {"xpass", "fwd_y", "inv_y", "epilogue"};
     const char *fnames[] = {"fused"};
     double best = 1e300;
-    int bestT = p->tune_RT, bestF = p->tune_RF, bestV = p->tune_FV;
+    int bestT = 0, bestF = 0, bestV = 0;
     for (int RT : {0, 1, 2, 4, 8, 16}) {
         p->tune_RT = RT;
         double ms;
@@ -1066,9 +1320,12 @@ sdf_status sdf_plan_autotune(sdf_plan p, int64_t K, const double *points, const 
     }
     p->tune_RF = bestF;
     p->tune_FV = bestV;
-    if (lines_T) *lines_T = bestT;
-    if (lines_F) *lines_F = bestF;
-    if (fused_variant) *fused_variant = bestV;
+    for (int a = 0; a < 3; ++a) rec.M[a] = p->M[a];
+    rec.RT = bestT;
+    rec.RF = bestF;
+    rec.FV = bestV;
+    tune_store(key, rec);
+    report();
     return SDF_OK;
 }
 

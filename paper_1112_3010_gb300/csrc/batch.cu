@@ -192,6 +192,63 @@ sdf_status sdf_batch_execute(sdf_batch b, const int64_t *K, const double *const 
     return SDF_OK;
 }
 
+sdf_status sdf_batch_autotune(sdf_batch b, const int64_t *K, const double *const *points,
+                              const double *const *weights, int reps) {
+    if (!b || !K || !points || reps < 1) return SDF_ERR_INVALID_ARG;
+    const int n = b->n;
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return fail(e);
+    // the owner of each problem's spectra: the first problem of its geometry
+    std::vector<int> owner(n, -1);
+    for (int i = 0; i < n; ++i) {
+        if (!b->plans[i]->shares_spectra) {
+            owner[i] = i;
+            continue;
+        }
+        for (int j = 0; j < i && owner[i] < 0; ++j) {
+            sdf_plan pj = b->plans[j], pi = b->plans[i];
+            bool same = !pj->shares_spectra && pj->h == pi->h && pj->tau == pi->tau;
+            for (int a = 0; a < b->D; ++a) same = same && pj->N[a] == pi->N[a];
+            if (same) owner[i] = j;
+        }
+        if (owner[i] < 0) return SDF_ERR_INVALID_ARG;  // cannot happen for a batch built by sdf_batch_create
+    }
+    // tune each owner on its own problem (padded sizes and tile schedule) ...
+    for (int i = 0; i < n; ++i) {
+        if (owner[i] != i) continue;
+        int rt, rf, fv;
+        sdf_status s = sdf_plan_autotune(b->plans[i], K[i], points[i], weights ? weights[i] : nullptr, reps, &rt,
+                                         &rf, &fv);
+        if (s != SDF_OK) return s;
+    }
+    // ... and give its sizes, spectra and schedule to the problems that share them
+    for (int i = 0; i < n; ++i) {
+        if (owner[i] == i) continue;
+        sdf_plan o = b->plans[owner[i]], pi = b->plans[i];
+        bool sameM = true;
+        for (int a = 0; a < b->D; ++a) sameM = sameM && o->M[a] == pi->M[a];
+        if (!sameM) {
+            sdf_status s = plan_repad(pi, o->M, o);
+            if (s != SDF_OK) return s;
+        }
+        pi->tune_RT = o->tune_RT;
+        pi->tune_RF = o->tune_RF;
+        pi->tune_FV = o->tune_FV;
+    }
+    // the captured graph is stale now: the next sdf_batch_execute captures anew
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->K.clear();
+    b->ptrs.clear();
+    return SDF_OK;
+}
+
 sdf_status sdf_batch_sync(sdf_batch b) {
     if (!b) return SDF_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(b->stream);

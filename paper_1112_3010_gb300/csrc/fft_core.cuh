@@ -1,6 +1,7 @@
 // fft_core.cuh -- the FFT building block shared by every transform pass.
 //
-// One CTA transforms R lines of length L = 2^logL (16 <= L <= 8192) at once.
+// One CTA transforms R lines of length L = 2^k (16 <= L <= 8192) or
+// L = 3 * 2^k (48 <= L <= 6144; see fft_line_r3) at once.
 // Each line gets TPL = L/16 threads; thread t of a line owns the 16 elements
 // t + m*TPL (m = 0..15) both on entry and on exit, so a forward transform's
 // output registers feed an inverse transform's input registers directly (the
@@ -58,18 +59,47 @@ __host__ __device__ __forceinline__ int ilog2(int64_t L) {
     return k;
 }
 
-// Host: the twiddle table of an L = 2^logL line, in the layout above
-// (h holds L entries; the last 16 stay zero).
-template <typename V> inline void fill_twiddle_table(int logL, V *h) {
+// Line codes.  A line of L = 2^k points has code k; a line of L = 3 * 2^k
+// points has code k | kLineR3 (its transform starts with a radix-3 stage).
+constexpr int kLineR3 = 1 << 8;
+__host__ __device__ __forceinline__ int line_len(int lc) { return ((lc & kLineR3) ? 3 : 1) << (lc & 0xff); }
+__host__ __device__ __forceinline__ bool line_r3(int lc) { return (lc & kLineR3) != 0; }
+// Code of a length 2^k or 3 * 2^k (-1 for any other length).
+inline int line_code(int64_t L) {
+    int k = 0;
+    int64_t q = L;
+    const bool r3 = (q % 3) == 0;
+    if (r3) q /= 3;
+    while (((int64_t)1 << k) < q) ++k;
+    return (((int64_t)1 << k) == q) ? (k | (r3 ? kLineR3 : 0)) : -1;
+}
+
+// Host: the twiddle table of a line with code lc, in the layout above (h
+// holds L entries, the unused tail stays zero).  Lines of 3 * 2^k points:
+// after the radix-3 stage (span 1, no twiddles) the radix-16 stages have
+// spans Ns = 3 * 16^s and keep w_{16 Ns}^{r k} at r*Ns + k - 3; a final
+// radix-P stage (span Ns = L/P) keeps w_L^{r j} at r*Ns + j - 3.
+template <typename V> inline void fill_twiddle_table(int lc, V *h) {
     using T = decltype(V::x);
-    const int64_t L = (int64_t)1 << logL;
-    const int nst = logL >> 2, rem = logL & 3;
+    const int64_t L = line_len(lc);
     for (int64_t e = 0; e < L; ++e) h[e].x = h[e].y = T(0);
     auto put = [&](int64_t e, int64_t i) {  // w_L^i
         const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)i / (long double)L;
         h[e].x = (T)cosl(ang);
         h[e].y = (T)sinl(ang);
     };
+    if (line_r3(lc)) {
+        int64_t Ns = 3;
+        for (; 16 * Ns <= L; Ns *= 16)
+            for (int64_t r = 1; r < 16; ++r)
+                for (int64_t k = 0; k < Ns; ++k) put(r * Ns + k - 3, r * k * (L / (16 * Ns)));
+        if (Ns < L)
+            for (int64_t r = 1; r < L / Ns; ++r)
+                for (int64_t j = 0; j < Ns; ++j) put(r * Ns + j - 3, r * j);
+        return;
+    }
+    const int logL = lc;
+    const int nst = logL >> 2, rem = logL & 3;
     for (int s = 1; s < nst; ++s) {
         const int64_t Ns = (int64_t)1 << (4 * s);
         for (int64_t r = 1; r < 16; ++r)
@@ -155,6 +185,19 @@ template <bool INV, typename V> __device__ __forceinline__ void dft4(V &a, V &b,
     c = csub(t0, t2);
     b = cadd(t1, t3);
     d = csub(t1, t3);
+}
+
+// 3-point DFT in place, natural order: y_q = sum_r x_r w3^{rq}, w3 = e^{-+2 pi i/3}.
+template <bool INV, typename V> __device__ __forceinline__ void dft3(V &a, V &b, V &c) {
+    using T = decltype(V::x);
+    const T h3 = T(0.86602540378443864676);  // sqrt(3)/2
+    const V s = cadd(b, c), d = csub(b, c);
+    const V m = mk<V>(a.x - T(0.5) * s.x, a.y - T(0.5) * s.y);
+    // forward: y1 = m - i h3 d, y2 = m + i h3 d (inverse: the other way)
+    const V id = INV ? mk<V>(-h3 * d.y, h3 * d.x) : mk<V>(h3 * d.y, -h3 * d.x);
+    a = cadd(a, s);
+    b = cadd(m, id);
+    c = csub(m, id);
 }
 
 template <bool INV, typename V> __device__ __forceinline__ void dft2(V &a, V &b) {
@@ -314,9 +357,75 @@ __device__ __forceinline__ bool fft_stage16(V (&v)[16], V *sm, int t, int logL, 
     return true;
 }
 
+// L = 3 * 2^lg point line (run-time length).  A radix-3 Stockham stage
+// (span 1) goes through shared memory: the Q = L/3 butterflies (x[j],
+// x[j + Q], x[j + 2Q]) -> (y[3j], y[3j + 1], y[3j + 2]) are spread over the
+// line's TPL = L/16 threads (16/3 per thread, so up to 6); then radix-16
+// stages of span Ns = 3 * 16^s and a final radix-2/4/8 stage, as for powers
+// of two but with the twiddle offset 3 (fill_twiddle_table).
+// LG > 0 fixes lg at compile time (the stage loop unrolls, spans and
+// addresses become constants).
+template <bool INV, int LG = 0, typename V>
+__device__ __forceinline__ void fft_line_r3(V (&v)[16], V *sm, int t, int lg, const V *__restrict__ tw) {
+    if constexpr (LG > 0) lg = LG;
+    const int L = 3 << lg, TPL = L >> 4, Q = 1 << lg;
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[pad16(t + m * TPL)] = v[m];
+    __syncthreads();
+    V a[6][3];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const int j = t + i * TPL;
+        if (j < Q) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) a[i][r] = sm[pad16(j + r * Q)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const int j = t + i * TPL;
+        if (j < Q) {
+            dft3<INV>(a[i][0], a[i][1], a[i][2]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sm[pad16(3 * j + q)] = a[i][q];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = sm[pad16(t + m * TPL)];
+    int Ns = 3;
+#pragma unroll
+    for (int st = 0; st < 3 && 16 * Ns <= L; ++st, Ns *= 16) {
+        const int k = t % Ns;
+        const V *ts = tw + (k - 3);  // w_{16 Ns}^{r k} at ts[r * Ns]
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            V w = ldtw(ts, r * Ns);
+            v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+        }
+        dft16<INV>(v);
+        if (16 * Ns == L) return;  // v[q] = X[t + q TPL]
+        __syncthreads();
+        const int base = (t - k) * 16 + k;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) sm[pad16(base + q * Ns)] = v[q];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = sm[pad16(t + m * TPL)];
+    }
+    // final stage (twiddles at r*Ns + j - 3: final_stage reads r*Ns + j - 16)
+    const int P = L / Ns;
+    if (P == 2) final_stage<2, INV>(v, t, TPL, Ns, tw + 13);
+    else if (P == 4) final_stage<4, INV>(v, t, TPL, Ns, tw + 13);
+    else final_stage<8, INV>(v, t, TPL, Ns, tw + 13);
+}
+
 // L-point FFT (forward: exp(-2 pi i nk/L); inverse: exp(+2 pi i nk/L), not
 // normalised) of one line.  On entry v[m] = x[t + m*TPL]; on exit
 // v[m] = X[t + m*TPL].  `sm` is this line's shared buffer of pad16(L) elements.
+// logL is a line code (line_len): L = 2^logL, or 3 * 2^k for k | kLineR3.
 // Every thread of the CTA must call this with the same logL (it synchronises).
 // `tw` is the table of L twiddles (shared memory for float, global for double).
 // LOGL > 0 fixes log2 L at compile time (logL is then ignored): every stage is
@@ -324,7 +433,9 @@ __device__ __forceinline__ bool fft_stage16(V (&v)[16], V *sm, int t, int logL, 
 // outputs never read cost nothing.
 template <bool INV, int LOGL = 0, typename V>
 __device__ __forceinline__ void fft_line(V (&v)[16], V *sm, int t, int logL, const V *__restrict__ tw) {
-    if constexpr (LOGL > 0) {
+    if constexpr (LOGL > 0 && (LOGL & kLineR3) != 0) {
+        fft_line_r3<INV, (LOGL & 0xff)>(v, sm, t, LOGL & 0xff, tw);
+    } else if constexpr (LOGL > 0) {
         constexpr int nst = LOGL >> 2, rem = LOGL & 3;
 #pragma unroll
         for (int s = 0; s < nst; ++s)
@@ -334,6 +445,10 @@ __device__ __forceinline__ void fft_line(V (&v)[16], V *sm, int t, int logL, con
         else if constexpr (rem == 2) final_stage<4, INV>(v, t, TPL, Ns, tw);
         else if constexpr (rem == 3) final_stage<8, INV>(v, t, TPL, Ns, tw);
     } else {
+        if (line_r3(logL)) {
+            fft_line_r3<INV>(v, sm, t, logL & 0xff, tw);
+            return;
+        }
         const int TPL = (1 << logL) >> 4;
         const int nst = logL >> 2, rem = logL & 3;
         for (int s = 0; s < nst; ++s)

@@ -76,7 +76,7 @@ template <typename T>
 cudaError_t fill_twiddles(void *dst, int64_t L, cudaStream_t st) {
     using V = typename cplx_t<T>::type;
     std::vector<V> h(L);
-    fill_twiddle_table(ilog2(L), h.data());
+    fill_twiddle_table(line_code(L), h.data());
     return cudaMemcpyAsync(dst, h.data(), sizeof(V) * L, cudaMemcpyHostToDevice, st);
 }
 

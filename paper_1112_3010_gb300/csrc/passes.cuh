@@ -42,7 +42,7 @@ struct LineCfg {
 static inline LineCfg line_cfg(int logL, int R) {
     LineCfg c;
     c.logL = logL;
-    c.L = 1 << logL;
+    c.L = line_len(logL);
     c.TPL = c.L >> 4;
     c.PL = pad16(c.L);
     c.R = R;
@@ -52,7 +52,7 @@ static inline LineCfg line_cfg(int logL, int R) {
 // Lines per CTA: the largest power of two with R*TPL <= max_threads,
 // line_smem(R, L) <= smem budget and R <= r_cap.
 static inline int pick_R(int logL, size_t vbytes, int max_threads, int r_cap, size_t smem_budget) {
-    const int L = 1 << logL, TPL = L >> 4;
+    const int L = line_len(logL), TPL = L >> 4;
     int R = 1;
     while (R * 2 <= r_cap && (R * 2) * TPL <= max_threads && line_smem(R * 2, L, (int)vbytes) <= smem_budget) R *= 2;
     return R;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(MT) k_xpass_cells(const int *__restrict__ bin_
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int L = line_len(logL), TPL = L >> 4, PL = pad16(L);
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
@@ -141,7 +141,7 @@ __global__ void SDF_LB(T) k_xpass_dense(const T *__restrict__ w, const T *__rest
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int L = line_len(logL), TPL = L >> 4, PL = pad16(L);
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(MT) k_fwd_T(const cx<T> *__restrict__ in, cx<T
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int L = line_len(logL), TPL = L >> 4, PL = pad16(L);
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(FV ? 256 : 512, FV ? 2 : 1) k_fused(const cx<T
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int L = line_len(logL), TPL = L >> 4, PL = pad16(L);
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     // consecutive line ids visit frequency pairs (k, M-k), which read the same
     // folded spectrum row: the second read hits L2
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(512, 1) k_fused2p(const cx<T> *__restrict__ in
     using V = cx<T>;
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ __align__(16) unsigned char smraw_p[];
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int L = line_len(logL), TPL = L >> 4, PL = pad16(L);
     const int64_t Hp = P.Hp;
     T *crow = reinterpret_cast<T *>(smraw_p);                      // nker rows of Hp
     V *sm = reinterpret_cast<V *>(smraw_p + sizeof(T) * nker * Hp);  // two exchange lines
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(MT) k_inv_T(const cx<T> *__restrict__ in, cx<T
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int L = line_len(logL), TPL = L >> 4, PL = pad16(L);
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int L = line_len(logL), TPL = L >> 4, PL = pad16(L);
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;
@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
         }
     }
     // capped nodes (the FP32 fix-up takes back the ones it recomputes)
-    ncap = __reduce_add_sync(0xffffffffu, ncap);
+    ncap = __reduce_add_sync(__activemask(), ncap);  // the last warp of a CTA may be partial
     if ((threadIdx.x & 31) == 0 && ncap) atomicAdd(&P.dsc_w->n_capped, (unsigned long long)ncap);
 }
 
@@ -729,9 +729,9 @@ template <typename T>
 static inline int tuned_R(const sdf_plan_impl *p, int logL, int maxthr = max_threads<T>()) {
     const int def = pick_R(logL, sizeof(cx<T>), maxthr, 16, kSmemBudget);
     if (!p || p->tune_RT <= 0) return def;
-    const int TPL = (1 << logL) >> 4;
+    const int TPL = line_len(logL) >> 4;
     int R = p->tune_RT;
-    while (R > 1 && (R * TPL > maxthr || line_smem(R, 1 << logL, (int)sizeof(cx<T>)) > kSmemBudget)) R >>= 1;
+    while (R > 1 && (R * TPL > maxthr || line_smem(R, line_len(logL), (int)sizeof(cx<T>)) > kSmemBudget)) R >>= 1;
     return R;
 }
 
@@ -751,22 +751,26 @@ static inline int xpass_max_threads(int logL) {
     } while (0)
 
 // CALL(LG) with LG = logL for the float line lengths compiled with a fixed
-// size (256 to 4096 points: every length the workloads use) and LG = 0 (the
-// length read at run time) for the rest and for double.
-#define SDF_BY_LOGL(T, logL, CALL)          \
-    do {                                    \
-        if constexpr (sizeof(T) == 4) {     \
-            switch (logL) {                 \
-                case 8: CALL(8); break;     \
-                case 9: CALL(9); break;     \
-                case 10: CALL(10); break;   \
-                case 11: CALL(11); break;   \
-                case 12: CALL(12); break;   \
-                default: CALL(0); break;    \
-            }                               \
-        } else {                            \
-            CALL(0);                        \
-        }                                   \
+// size (256 to 4096 points, and 768, 1536, 3072 = 3 * 2^k: every length the
+// workloads use) and LG = 0 (the length read at run time) for the rest and
+// for double.
+#define SDF_BY_LOGL(T, logL, CALL)                                  \
+    do {                                                            \
+        if constexpr (sizeof(T) == 4) {                             \
+            switch (logL) {                                         \
+                case 8: CALL(8); break;                             \
+                case 9: CALL(9); break;                             \
+                case 10: CALL(10); break;                           \
+                case 11: CALL(11); break;                           \
+                case 12: CALL(12); break;                           \
+                case 8 | kLineR3: CALL(8 | kLineR3); break;         \
+                case 9 | kLineR3: CALL(9 | kLineR3); break;         \
+                case 10 | kLineR3: CALL(10 | kLineR3); break;       \
+                default: CALL(0); break;                            \
+            }                                                       \
+        } else {                                                    \
+            CALL(0);                                                \
+        }                                                           \
     } while (0)
 
 // adj: the adjoint programme (transform of a = w/phi) instead of the forward one
@@ -798,6 +802,17 @@ static inline FusedParams make_fused_params(const sdf_plan_impl *p, bool adj = f
     F.Hp = spec_row_len(p);
     return F;
 }
+
+// Launch one variant of the fused pass (defined, and explicitly instantiated
+// for every variant fused_step launches, in passes_fused_kern.cuh's users).
+template <typename T, int DD, int FVV, int LG>
+cudaError_t run_fused(unsigned grid, int nthr, size_t smem, cudaStream_t st, const cx<T> *fin, cx<T> *fout, int logL,
+                      int n_in, int n_out, int R, int64_t n_lines, int64_t in_fs, int64_t out_fs, const FusedParams &F,
+                      const cx<T> *twl, const FusedParams &F1, cx<T> *fout1);
+template <typename T, int LG>
+cudaError_t run_fused2p(unsigned grid, int nthr, size_t smem, cudaStream_t st, const cx<T> *fin, cx<T> *fout,
+                        int logL, int n_in, int n_out, int64_t in_fs, int64_t out_fs, const FusedParams &F, int nker,
+                        const cx<T> *twl);
 
 // The fused pass (passes_fused.cu): forward along the last axis, multiply by
 // the kernel spectra, inverse; dense: the adjoint programme.

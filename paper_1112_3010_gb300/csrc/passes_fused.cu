@@ -1,6 +1,8 @@
 // passes_fused.cu -- launcher of the fused pass (Table 1 steps 3-5 of the
 // paper): forward transform along the last axis, multiply by every kernel
-// spectrum, inverse transform along the same axis.
+// spectrum, inverse transform along the same axis.  The kernel variants are
+// compiled in passes_fused_f2.cu, passes_fused_f3.cu and passes_fused_d.cu
+// (in parallel); this file only chooses and launches them.
 #include "passes.cuh"
 
 namespace sdf {
@@ -14,7 +16,7 @@ cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL
     const int D = p->D;
     const int64_t N1 = p->N[1], N2 = p->N[2], M0 = p->M[0];
     {
-        const int TPL = (1 << logL) >> 4;
+        const int TPL = line_len(logL) >> 4;
         int R = 1;
         while (R * 2 * TPL <= 256) R *= 2;
         if (p->tune_RF > 0) {
@@ -46,22 +48,24 @@ cudaError_t fused_step(sdf_plan_impl *p, const cx<T> *fin, cx<T> *fout, int logL
         // per-line variant below measured faster on GB300 and is the default
         const size_t smem2p = (!dense && sizeof(T) == 4) ? fused2p_smem(p) : 0;
         if (smem2p && p->tune_FV == 3 && !p1) {
-#define SDF_F2P(LG)                                                                                        \
-    do {                                                                                                   \
-        if ((e = set_smem<T>((const void *)k_fused2p<T, LG>, smem2p)) != cudaSuccess) return e;            \
-        k_fused2p<T, LG><<<(unsigned)(M0 / 2 + 1), 2 * TPL, smem2p, st>>>(                                 \
-            fin, fout, logL, n_in, (int)n_out, in_fs, out_fs, F, (int)p->kernels.size(), twl);        \
+#define SDF_F2P(LG)                                                                                     \
+    do {                                                                                                \
+        if ((e = run_fused2p<T, LG>((unsigned)(M0 / 2 + 1), 2 * TPL, smem2p, st, fin, fout, logL, n_in,  \
+                                    (int)n_out, in_fs, out_fs, F, (int)p->kernels.size(), twl)) !=      \
+            cudaSuccess)                                                                                \
+            return e;                                                                                   \
     } while (0)
             if constexpr (sizeof(T) == 4) SDF_BY_LOGL(T, logL, SDF_F2P);
 #undef SDF_F2P
             prof_end(p, st);
             return cudaGetLastError();
         }
-#define SDF_FUSED(DD, FVV, LG)                                                                                   \
-    do {                                                                                                         \
-        if ((e = set_smem<T>((const void *)k_fused<T, DD, FVV, LG>, smem)) != cudaSuccess) return e;            \
-        k_fused<T, DD, FVV, LG><<<(unsigned)grid, R * c.TPL, smem, st>>>(fin, fout, logL, n_in, (int)n_out, R, \
-                                                                      n_lines, in_fs, out_fs, F, twl, F1, fout1); \
+#define SDF_FUSED(DD, FVV, LG)                                                                               \
+    do {                                                                                                     \
+        if ((e = run_fused<T, DD, FVV, LG>((unsigned)grid, R * c.TPL, smem, st, fin, fout, logL, n_in,        \
+                                           (int)n_out, R, n_lines, in_fs, out_fs, F, twl, F1, fout1)) !=     \
+            cudaSuccess)                                                                                     \
+            return e;                                                                                        \
     } while (0)
 #define SDF_FUSED2(LG) SDF_FUSED(2, 0, LG)
 #define SDF_FUSED3(LG) SDF_FUSED(3, 0, LG)

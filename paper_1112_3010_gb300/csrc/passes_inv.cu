@@ -138,7 +138,7 @@ __global__ void SDF_LB(T) k_epi_dense(const cx<T> *__restrict__ in, int logL, in
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int L = 1 << logL, TPL = L >> 4, PL = pad16(L);
+    const int L = line_len(logL), TPL = L >> 4, PL = pad16(L);
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
     const int64_t line = (int64_t)blockIdx.x * R + lr;
     const bool valid = line < n_lines;

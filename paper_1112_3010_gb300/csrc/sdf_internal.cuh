@@ -185,6 +185,10 @@ inline int64_t spec_rows(const sdf_plan_impl *p) {
 
 sdf_status plan_create_shared(sdf_plan *out, int D, const int64_t *dims, double h, double tau, int precision,
                               unsigned outputs, void *stream, const sdf_plan_impl *share_from);
+// New padded sizes (twiddles, spectra, buffers rebuilt; share_from: borrow
+// its spectra), and whether sizes M are allowed for plan p.
+sdf_status plan_repad(sdf_plan_impl *p, const int64_t *M, const sdf_plan_impl *share_from);
+bool padding_ok(const sdf_plan_impl *p, const int64_t *M);
 
 // plan set-up steps shared by sdf_plan_create and sdf_execute_noalloc
 void plan_geometry(sdf_plan_impl *p, int D, const int64_t *dims, double h, double tau, int precision,

@@ -265,7 +265,7 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
     for (int a = 0; a < D; ++a) {
         const int64_t L = p->M[a];
         std::vector<double2> h(L);
-        fill_twiddle_table(ilog2(L), h.data());
+        fill_twiddle_table(line_code(L), h.data());
         if ((e = cudaMalloc(&tw64[a], sizeof(double2) * L)) != cudaSuccess) return e;
         if ((e = cudaMemcpy(tw64[a], h.data(), sizeof(double2) * L, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     }
