@@ -201,9 +201,19 @@ def algorithmic_bytes(plan_info, name, stats, n_field, n_group, n_kern):
 FIXUP_FMA_OPS = 19
 
 
-def fixup_peak_gterms():
-    """FP32-pipe bound on the fix-up's node-point terms per second (GB300)."""
-    sms, lanes, ghz = 152, 128, 2.07
+def fixup_peak_gterms(sms=None):
+    """FP32-pipe bound on the fix-up's node-point terms per second: the
+    device's multiprocessors x 128 FP32 lanes x the maximum SM clock (from
+    MEASURED_PEAKS.json, else 2.07 GHz) / FMA-pipe operations per term."""
+    lanes, ghz = 128, 2.07
+    if sms is None:
+        sms = 152
+        try:
+            import torch
+            if torch.cuda.is_available():
+                sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        except Exception:
+            pass
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         ghz = float(json.load(open(p)).get("sm_max_mhz", 2070.0)) / 1000.0
@@ -580,11 +590,12 @@ def main():
         n, t = prof["fixup"]
         terms = sum(st.n_fixup_terms for st in stats)  # all plans, one execute each
         ach = terms / (t / n * len(plans) * 1e-3) / 1e9
-        peak = fixup_peak_gterms()
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        peak = fixup_peak_gterms(sms)
         roof = {"kernel": "fixup", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gterm/s",
                 "frac": ach / peak, "traffic": measured_traffic("fixup", n_launch_terms=terms / len(plans)),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / %d FMA-pipe ops per term"
-                               % FIXUP_FMA_OPS,
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x max SM clock / %d FMA-pipe ops per term"
+                               % (sms, FIXUP_FMA_OPS),
                 "avg_launch_ms": t / n}
     elif dom in passes:
         pz = passes[dom]

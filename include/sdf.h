@@ -352,6 +352,22 @@ sdf_status sdf_plan_set_noise_constants(sdf_plan plan, double c_fp32, double c_f
 sdf_status sdf_plan_set_tuning(sdf_plan plan, int lines_T, int lines_F, int fused_variant);
 
 /*
+ * sdf_plan_set_epilogue_loads -- how the epilogue (the last inverse
+ * transform and Table 1 step 6) reads its transposed input.  mode 0 (the
+ * default): SDF_FP32 plans whose last-axis lines have a compiled length
+ * that is a multiple of 256 (256 ... 4096, 768, 1536, 3072) with at least
+ * two lines per CTA and an even line count stage each group's lines in
+ * shared memory by TMA tensor copies (cp.async.bulk.tensor, mbarrier
+ * completion), the next group's copy overlapping the current group's
+ * transform; other plans load per thread.  mode 1: per-thread loads always.
+ * Results are identical either way.  A TMA wait that does not complete
+ * within a bounded number of polls makes the execute report
+ * SDF_ERR_TIMEOUT (sdf_sync).  SDF_ERR_INVALID_ARG for another mode or a
+ * NULL plan.  sdf_plan_autotune times both.
+ */
+sdf_status sdf_plan_set_epilogue_loads(sdf_plan plan, int mode);
+
+/*
  * sdf_plan_autotune -- choose the padded sizes and the tile schedule by
  * timing them on the plan's stream with the given inputs (as sdf_execute;
  * outputs are not written), keep the fastest, and report the schedule in
@@ -361,8 +377,9 @@ sdf_status sdf_plan_set_tuning(sdf_plan plan, int lines_T, int lines_F, int fuse
  *      it is smaller, the least 3 * 2^k >= 2 N_a - 1 (sdf_plan_set_padding);
  *      every combination is timed over the whole execute.  A plan of a batch
  *      that borrows another plan's spectra keeps its sizes.
- *   2. The tile schedule (sdf_plan_set_tuning) on those sizes: the passes
- *      each knob affects are timed.
+ *   2. The tile schedule (sdf_plan_set_tuning) and the epilogue's loads
+ *      (sdf_plan_set_epilogue_loads) on those sizes: the passes each knob
+ *      affects are timed.
  * Each candidate runs `reps` executes after one warm-up, timed with CUDA
  * events.  The choice is kept in a cache keyed by the GPU's name and
  * architecture, D, dims, precision, outputs and kernel set: a later call on

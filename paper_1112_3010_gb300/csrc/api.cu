@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "green.cuh"
 #include "sdf_internal.cuh"
 
@@ -78,8 +80,32 @@ double theta_coef(const sdf_plan_impl *p, int prec) {
     return prec == SDF_FP64 ? p->noise_c64 * ldexp(1.0, -53) * base : p->noise_c32 * ldexp(1.0, -24) * base;
 }
 
+// Multiprocessors of the current device (grid sizes of the grid-stride
+// kernels), looked up once per device.
+int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+ScopedRange::ScopedRange(const char *name) { nvtxRangePushA(name); }
+ScopedRange::~ScopedRange() { nvtxRangePop(); }
+
 void prof_begin(sdf_plan_impl *p, const char *name, cudaStream_t st) {
     ++p->nlaunch;
+    nvtxRangePushA(name);  // one NVTX range per kernel launch (closed by prof_end)
     if (!p->prof_on) return;
     ProfRec r;
     r.name = name;
@@ -96,6 +122,7 @@ void prof_begin(sdf_plan_impl *p, const char *name, cudaStream_t st) {
 }
 
 void prof_end(sdf_plan_impl *p, cudaStream_t st) {
+    nvtxRangePop();
     if (!p->prof_on || p->prof_recs.empty()) return;
     ProfRec &r = p->prof_recs.back();
     if (r.b) cudaEventRecord(r.b, st);
@@ -601,6 +628,7 @@ static sdf_status check_execute_args(sdf_plan p, int64_t K, const double *points
 
 sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double *weights, void *S, void *dS,
                        void *d2S, int8_t *sign, uint8_t *flags) {
+    ScopedRange range_("sdf_execute");
     sdf_status s = check_execute_args(p, K, points, weights, dS, d2S, sign);
     if (s != SDF_OK) return s;
     CK(ensure_points(p, K));
@@ -630,6 +658,7 @@ sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double
 sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const double *points, const double *weights,
                              void *const *S, void *const *dS, void *const *d2S, int8_t *const *sign,
                              uint8_t *const *flags) {
+    ScopedRange range_("sdf_execute_multi");
     if (n < 1 || !plans || !plans[0] || !points) return SDF_ERR_INVALID_ARG;
     sdf_plan p0 = plans[0];
     auto at = [](auto *const *arr, int i) { return arr ? arr[i] : nullptr; };
@@ -1028,6 +1057,12 @@ sdf_status sdf_plan_set_tuning(sdf_plan p, int lines_T, int lines_F, int fused_v
     return SDF_OK;
 }
 
+sdf_status sdf_plan_set_epilogue_loads(sdf_plan p, int mode) {
+    if (!p || (mode != 0 && mode != 1)) return SDF_ERR_INVALID_ARG;
+    p->tune_EV = mode;
+    return SDF_OK;
+}
+
 sdf_status sdf_plan_set_full_range(sdf_plan p, int enable) {
     if (!p) return SDF_ERR_INVALID_ARG;
     if (p->prec != SDF_FP32) {
@@ -1136,7 +1171,7 @@ static sdf_status time_kernels(sdf_plan p, int64_t K, const double *points, cons
 }
 
 // ---- the autotuner's cache: one line per tuned problem,
-// "<key>\t<M0> <M1> <M2> <lines_T> <lines_F> <fused_variant>", the last line
+// "<key>\t<M0> <M1> <M2> <lines_T> <lines_F> <fused_variant> <epilogue_loads>", the last line
 // of a key wins.  Path: $SDF_AUTOTUNE_CACHE (empty: no cache), else
 // $XDG_CACHE_HOME/sdf_gb300/autotune.tsv, else $HOME/.cache/sdf_gb300/autotune.tsv.
 static std::mutex g_tune_mutex;
@@ -1176,7 +1211,7 @@ static std::string tune_key(const sdf_plan_impl *p) {
 
 struct TuneRec {
     int64_t M[3];
-    int RT, RF, FV;
+    int RT, RF, FV, EV;
 };
 
 static bool tune_lookup(const std::string &key, TuneRec *out) {
@@ -1193,14 +1228,15 @@ static bool tune_lookup(const std::string &key, TuneRec *out) {
         *tab = 0;
         if (key != line) continue;
         long long m0, m1, m2;
-        int rt, rf, fv;
-        if (sscanf(tab + 1, "%lld %lld %lld %d %d %d", &m0, &m1, &m2, &rt, &rf, &fv) == 6) {
+        int rt, rf, fv, ev = 0;
+        if (sscanf(tab + 1, "%lld %lld %lld %d %d %d %d", &m0, &m1, &m2, &rt, &rf, &fv, &ev) >= 6) {
             out->M[0] = m0;
             out->M[1] = m1;
             out->M[2] = m2;
             out->RT = rt;
             out->RF = rf;
             out->FV = fv;
+            out->EV = ev;
             found = true;
         }
     }
@@ -1217,8 +1253,8 @@ static void tune_store(const std::string &key, const TuneRec &r) {
         if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
     FILE *f = fopen(path.c_str(), "a");
     if (!f) return;
-    fprintf(f, "%s\t%lld %lld %lld %d %d %d\n", key.c_str(), (long long)r.M[0], (long long)r.M[1], (long long)r.M[2],
-            r.RT, r.RF, r.FV);
+    fprintf(f, "%s\t%lld %lld %lld %d %d %d %d\n", key.c_str(), (long long)r.M[0], (long long)r.M[1],
+            (long long)r.M[2], r.RT, r.RF, r.FV, r.EV);
     fclose(f);
 }
 
@@ -1246,13 +1282,14 @@ sdf_status sdf_plan_autotune(sdf_plan p, int64_t K, const double *points, const 
         p->tune_RT = rec.RT;
         p->tune_RF = rec.RF;
         p->tune_FV = rec.FV;
+        p->tune_EV = rec.EV;
         report();
         return SDF_OK;
     }
     // 1. padded sizes: per axis the power of two, or 3 * 2^k where that is
     // smaller; every combination timed over the whole execute (default tile
     // schedule).  A plan of a batch that borrows its spectra keeps its sizes.
-    p->tune_RT = p->tune_RF = p->tune_FV = 0;
+    p->tune_RT = p->tune_RF = p->tune_FV = p->tune_EV = 0;
     if (!p->shares_spectra) {
         std::vector<std::vector<int64_t>> opts(p->D);
         size_t ncomb = 1;
@@ -1291,18 +1328,23 @@ sdf_status sdf_plan_autotune(sdf_plan p, int64_t K, const double *points, const 
     const char *tnames[] = {"xpass", "fwd_y", "inv_y", "epilogue"};
     const char *fnames[] = {"fused"};
     double best = 1e300;
-    int bestT = 0, bestF = 0, bestV = 0;
-    for (int RT : {0, 1, 2, 4, 8, 16}) {
-        p->tune_RT = RT;
-        double ms;
-        sdf_status s = time_kernels(p, K, points, weights, reps, tnames, 4, &ms);
-        if (s != SDF_OK) return s;
-        if (ms < best) {
-            best = ms;
-            bestT = RT;
+    int bestT = 0, bestF = 0, bestV = 0, bestE = 0;
+    for (int EV : {0, 1}) {
+        for (int RT : {0, 1, 2, 4, 8, 16}) {
+            p->tune_RT = RT;
+            p->tune_EV = EV;
+            double ms;
+            sdf_status s = time_kernels(p, K, points, weights, reps, tnames, 4, &ms);
+            if (s != SDF_OK) return s;
+            if (ms < best) {
+                best = ms;
+                bestT = RT;
+                bestE = EV;
+            }
         }
     }
     p->tune_RT = bestT;
+    p->tune_EV = bestE;
     best = 1e300;
     for (int RF : {0, 1, 2, 4}) {
         for (int FV : {1, 2, 3}) {
@@ -1324,6 +1366,7 @@ sdf_status sdf_plan_autotune(sdf_plan p, int64_t K, const double *points, const 
     rec.RT = bestT;
     rec.RF = bestF;
     rec.FV = bestV;
+    rec.EV = bestE;
     tune_store(key, rec);
     report();
     return SDF_OK;

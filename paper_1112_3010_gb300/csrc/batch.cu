@@ -234,6 +234,7 @@ sdf_status sdf_batch_autotune(sdf_batch b, const int64_t *K, const double *const
         pi->tune_RT = o->tune_RT;
         pi->tune_RF = o->tune_RF;
         pi->tune_FV = o->tune_FV;
+        pi->tune_EV = o->tune_EV;
     }
     // the captured graph is stale now: the next sdf_batch_execute captures anew
     if (b->exec) {

@@ -77,7 +77,7 @@ extern "C" sdf_status sdf_curvature(sdf_plan p, const void *dS, const void *d2S,
         return SDF_ERR_UNSUPPORTED;
     }
     const int64_t n = p->nnodes;
-    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     prof_begin(p, "curvature", p->stream);
     if (p->prec == SDF_FP64) {
         if (p->D == 2)

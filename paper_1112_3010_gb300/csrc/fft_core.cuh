@@ -75,41 +75,35 @@ inline int line_code(int64_t L) {
 }
 
 // Host: the twiddle table of a line with code lc, in the layout above (h
-// holds L entries, the unused tail stays zero).  Lines of 3 * 2^k points:
-// after the radix-3 stage (span 1, no twiddles) the radix-16 stages have
-// spans Ns = 3 * 16^s and keep w_{16 Ns}^{r k} at r*Ns + k - 3; a final
-// radix-P stage (span Ns = L/P) keeps w_L^{r j} at r*Ns + j - 3.
+// holds L entries, the unused tail stays zero).  Lines of L = 3Q points (Q =
+// 2^k): the radix-16 and radix-P stages of Q come first and keep the table
+// of a Q-point line (entries below Q - 16); the last stage, radix 3 with span
+// Q, keeps w_L^{r j} (r = 1, 2; j < Q) at Q - 16 + (r - 1) Q + j.
 template <typename V> inline void fill_twiddle_table(int lc, V *h) {
     using T = decltype(V::x);
     const int64_t L = line_len(lc);
     for (int64_t e = 0; e < L; ++e) h[e].x = h[e].y = T(0);
-    auto put = [&](int64_t e, int64_t i) {  // w_L^i
-        const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)i / (long double)L;
+    auto put_n = [&](int64_t e, int64_t i, int64_t n) {  // w_n^i
+        const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)i / (long double)n;
         h[e].x = (T)cosl(ang);
         h[e].y = (T)sinl(ang);
     };
-    if (line_r3(lc)) {
-        int64_t Ns = 3;
-        for (; 16 * Ns <= L; Ns *= 16)
-            for (int64_t r = 1; r < 16; ++r)
-                for (int64_t k = 0; k < Ns; ++k) put(r * Ns + k - 3, r * k * (L / (16 * Ns)));
-        if (Ns < L)
-            for (int64_t r = 1; r < L / Ns; ++r)
-                for (int64_t j = 0; j < Ns; ++j) put(r * Ns + j - 3, r * j);
-        return;
-    }
-    const int logL = lc;
-    const int nst = logL >> 2, rem = logL & 3;
+    const int logQ = lc & 0xff;
+    const int64_t Q = (int64_t)1 << logQ;
+    const int nst = logQ >> 2, rem = logQ & 3;
     for (int s = 1; s < nst; ++s) {
         const int64_t Ns = (int64_t)1 << (4 * s);
         for (int64_t r = 1; r < 16; ++r)
-            for (int64_t k = 0; k < Ns; ++k) put(r * Ns + k - 16, r * k * (L / (16 * Ns)));
+            for (int64_t k = 0; k < Ns; ++k) put_n(r * Ns + k - 16, r * k * (Q / (16 * Ns)), Q);
     }
     if (rem) {
         const int64_t Ns = (int64_t)1 << (4 * nst), P = (int64_t)1 << rem;
         for (int64_t r = 1; r < P; ++r)
-            for (int64_t j = 0; j < Ns; ++j) put(r * Ns + j - 16, r * j);
+            for (int64_t j = 0; j < Ns; ++j) put_n(r * Ns + j - 16, r * j, Q);
     }
+    if (line_r3(lc))
+        for (int64_t r = 1; r < 3; ++r)
+            for (int64_t j = 0; j < Q; ++j) put_n(Q - 16 + (r - 1) * Q + j, r * j, L);
 }
 
 // Shared-memory stride between the R lines of a CTA.  Threads of a warp
@@ -357,69 +351,105 @@ __device__ __forceinline__ bool fft_stage16(V (&v)[16], V *sm, int t, int logL, 
     return true;
 }
 
-// L = 3 * 2^lg point line (run-time length).  A radix-3 Stockham stage
-// (span 1) goes through shared memory: the Q = L/3 butterflies (x[j],
-// x[j + Q], x[j + 2Q]) -> (y[3j], y[3j + 1], y[3j + 2]) are spread over the
-// line's TPL = L/16 threads (16/3 per thread, so up to 6); then radix-16
-// stages of span Ns = 3 * 16^s and a final radix-2/4/8 stage, as for powers
-// of two but with the twiddle offset 3 (fill_twiddle_table).
-// LG > 0 fixes lg at compile time (the stage loop unrolls, spans and
-// addresses become constants).
+// L = 3Q point line, Q = 2^lg.  The radix-16 stages of Q (spans 1, 16, ...)
+// and, when lg is not a multiple of 4, a radix-P stage (P = 2, 4, 8) run as
+// for a Q-point line -- the Stockham stage formula holds for any L the radix
+// divides -- but the last of them stores its outputs to shared memory
+// instead of the registers; the radix-3 stage (span Q, twiddles w_L^{r j})
+// then works in place there, one butterfly (y[j], y[j + Q], y[j + 2Q]) at a
+// time (Q butterflies over L/16 threads: up to 6 each), and every thread
+// loads its 16 outputs X[t + m L/16].  LG > 0 fixes lg at compile time.
 template <bool INV, int LG = 0, typename V>
 __device__ __forceinline__ void fft_line_r3(V (&v)[16], V *sm, int t, int lg, const V *__restrict__ tw) {
     if constexpr (LG > 0) lg = LG;
     const int L = 3 << lg, TPL = L >> 4, Q = 1 << lg;
-    __syncthreads();
+    const int nst = lg >> 2, rem = lg & 3;
+    auto load_canon = [&]() {
+        __syncthreads();
+        if (TPL % 16 == 0) {
+            const V *s0 = sm + pad16(t);
+            const int st = TPL + (TPL >> 4);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) sm[pad16(t + m * TPL)] = v[m];
-    __syncthreads();
-    V a[6][3];
+            for (int m = 0; m < 16; ++m) v[m] = s0[m * st];
+        } else {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        const int j = t + i * TPL;
-        if (j < Q) {
-#pragma unroll
-            for (int r = 0; r < 3; ++r) a[i][r] = sm[pad16(j + r * Q)];
+            for (int m = 0; m < 16; ++m) v[m] = sm[pad16(t + m * TPL)];
         }
-    }
-    __syncthreads();
+    };
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        const int j = t + i * TPL;
-        if (j < Q) {
-            dft3<INV>(a[i][0], a[i][1], a[i][2]);
+    for (int s = 0; s < 3; ++s) {
+        if (s >= nst) break;
+        const int Ns = 1 << (4 * s);
+        const int k = t & (Ns - 1);
+        if (s > 0) {
+            const V *ts = tw + (k - 16);  // w_{16 Ns}^{r k} at ts[r * Ns]
 #pragma unroll
-            for (int q = 0; q < 3; ++q) sm[pad16(3 * j + q)] = a[i][q];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = sm[pad16(t + m * TPL)];
-    int Ns = 3;
-#pragma unroll
-    for (int st = 0; st < 3 && 16 * Ns <= L; ++st, Ns *= 16) {
-        const int k = t % Ns;
-        const V *ts = tw + (k - 3);  // w_{16 Ns}^{r k} at ts[r * Ns]
-#pragma unroll
-        for (int r = 1; r < 16; ++r) {
-            V w = ldtw(ts, r * Ns);
-            v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+            for (int r = 1; r < 16; ++r) {
+                V w = ldtw(ts, r * Ns);
+                v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+            }
         }
         dft16<INV>(v);
-        if (16 * Ns == L) return;  // v[q] = X[t + q TPL]
         __syncthreads();
-        const int base = (t - k) * 16 + k;
+        const int base = ((t - k) << 4) + k;
 #pragma unroll
         for (int q = 0; q < 16; ++q) sm[pad16(base + q * Ns)] = v[q];
+        if (s + 1 < nst || rem) load_canon();
+    }
+    if (rem) {
+        // radix-P stage, span Ns = 16^nst (not the last): butterflies j = t + b TPL
+        const int P = 1 << rem, B = 16 / P, Ns = 1 << (4 * nst);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            if (b >= B) break;
+            const int j = t + b * TPL, k = j & (Ns - 1);
+#pragma unroll
+            for (int r = 1; r < 8; ++r) {
+                if (r >= P) break;
+                V w = ldtw(tw, r * Ns + k - 16);  // w_{P Ns}^{r k}
+                v[b + r * B] = INV ? cmulc(v[b + r * B], w) : cmul(v[b + r * B], w);
+            }
+        }
+        if (P == 2) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) dft2<INV>(v[b], v[b + 8]);
+        } else if (P == 4) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) dft4<INV>(v[b], v[b + 4], v[b + 8], v[b + 12]);
+        } else {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) dft8s<INV, 2>(&v[b]);
+        }
         __syncthreads();
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = sm[pad16(t + m * TPL)];
+        for (int b = 0; b < 16; ++b) {
+            if (b >= B) break;
+            const int j = t + b * TPL, k = j & (Ns - 1);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q >= P) break;
+                sm[pad16((j - k) * P + k + q * Ns)] = v[b + q * B];
+            }
+        }
     }
-    // final stage (twiddles at r*Ns + j - 3: final_stage reads r*Ns + j - 16)
-    const int P = L / Ns;
-    if (P == 2) final_stage<2, INV>(v, t, TPL, Ns, tw + 13);
-    else if (P == 4) final_stage<4, INV>(v, t, TPL, Ns, tw + 13);
-    else final_stage<8, INV>(v, t, TPL, Ns, tw + 13);
+    __syncthreads();
+    // radix 3 in place: X[j + q Q] = sum_r w3^{rq} w_L^{rj} y[j + r Q]
+    const V *t1 = tw + (Q - 16), *t2 = tw + (2 * Q - 16);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const int j = t + i * TPL;
+        if (j < Q) {
+            V a0 = sm[pad16(j)], a1 = sm[pad16(j + Q)], a2 = sm[pad16(j + 2 * Q)];
+            const V w1 = ldtw(t1, j), w2 = ldtw(t2, j);
+            a1 = INV ? cmulc(a1, w1) : cmul(a1, w1);
+            a2 = INV ? cmulc(a2, w2) : cmul(a2, w2);
+            dft3<INV>(a0, a1, a2);
+            sm[pad16(j)] = a0;
+            sm[pad16(j + Q)] = a1;
+            sm[pad16(j + 2 * Q)] = a2;
+        }
+    }
+    load_canon();
 }
 
 // L-point FFT (forward: exp(-2 pi i nk/L); inverse: exp(+2 pi i nk/L), not

@@ -559,11 +559,52 @@ struct EpiParams {
     int fixup;  // FP32 plan: nodes below theta32 go to the fix-up
     double hs_inv;  // 1 / scale of the stored Hessian kernels
     float tau_f, itau_f, hs_inv_f;  // tau, 1/tau, hs_inv in float (float kernels stay off the FP64 pipe)
+    unsigned stage_off;  // TMA variant: staging buffer at or after this byte offset (1 KB of slack)
 };
 
-template <typename T, int D, int MT, int LOGL = 0>
+// ---------------------------------------------------------------- TMA staging (epilogue)
+// One thread arms an mbarrier with the bytes it expects and issues 3D tiled
+// tensor copies (cp.async.bulk.tensor) of a group's lines into shared memory;
+// every thread waits on the barrier's phase.  Waits are bounded: on expiry
+// the caller records SDF_ERR_TIMEOUT and stops.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// true once phase `parity` of the barrier has completed; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, int x, int y, int z, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+constexpr unsigned kTmaWaitLimit = 1u << 22;  // polls of a barrier before a wait counts as expired
+constexpr int kTmaBoxRows = 256;               // rows (transform elements) per tensor copy
+
+// TMA: the lines of a group reach shared memory by tensor copies (map
+// `tmap`, box 2R floats x kTmaBoxRows rows x 1 group) into a staging buffer
+// at P.stage_off, the next group's copy issued as soon as every thread has
+// read the current one; otherwise each thread loads its elements itself.
+template <typename T, int D, int MT, int LOGL = 0, bool TMA = false>
 __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, int logL, int R, int64_t n_lines,
-                                                   EpiParams P, const cx<T> *__restrict__ tw) {
+                                                   EpiParams P, const cx<T> *__restrict__ tw,
+                                                   const __grid_constant__ CUtensorMap tmap) {
     using V = cx<T>;
     if constexpr (LOGL > 0) logL = LOGL;  // line length fixed at compile time
     extern __shared__ unsigned char smraw[];
@@ -635,13 +676,47 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
         }
     }
 
+    // TMA staging: the barrier, the buffer, and the first group's copies
+    __shared__ __align__(8) unsigned long long s_bar;
+    // the buffer starts at the first 1024-byte boundary at or after stage_off
+    const unsigned sbase = smem_u32(smraw);
+    V *stage = reinterpret_cast<V *>(smraw + (((sbase + P.stage_off + 1023u) & ~1023u) - sbase));
+    const unsigned bar = smem_u32(&s_bar);
+    const unsigned stage_bytes = (unsigned)(R * L * sizeof(V));
+    auto issue = [&](int g) {  // one thread: copy group g's lines of this CTA
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, stage_bytes);
+        for (int u0 = 0; u0 < L; u0 += kTmaBoxRows)
+            tma_load_3d(smem_u32(stage + u0 * R), &tmap, 2 * (int)((int64_t)blockIdx.x * R), u0, g, bar);
+    };
+    bool expired = false;
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            issue(P.order[0]);
+        }
+        __syncthreads();
+    }
+
     for (int gi = 0; gi < P.ngroup; ++gi) {
         const int g = P.order[gi];
         V v[16];
-        const V *src = in + g * P.in_fs + line;
+        if constexpr (TMA) {
+            const bool ok = mbar_wait(bar, (unsigned)(gi & 1), kTmaWaitLimit);
+            if (__syncthreads_or(!ok)) {  // every thread takes the same way out
+                expired = true;
+                break;
+            }
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
-        __syncthreads();
+            for (int m = 0; m < 16; ++m) v[m] = stage[(t + m * TPL) * R + lr];
+            __syncthreads();  // the buffer is free again
+            if (threadIdx.x == 0 && gi + 1 < P.ngroup) issue(P.order[gi + 1]);
+        } else {
+            const V *src = in + g * P.in_fs + line;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) v[m] = valid ? src[(int64_t)(t + m * TPL) * n_lines] : mk<V>(T(0), T(0));
+            __syncthreads();
+        }
         fft_line<true, LOGL>(v, my, t, logL, tws);
         if (!valid) continue;
 #pragma unroll
@@ -709,6 +784,15 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
             }
         }
     }
+    if constexpr (TMA) {
+        if (expired) {
+            // record the expiry; let the copy in flight land (bounded) before the CTA leaves
+            if (threadIdx.x == 0) atomicCAS(&P.dsc_w->status, 0, (int)SDF_ERR_TIMEOUT);
+            mbar_wait(bar, 0u, kTmaWaitLimit);
+            mbar_wait(bar, 1u, kTmaWaitLimit);
+            return;
+        }
+    }
     // capped nodes (the FP32 fix-up takes back the ones it recomputes)
     ncap = __reduce_add_sync(__activemask(), ncap);  // the last warp of a CTA may be partial
     if ((threadIdx.x & 31) == 0 && ncap) atomicAdd(&P.dsc_w->n_capped, (unsigned long long)ncap);
@@ -771,6 +855,21 @@ static inline int xpass_max_threads(int logL) {
         } else {                                                    \
             CALL(0);                                                \
         }                                                           \
+    } while (0)
+
+// CALL(LG) over the compiled float line lengths only (the TMA epilogue).
+#define SDF_BY_LOGL_COMPILED(logL, CALL)                      \
+    do {                                                      \
+        switch (logL) {                                       \
+            case 8: CALL(8); break;                           \
+            case 9: CALL(9); break;                           \
+            case 10: CALL(10); break;                         \
+            case 11: CALL(11); break;                         \
+            case 12: CALL(12); break;                         \
+            case 8 | kLineR3: CALL(8 | kLineR3); break;       \
+            case 9 | kLineR3: CALL(9 | kLineR3); break;       \
+            default: CALL(10 | kLineR3); break;               \
+        }                                                     \
     } while (0)
 
 // adj: the adjoint programme (transform of a = w/phi) instead of the forward one

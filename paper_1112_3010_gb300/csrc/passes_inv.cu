@@ -1,9 +1,56 @@
 // passes_inv.cu -- launchers of the inverse passes after the fused pass:
 // the 3D inverse y-pass, the epilogue (Table 1 step 6 of the paper: S, its
 // derivatives and the sign) and the adjoint's last pass.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "passes.cuh"
 
 namespace sdf {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when unavailable.
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// The epilogue input as a 3D float tensor: x = 2 n_lines floats (re, im of
+// each line, lines contiguous), y = M0 elements (stride n_lines complex), z =
+// the groups (stride in_fs); box 2R floats x kTmaBoxRows x 1.  Cached in the
+// plan per (buffer, n_lines, M0, groups, R).  False when it cannot be made.
+static bool epilogue_tmap(sdf_plan_impl *p, const float2 *in, int64_t n_lines, int64_t M0, int64_t in_fs, int ngroup,
+                          int R) {
+    const int64_t key[5] = {(int64_t)(uintptr_t)in, n_lines, M0, ngroup, R};
+    bool same = true;
+    for (int i = 0; i < 5; ++i) same = same && key[i] == p->epi_tmap_key[i];
+    if (same) return true;
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * n_lines), (cuuint64_t)M0, (cuuint64_t)ngroup};
+    const cuuint64_t strides[2] = {(cuuint64_t)(n_lines * sizeof(float2)), (cuuint64_t)(in_fs * sizeof(float2))};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * R), (cuuint32_t)kTmaBoxRows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (fn(&p->epi_tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(in), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        for (int i = 0; i < 5; ++i) p->epi_tmap_key[i] = 0;
+        return false;
+    }
+    for (int i = 0; i < 5; ++i) p->epi_tmap_key[i] = key[i];
+    return true;
+}
 
 // Inverse passes after the fused pass; the result of the fused pass is in
 // bufB (2D) or bufA (3D).  For 3D the inverse y-pass goes bufA -> bufB.
@@ -94,21 +141,57 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
     const int logL = p->logM[0];
     const int R = tuned_R<T>(p, logL);
     LineCfg c = line_cfg(logL, R);
-    const size_t smem = line_smem(R, c.L, (int)sizeof(V));
+    size_t smem = line_smem(R, c.L, (int)sizeof(V));
     const int64_t grid = (n_lines + R - 1) / R;
     const V *tw0 = reinterpret_cast<const V *>(p->tw[0]);
-#define SDF_EPI(DD, LG)                                                                                       \
-    do {                                                                                                      \
-        if ((e = set_smem<T>((const void *)k_epilogue<T, DD, 512, LG>, smem)) != cudaSuccess) return e;      \
-        k_epilogue<T, DD, 512, LG><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, tw0); \
+    // TMA staging of the transposed input: float lines of a compiled length
+    // that is a multiple of the box rows, at least two lines per CTA (16-byte
+    // rows), an even line count (16-byte strides), the staging buffer beside
+    // the line buffers within the shared memory of a CTA
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    bool tma = false;
+    if constexpr (sizeof(T) == 4) {
+        const bool compiled = (logL >= 8 && logL <= 12) || (logL >= (8 | kLineR3) && logL <= (10 | kLineR3));
+        const size_t off = smem;
+        const size_t tot = off + 1024 + (size_t)R * c.L * sizeof(V);
+        if (p->tune_EV == 0 && compiled && R >= 2 && c.L % kTmaBoxRows == 0 && n_lines % 2 == 0 &&
+            tot <= 227 * 1024 &&
+            epilogue_tmap(p, reinterpret_cast<const float2 *>(lin), n_lines, M0, E.in_fs, p->ngroup, R)) {
+            tma = true;
+            E.stage_off = (unsigned)off;
+            smem = tot;
+            tmap = p->epi_tmap;
+        }
+    }
+#define SDF_EPI(DD, LG, TM)                                                                                     \
+    do {                                                                                                        \
+        if ((e = set_smem<T>((const void *)k_epilogue<T, DD, 512, LG, TM>, smem)) != cudaSuccess) return e;    \
+        k_epilogue<T, DD, 512, LG, TM><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, \
+                                                                                       tw0, tmap);             \
     } while (0)
     prof_begin(p, "epilogue", p->stream);
-#define SDF_EPI2(LG) SDF_EPI(2, LG)
-#define SDF_EPI3(LG) SDF_EPI(3, LG)
-    if (D == 2) SDF_BY_LOGL(T, logL, SDF_EPI2);
-    else SDF_BY_LOGL(T, logL, SDF_EPI3);
+#define SDF_EPI2(LG) SDF_EPI(2, LG, false)
+#define SDF_EPI3(LG) SDF_EPI(3, LG, false)
+#define SDF_EPI2T(LG) SDF_EPI(2, LG, true)
+#define SDF_EPI3T(LG) SDF_EPI(3, LG, true)
+    if constexpr (sizeof(T) == 4) {
+        if (tma) {
+            if (D == 2) SDF_BY_LOGL_COMPILED(logL, SDF_EPI2T);
+            else SDF_BY_LOGL_COMPILED(logL, SDF_EPI3T);
+        } else if (D == 2) {
+            SDF_BY_LOGL(T, logL, SDF_EPI2);
+        } else {
+            SDF_BY_LOGL(T, logL, SDF_EPI3);
+        }
+    } else {
+        if (D == 2) SDF_BY_LOGL(T, logL, SDF_EPI2);
+        else SDF_BY_LOGL(T, logL, SDF_EPI3);
+    }
 #undef SDF_EPI2
 #undef SDF_EPI3
+#undef SDF_EPI2T
+#undef SDF_EPI3T
 #undef SDF_EPI
     prof_end(p, p->stream);
     (void)N2;

@@ -538,7 +538,7 @@ cudaError_t launch_cheb(sdf_plan_impl *p, cudaStream_t on) {
 
 cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags) {
     prof_begin(p, "source_flags", p->stream);
-    k_source_flags<<<152 * 8, 256, 0, p->stream>>>(p->nbins, p->bin_start, p->bin_nuniq, p->ucell, (int)p->N[0],
+    k_source_flags<<<(unsigned)sm_count() * 8, 256, 0, p->stream>>>(p->nbins, p->bin_start, p->bin_nuniq, p->ucell, (int)p->N[0],
                                                   (int)p->N[1], (int)p->nb[0], (int)p->nb[1], flags);
     prof_end(p, p->stream);
     return cudaGetLastError();

@@ -1,6 +1,7 @@
 // sdf_internal.cuh -- plan layout and kernel launchers shared by the .cu files
 // of the library.  Nothing here is part of the C ABI (include/sdf.h).
 #pragma once
+#include <cuda.h>  // CUtensorMap (the type only: tensor maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -136,7 +137,12 @@ struct sdf_plan_impl {
     // tile schedule (0: built-in rule): lines per CTA of the transposed passes
     // and of the fused pass, and the fused pass's register variant
     int tune_RT = 0, tune_RF = 0, tune_FV = 0;
+    int tune_EV = 0;  // epilogue loads: 0 = TMA staging where it applies, 1 = per-thread loads
     bool full_range = false;  // fix-up without the theta_64 cap (sdf_plan_set_full_range)
+    // the epilogue's TMA tensor map over its input (encoded for the buffer,
+    // sizes and lines per CTA in epi_tmap_key; rebuilt when they change)
+    CUtensorMap epi_tmap;
+    int64_t epi_tmap_key[5] = {0, 0, 0, 0, 0};
     int kernel_set = SDF_KERNEL_EXP;  // sdf_plan_set_kernel
     // profiling
     bool prof_on = false;
@@ -145,7 +151,18 @@ struct sdf_plan_impl {
     std::vector<cudaEvent_t> prof_pool;
 };
 
-// Bracket one kernel launch: prof_begin before, prof_end after.
+// An NVTX range for the lifetime of the object (public calls); kernel
+// launches get theirs from prof_begin / prof_end.
+struct ScopedRange {
+    explicit ScopedRange(const char *name);
+    ~ScopedRange();
+};
+
+// Multiprocessors of the current device.
+int sm_count();
+
+// Bracket one kernel launch: prof_begin before, prof_end after (also an NVTX
+// range named after the kernel).
 void prof_begin(sdf_plan_impl *p, const char *name, cudaStream_t st);
 void prof_end(sdf_plan_impl *p, cudaStream_t st);
 
