@@ -611,8 +611,6 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     V *sm = reinterpret_cast<V *>(smraw);
     const int L = line_len(logL), TPL = L >> 4, PL = pad16(L);
     const int tid = threadIdx.x, lr = tid % R, t = tid / R;
-    const int64_t line = (int64_t)blockIdx.x * R + lr;
-    const bool valid = line < n_lines;
     V *my = sm + lr * line_stride(PL, R, (int)sizeof(V));
     const V *tws = stage_twiddles(sm + R * line_stride(PL, R, (int)sizeof(V)), tw, L);
     const int N0 = P.N0;
@@ -645,25 +643,55 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
         itau = 1.0 / P.tau;
         hs_inv = P.hs_inv;
     }
+    constexpr int NH = D * (D + 1) / 2;
+    T *Sout = reinterpret_cast<T *>(P.S);
+    T *dS = reinterpret_cast<T *>(P.dS);
+    T *d2S = reinterpret_cast<T *>(P.d2S);
+    unsigned ncap = 0;      // nodes of this thread flagged CAPPED
+
+    // TMA staging: the barrier, the buffer, the copies.  The TMA kernel is
+    // persistent (CTAs stride over the blocks of R lines), and the copy of the
+    // next block's first group is issued while the current block's last
+    // group is transformed.
+    __shared__ __align__(8) unsigned long long s_bar;
+    // the buffer starts at the first 1024-byte boundary at or after stage_off
+    const unsigned sbase = smem_u32(smraw);
+    V *stage = reinterpret_cast<V *>(smraw + (((sbase + P.stage_off + 1023u) & ~1023u) - sbase));
+    const unsigned bar = smem_u32(&s_bar);
+    const unsigned stage_bytes = (unsigned)(R * L * sizeof(V));
+    const int64_t nblk = (n_lines + R - 1) / R;
+    auto issue = [&](int64_t blk, int g) {  // one thread: copy group g of block blk
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, stage_bytes);
+        for (int u0 = 0; u0 < L; u0 += kTmaBoxRows)
+            tma_load_3d(smem_u32(stage + u0 * R), &tmap, 2 * (int)(blk * R), u0, g, bar);
+    };
+    bool expired = false;
+    unsigned nwait = 0;  // copies waited for so far: the barrier phase
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            if (blockIdx.x < nblk) issue(blockIdx.x, P.order[0]);
+        }
+        __syncthreads();
+    }
+
+    for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t line = blk * R + lr;
+    const bool valid = line < n_lines;
     // bin row of this line, for the fix-up's tile flags
     const int64_t brow = valid ? (int64_t)P.nb0 * (((int)(line % P.N1) >> 3) + (int64_t)P.nb1 * ((int)(line / P.N1) >> 3))
                                : 0;
-    constexpr int NH = D * (D + 1) / 2;
-
     T phi[8];  // 1/phi per node, once the phi group is done
     T gs[D][8];
     unsigned sgn = 0xffu;   // bit m: +1 (no sign requested: all +1)
     unsigned trusted = 0;
-    unsigned ncap = 0;      // nodes of this thread flagged CAPPED
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         phi[m] = T(1);
 #pragma unroll
         for (int a = 0; a < D; ++a) gs[a][m] = T(0);
     }
-    T *Sout = reinterpret_cast<T *>(P.S);
-    T *dS = reinterpret_cast<T *>(P.dS);
-    T *d2S = reinterpret_cast<T *>(P.d2S);
     if (P.sign_in && valid) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -676,41 +704,23 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
         }
     }
 
-    // TMA staging: the barrier, the buffer, and the first group's copies
-    __shared__ __align__(8) unsigned long long s_bar;
-    // the buffer starts at the first 1024-byte boundary at or after stage_off
-    const unsigned sbase = smem_u32(smraw);
-    V *stage = reinterpret_cast<V *>(smraw + (((sbase + P.stage_off + 1023u) & ~1023u) - sbase));
-    const unsigned bar = smem_u32(&s_bar);
-    const unsigned stage_bytes = (unsigned)(R * L * sizeof(V));
-    auto issue = [&](int g) {  // one thread: copy group g's lines of this CTA
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, stage_bytes);
-        for (int u0 = 0; u0 < L; u0 += kTmaBoxRows)
-            tma_load_3d(smem_u32(stage + u0 * R), &tmap, 2 * (int)((int64_t)blockIdx.x * R), u0, g, bar);
-    };
-    bool expired = false;
-    if constexpr (TMA) {
-        if (threadIdx.x == 0) {
-            mbar_init(bar, 1);
-            issue(P.order[0]);
-        }
-        __syncthreads();
-    }
-
     for (int gi = 0; gi < P.ngroup; ++gi) {
         const int g = P.order[gi];
         V v[16];
         if constexpr (TMA) {
-            const bool ok = mbar_wait(bar, (unsigned)(gi & 1), kTmaWaitLimit);
+            const bool ok = mbar_wait(bar, nwait & 1u, kTmaWaitLimit);
+            ++nwait;
             if (__syncthreads_or(!ok)) {  // every thread takes the same way out
                 expired = true;
                 break;
             }
 #pragma unroll
             for (int m = 0; m < 16; ++m) v[m] = stage[(t + m * TPL) * R + lr];
-            __syncthreads();  // the buffer is free again
-            if (threadIdx.x == 0 && gi + 1 < P.ngroup) issue(P.order[gi + 1]);
+            __syncthreads();  // the buffer is free again: the next copy
+            if (threadIdx.x == 0) {
+                if (gi + 1 < P.ngroup) issue(blk, P.order[gi + 1]);
+                else if (blk + gridDim.x < nblk) issue(blk + gridDim.x, P.order[0]);
+            }
         } else {
             const V *src = in + g * P.in_fs + line;
 #pragma unroll
@@ -784,6 +794,8 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
             }
         }
     }
+    if (expired) break;
+    }  // blocks of lines
     if constexpr (TMA) {
         if (expired) {
             // record the expiry; let the copy in flight land (bounded) before the CTA leaves

@@ -164,11 +164,20 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
             tmap = p->epi_tmap;
         }
     }
-#define SDF_EPI(DD, LG, TM)                                                                                     \
-    do {                                                                                                        \
-        if ((e = set_smem<T>((const void *)k_epilogue<T, DD, 512, LG, TM>, smem)) != cudaSuccess) return e;    \
-        k_epilogue<T, DD, 512, LG, TM><<<(unsigned)grid, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E, \
-                                                                                       tw0, tmap);             \
+    // the TMA kernel is persistent: as many CTAs as fit on the device at once
+#define SDF_EPI(DD, LG, TM)                                                                                      \
+    do {                                                                                                         \
+        const void *fn_ = (const void *)k_epilogue<T, DD, 512, LG, TM>;                                          \
+        if ((e = set_smem<T>(fn_, smem)) != cudaSuccess) return e;                                               \
+        int64_t g_ = grid;                                                                                       \
+        if (TM) {                                                                                                \
+            int per_sm = 0;                                                                                      \
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn_, R * c.TPL, smem)) != cudaSuccess) \
+                return e;                                                                                        \
+            g_ = std::min<int64_t>(grid, (int64_t)std::max(per_sm, 1) * sm_count());                             \
+        }                                                                                                        \
+        k_epilogue<T, DD, 512, LG, TM><<<(unsigned)g_, R * c.TPL, smem, p->stream>>>(lin, logL, R, n_lines, E,  \
+                                                                                     tw0, tmap);                \
     } while (0)
     prof_begin(p, "epilogue", p->stream);
 #define SDF_EPI2(LG) SDF_EPI(2, LG, false)
