@@ -579,6 +579,25 @@ sdf_status sdf_execute_noalloc(int D, const int64_t *dims, double h, double tau,
                                void *S, void *dS, void *d2S, int8_t *sign,
                                uint8_t *flags, void *stream);
 
+/*
+ * sdf_debug_hook -- test hooks for the failure paths (process-wide; the
+ * paper has no counterpart).  value >= 0, else SDF_ERR_INVALID_ARG; an
+ * unknown hook gives SDF_ERR_INVALID_ARG.
+ *   SDF_HOOK_FAIL_ALLOC      the value-th device allocation the library
+ *                            makes from now on (1 = the next) fails as if the
+ *                            device were out of memory: the call reports
+ *                            SDF_ERR_OOM and releases what it had allocated.
+ *                            0 disables.
+ *   SDF_HOOK_TMA_WAIT_POLLS  the epilogue's TMA waits give up after `value`
+ *                            non-blocking polls (0: the built-in bound), so
+ *                            an execute meets the expiry path on purpose: the
+ *                            copy in flight still lands (the kernel waits for
+ *                            it, bounded) and sdf_sync reports
+ *                            SDF_ERR_TIMEOUT; the plan stays usable.
+ */
+enum { SDF_HOOK_FAIL_ALLOC = 1, SDF_HOOK_TMA_WAIT_POLLS = 2 };
+sdf_status sdf_debug_hook(int hook, int64_t value);
+
 /* Free the plan and everything it owns (synchronises its stream). */
 void sdf_plan_destroy(sdf_plan plan);
 

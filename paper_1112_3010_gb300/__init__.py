@@ -36,7 +36,8 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature", "sdf_plan_set_full_range",
             "sdf_mesh_sources", "sdf_plan_set_kernel", "sdf_green_profile", "sdf_execute_multi",
             "sdf_execute_multi_host", "sdf_plan_set_padding", "sdf_batch_autotune",
-            "sdf_plan_set_epilogue_loads"]
+            "sdf_plan_set_epilogue_loads", "sdf_debug_hook"]
+SDF_HOOK_FAIL_ALLOC, SDF_HOOK_TMA_WAIT_POLLS = 1, 2
 
 
 class SDFError(RuntimeError):
@@ -132,6 +133,8 @@ def load_library(path: str | None = None):
         ip = ctypes.POINTER(ctypes.c_int)
         L.sdf_plan_autotune.argtypes = [vp, i64, vp, vp, ctypes.c_int, ip, ip, ip]
         L.sdf_plan_autotune.restype = ctypes.c_int
+        L.sdf_debug_hook.argtypes = [ctypes.c_int, i64]
+        L.sdf_debug_hook.restype = ctypes.c_int
         L.sdf_plan_set_epilogue_loads.argtypes = [vp, ctypes.c_int]
         L.sdf_plan_set_epilogue_loads.restype = ctypes.c_int
         L.sdf_plan_set_padding.argtypes = [vp, ctypes.POINTER(i64)]
@@ -324,6 +327,11 @@ def sdf_batch_execute(handle, K, points, weights, S, dS, d2S, sign, flags):
     _ck(_lib().sdf_batch_execute(handle, Ks, _ptr_array(points), _ptr_array(weights), _ptr_array(S),
                                  _ptr_array(dS), _ptr_array(d2S), _ptr_array(sign), _ptr_array(flags)),
         "sdf_batch_execute")
+
+
+def sdf_debug_hook(hook, value):
+    """Test hooks of the failure paths (SDF_HOOK_*)."""
+    _ck(_lib().sdf_debug_hook(int(hook), int(value)), "sdf_debug_hook")
 
 
 def sdf_plan_set_epilogue_loads(handle, mode):

@@ -134,8 +134,8 @@ static cudaError_t adjoint_setup(sdf_plan_impl *p) {
         p->adj_gch[1][1] = CH_NONE;
     }
     const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
-    if ((e = cudaMalloc(&p->adj_planes, esz * (D + 1) * p->nnodes)) != cudaSuccess) return e;
-    if ((e = cudaMalloc((void **)&p->adj_part, sizeof(double) * 2 * kAdjParts)) != cudaSuccess) return e;
+    if ((e = dev_alloc(&p->adj_planes, esz * (D + 1) * p->nnodes)) != cudaSuccess) return e;
+    if ((e = dev_alloc((void **)&p->adj_part, sizeof(double) * 2 * kAdjParts)) != cudaSuccess) return e;
     p->workspace_bytes += esz * (D + 1) * p->nnodes + sizeof(double) * 2 * kAdjParts;
     p->adj_ngroup = 2;
     return cudaSuccess;

@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <sys/stat.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <mutex>
@@ -79,6 +80,24 @@ double theta_coef(const sdf_plan_impl *p, int prec) {
     const double base = sqrt(log2(n)) / sqrt(n) * p->q_factor / kTrustEps;
     return prec == SDF_FP64 ? p->noise_c64 * ldexp(1.0, -53) * base : p->noise_c32 * ldexp(1.0, -24) * base;
 }
+
+// ---- test hooks (sdf_debug_hook): a device allocation that fails on
+// request, and the poll limit of the epilogue's TMA waits
+static std::atomic<long long> g_fail_alloc{0};   // > 0: the count-down to the allocation that fails
+static std::atomic<long long> g_tma_polls{0};    // > 0: non-blocking polls before a TMA wait expires
+
+cudaError_t dev_alloc(void **ptr, size_t bytes) {
+    long long c = g_fail_alloc.load();
+    while (c > 0 && !g_fail_alloc.compare_exchange_weak(c, c - 1)) {
+    }
+    if (c == 1) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;  // as the runtime reports an exhausted device
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+unsigned tma_wait_polls() { return (unsigned)g_tma_polls.load(); }
 
 // Multiprocessors of the current device (grid sizes of the grid-stride
 // kernels), looked up once per device.
@@ -354,7 +373,7 @@ void plan_buffer_sizes(sdf_plan_impl *p) {
 }  // namespace sdf
 
 static cudaError_t alloc(void **ptr, size_t bytes, size_t *acc) {
-    cudaError_t e = cudaMalloc(ptr, bytes);
+    cudaError_t e = dev_alloc(ptr, bytes);
     if (e == cudaSuccess && acc) *acc += bytes;
     return e;
 }
@@ -605,12 +624,12 @@ static cudaError_t ensure_points(sdf_plan_impl *p, int64_t K) {
     p->Kcap = 0;
     const int64_t cap = std::max<int64_t>(K, 1024);
     cudaError_t e;
-    if ((e = cudaMalloc(&p->pt_key, sizeof(int) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&p->pt_lc, sizeof(int) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&p->pt_entry, sizeof(long long) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&p->ucell, sizeof(int) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&p->ucount, sizeof(int) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&p->uw, sizeof(double) * 3 * cap)) != cudaSuccess) return e;
+    if ((e = dev_alloc((void **)&p->pt_key, sizeof(int) * cap)) != cudaSuccess) return e;
+    if ((e = dev_alloc((void **)&p->pt_lc, sizeof(int) * cap)) != cudaSuccess) return e;
+    if ((e = dev_alloc((void **)&p->pt_entry, sizeof(long long) * cap)) != cudaSuccess) return e;
+    if ((e = dev_alloc((void **)&p->ucell, sizeof(int) * cap)) != cudaSuccess) return e;
+    if ((e = dev_alloc((void **)&p->ucount, sizeof(int) * cap)) != cudaSuccess) return e;
+    if ((e = dev_alloc((void **)&p->uw, sizeof(double) * 3 * cap)) != cudaSuccess) return e;
     p->Kcap = cap;
     return cudaSuccess;
 }
@@ -825,7 +844,7 @@ sdf_status sdf_execute_host(sdf_plan p, int64_t K, const double *points, const d
         cudaFree(p->staging);
         p->staging = nullptr;
         p->staging_bytes = 0;
-        CK(cudaMalloc((void **)&p->staging, tot));
+        CK(dev_alloc((void **)&p->staging, tot));
         p->staging_bytes = tot;
     }
     char *base = reinterpret_cast<char *>(p->staging);
@@ -881,7 +900,7 @@ sdf_status sdf_execute_multi_host(int n, const sdf_plan *plans, int64_t K, const
             cudaFree(p->staging);
             p->staging = nullptr;
             p->staging_bytes = 0;
-            CK(cudaMalloc((void **)&p->staging, tot));
+            CK(dev_alloc((void **)&p->staging, tot));
             p->staging_bytes = tot;
         }
         char *base = reinterpret_cast<char *>(p->staging);
@@ -1055,6 +1074,15 @@ sdf_status sdf_plan_set_tuning(sdf_plan p, int lines_T, int lines_F, int fused_v
     p->tune_RF = lines_F > 0 ? lines_F : 0;
     p->tune_FV = (fused_variant >= 1 && fused_variant <= 3) ? fused_variant : 0;
     return SDF_OK;
+}
+
+sdf_status sdf_debug_hook(int hook, int64_t value) {
+    if (value < 0) return SDF_ERR_INVALID_ARG;
+    switch (hook) {
+        case SDF_HOOK_FAIL_ALLOC: g_fail_alloc.store(value); return SDF_OK;
+        case SDF_HOOK_TMA_WAIT_POLLS: g_tma_polls.store(value); return SDF_OK;
+        default: return SDF_ERR_INVALID_ARG;
+    }
 }
 
 sdf_status sdf_plan_set_epilogue_loads(sdf_plan p, int mode) {

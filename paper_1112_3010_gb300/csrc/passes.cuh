@@ -560,6 +560,7 @@ struct EpiParams {
     double hs_inv;  // 1 / scale of the stored Hessian kernels
     float tau_f, itau_f, hs_inv_f;  // tau, 1/tau, hs_inv in float (float kernels stay off the FP64 pipe)
     unsigned stage_off;  // TMA variant: staging buffer at or after this byte offset (1 KB of slack)
+    unsigned wait_polls; // TMA variant: 0, or the non-blocking polls after which a wait expires (test hook)
 };
 
 // ---------------------------------------------------------------- TMA staging (epilogue)
@@ -581,6 +582,20 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigne
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// as mbar_wait with non-blocking polls (mbarrier.test_wait): `limit` polls
+// cover a few nanoseconds each (the test hook of the expiry path)
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity, unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
             : "r"(bar), "r"(parity)
             : "memory");
@@ -708,7 +723,8 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
         const int g = P.order[gi];
         V v[16];
         if constexpr (TMA) {
-            const bool ok = mbar_wait(bar, nwait & 1u, kTmaWaitLimit);
+            const bool ok = P.wait_polls ? mbar_test(bar, nwait & 1u, P.wait_polls)
+                                         : mbar_wait(bar, nwait & 1u, kTmaWaitLimit);
             ++nwait;
             if (__syncthreads_or(!ok)) {  // every thread takes the same way out
                 expired = true;

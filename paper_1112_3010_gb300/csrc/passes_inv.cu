@@ -160,6 +160,7 @@ static cudaError_t inverse_epilogue_impl(sdf_plan_impl *p, bool with_weights, vo
             epilogue_tmap(p, reinterpret_cast<const float2 *>(lin), n_lines, M0, E.in_fs, p->ngroup, R)) {
             tma = true;
             E.stage_off = (unsigned)off;
+            E.wait_polls = tma_wait_polls();
             smem = tot;
             tmap = p->epi_tmap;
         }

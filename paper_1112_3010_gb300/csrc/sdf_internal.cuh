@@ -161,6 +161,11 @@ struct ScopedRange {
 // Multiprocessors of the current device.
 int sm_count();
 
+// cudaMalloc through the allocation-failure test hook (sdf_debug_hook); the
+// poll limit the hook sets for the epilogue's TMA waits (0: the default).
+cudaError_t dev_alloc(void **ptr, size_t bytes);
+unsigned tma_wait_polls();
+
 // Bracket one kernel launch: prof_begin before, prof_end after (also an NVTX
 // range named after the kernel).
 void prof_begin(sdf_plan_impl *p, const char *name, cudaStream_t st);

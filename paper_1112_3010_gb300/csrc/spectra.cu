@@ -262,19 +262,31 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
     for (int a = 0; a < D; ++a) total *= p->M[a];
     // FP64 twiddle tables for the plan-time transforms
     std::vector<double2 *> tw64(D, nullptr);
+    double2 *bufX = nullptr, *bufY = nullptr;
+    double *part = nullptr, *resid = nullptr;
+    auto release = [&]() {
+        cudaFree(bufX);
+        cudaFree(bufY);
+        cudaFree(part);
+        for (auto t : tw64) cudaFree(t);
+    };
     for (int a = 0; a < D; ++a) {
         const int64_t L = p->M[a];
         std::vector<double2> h(L);
         fill_twiddle_table(line_code(L), h.data());
-        if ((e = cudaMalloc(&tw64[a], sizeof(double2) * L)) != cudaSuccess) return e;
-        if ((e = cudaMemcpy(tw64[a], h.data(), sizeof(double2) * L, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = dev_alloc((void **)&tw64[a], sizeof(double2) * L)) != cudaSuccess ||
+            (e = cudaMemcpy(tw64[a], h.data(), sizeof(double2) * L, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            release();
+            return e;
+        }
     }
-    double2 *bufX = nullptr, *bufY = nullptr;
-    double *part = nullptr, *resid = nullptr;
     const int nblk = 1024;
-    if ((e = cudaMalloc(&bufX, sizeof(double2) * total)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&bufY, sizeof(double2) * total)) != cudaSuccess) { cudaFree(bufX); return e; }
-    if ((e = cudaMalloc(&part, sizeof(double) * (nblk + 1))) != cudaSuccess) return e;
+    if ((e = dev_alloc((void **)&bufX, sizeof(double2) * total)) != cudaSuccess ||
+        (e = dev_alloc((void **)&bufY, sizeof(double2) * total)) != cudaSuccess ||
+        (e = dev_alloc((void **)&part, sizeof(double) * (nblk + 1))) != cudaSuccess) {
+        release();
+        return e;
+    }
     resid = part + nblk;
     std::vector<double> hpart(nblk);
     double inv_n = 1.0 / (double)total;
@@ -316,7 +328,7 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
         if ((e = cudaMemsetAsync(resid, 0, sizeof(double), st)) != cudaSuccess) break;
         const int nodd = __builtin_popcount((unsigned)ks.parity);
         double scale = inv_n * ks.scale;
-        if ((e = cudaMalloc(&ks.c, esz * ctotal)) != cudaSuccess) break;
+        if ((e = dev_alloc(&ks.c, esz * ctotal)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(ks.c, 0, esz * ctotal, st)) != cudaSuccess) break;
         if (p->prec == SDF_FP64)
             k_compress<double><<<1024, 256, 0, st>>>(src, reinterpret_cast<double *>(ks.c), D, p->M[0], p->M[1],
@@ -331,10 +343,7 @@ cudaError_t build_spectra(sdf_plan_impl *p) {
         ks.l1 = l1;
         p->workspace_bytes += esz * ctotal;
     }
-    cudaFree(bufX);
-    cudaFree(bufY);
-    cudaFree(part);
-    for (auto t : tw64) cudaFree(t);
+    release();
     return e;
 }
 
