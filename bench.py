@@ -195,10 +195,11 @@ def algorithmic_bytes(plan_info, name, stats, n_field, n_group, n_kern):
 
 # FP32 FMA-pipe operations per node-point term of the fix-up's summing loop
 # (2D, S + grad S + Hessian in moment form): r^2, r, the exponent, E, E/r,
-# the Hessian factor (3), five running sums (sE, sA, 2 gradient), the three
-# Hessian moments with their two products, and the per-point offsets shared
-# by the thread's two nodes.
-FIXUP_FMA_OPS = 19
+# the Hessian factor (3), five running sums (sE, sA, 2 gradient), two
+# Hessian moments with their one product (the third comes from the trace
+# at the end), and the per-point offsets (4) shared by the thread's two
+# nodes.
+FIXUP_FMA_OPS = 17
 
 
 def fixup_peak_gterms(sms=None):

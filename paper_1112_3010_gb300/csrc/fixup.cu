@@ -494,9 +494,11 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
                         if constexpr (LVL >= 2) {
                             const float2 F = __fmul2_rn(__fmul2_rn(Eir, ir), __ffma2_rn(ir, ih2, itau2));
                             sA = __fadd2_rn(sA, Eir);
+                            // every moment but the last diagonal one, which
+                            // the trace gives at the end
                             int qh = 0;
 #pragma unroll
-                            for (int a = 0; a < D; ++a) {
+                            for (int a = 0; a < D - 1; ++a) {
                                 const float2 Fd = __fmul2_rn(F, dv[a]);
 #pragma unroll
                                 for (int bb = a; bb < D; ++bb, ++qh) sB[qh] = __ffma2_rn(Fd, dv[bb], sB[qh]);
@@ -596,12 +598,32 @@ __global__ void __launch_bounds__(D == 2 ? 32 * kTB2 * kTB2 : 256, D == 2 ? 7 : 
         }
         if (LVL >= 2 && d2S) {
             // sB is stored row by row (xx, xy, [xz,] yy, ...); d2S is
-            // diagonal first, then the pairs a < b
+            // diagonal first, then the pairs a < b.  The last diagonal
+            // moment was not summed: per term F r^2 = E/(h r) + E/tau, so
+            // sum_a sB_aa = sA/h + (sE - E0)/tau, E0 the term of a point at
+            // the node itself (its 1/r is taken as 0; it is the only point
+            // at distance 0, so the shift makes E0 its multiplicity), and
+            // H_last = sum_{a<last} sB_aa/sE - (1 - E0/sE)/tau + g_last^2/tau
             const float Ad = lane(sA, j) * ih * inv;
+            float e0 = 0.f;
+            if (mg[j] == 0.f) {
+                const int xj = x, yj = (D == 2) ? y + 8 * j : y, zj = (D == 2) ? 0 : z + 4 * j;
+                const int64_t gb = (xj >> 3) + (int64_t)P.nb0 * ((yj >> 3) + (int64_t)P.nb1 * (zj >> 3));
+                const int lc = (xj & 7) + 8 * (yj & 7) + 64 * (zj & 7);
+                const int u0 = P.bin_start[gb], u1 = u0 + P.bin_nuniq[gb];
+                for (int u = u0; u < u1; ++u)
+                    if (P.ucell[u] == lc) e0 = (float)P.ucount[u];
+            }
+            float tr = 0.f;
+#pragma unroll
+            for (int a = 0; a < D - 1; ++a) tr += lane(sB[sym_index<D>(a, a)], j) * inv;
             int q = 0;
 #pragma unroll
-            for (int a = 0; a < D; ++a, ++q)
-                d2S[q * P.nnodes + nd] = (TO)(Ad - lane(sB[sym_index<D>(a, a)], j) * inv + g[a] * g[a] * itau);
+            for (int a = 0; a < D; ++a, ++q) {
+                const float Baa = (a < D - 1) ? Ad - lane(sB[sym_index<D>(a, a)], j) * inv
+                                              : tr - (1.f - e0 * inv) * itau;
+                d2S[q * P.nnodes + nd] = (TO)(Baa + g[a] * g[a] * itau);
+            }
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
