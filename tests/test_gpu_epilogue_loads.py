@@ -20,6 +20,9 @@ CASES = {
     "stars384_M768": (lambda: wl.stars(N=384, K=6000, n_shapes=1, tau=2.0 / 384, seed=63, r_lo=0.15, r_hi=0.4,
                                        center=(0.5, 0.5)), ("S", "dS", "sign"), (768, 768)),
     "sphere64": (lambda: wl.sphere(N=64, K=4000, radius=0.3, tau=0.02, seed=71), ("S", "dS", "sign"), None),
+    # 3D at a compiled line length (256): the TMA epilogue applies
+    "sphere128": (lambda: wl.sphere(N=128, K=12000, radius=0.3, tau=0.01, seed=73), ("S", "dS", "d2S", "sign"),
+                  None),
 }
 
 
