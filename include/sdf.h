@@ -228,10 +228,16 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K,
 /*
  * sdf_execute_multi_host -- sdf_execute_multi with HOST buffers, as
  * sdf_execute_host is to sdf_execute: the points and weights are copied once
- * (to plans[0]'s staging buffer); S, dS and d2S in pinned host memory are
- * written by the kernels directly, other outputs are staged on the plan's
- * device and copied back.  Waits for every plan's stream and returns the
- * first non-OK status of sdf_sync() over the plans.  Errors as
+ * (to plans[0]'s staging buffer); every output is computed into the plan's
+ * device staging buffer and copied back by the copy engine, each plan's as
+ * soon as its fix-up is done.  With two or more FP32 plans whose S, dS and
+ * d2S buffers (those requested) of plans[0] are page-locked (pinned,
+ * device-mapped), plans[0]'s S, dS and d2S are copied as soon as its
+ * epilogue has written them, while the other plans compute, and its fix-up
+ * then writes the nodes it recomputes straight into those host buffers.
+ * The staging buffers grow to the outputs' size on first use (an
+ * allocation, SDF_ERR_OOM if it fails).  Waits for every plan's stream and
+ * returns the first non-OK status of sdf_sync() over the plans.  Errors as
  * sdf_execute_multi.
  */
 sdf_status sdf_execute_multi_host(int n, const sdf_plan *plans, int64_t K,

@@ -202,8 +202,9 @@ def sdf_execute_multi(handles, K, points, weights, S, dS, d2S, sign, flags):
 
 
 def sdf_execute_multi_host(handles, K, points, weights, S, dS, d2S, sign, flags):
-    """As sdf_execute_multi with host tensors (pinned S/dS/d2S are written by
-    the kernels directly)."""
+    """As sdf_execute_multi with host tensors: outputs come back by the copy
+    engine, the first plan's S/dS/d2S (when pinned) while the other plans
+    still compute."""
     n = len(handles)
     hv = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
 

@@ -674,10 +674,34 @@ sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double
     return SDF_OK;
 }
 
+// Host destinations of one plan's outputs in sdf_execute_multi_host (the
+// device outputs given to multi_core are then the plan's staging buffers).
+// early: S, dS and d2S are copied to the host as soon as the epilogue has
+// written them, and the fix-up, which runs after that copy, writes its nodes
+// straight into the host buffers (mS, mdS, md2: their device-mapped
+// addresses); otherwise every output is copied after the plan's fix-up.
+struct HostCopy {
+    void *S, *dS, *d2S;
+    int8_t *sign;
+    uint8_t *flags;
+    void *mS, *mdS, *md2;
+    bool early;
+};
+
+static sdf_status multi_core(int n, const sdf_plan *plans, int64_t K, const double *points, const double *weights,
+                             void *const *S, void *const *dS, void *const *d2S, int8_t *const *sign,
+                             uint8_t *const *flags, const HostCopy *hc);
+
 sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const double *points, const double *weights,
                              void *const *S, void *const *dS, void *const *d2S, int8_t *const *sign,
                              uint8_t *const *flags) {
     ScopedRange range_("sdf_execute_multi");
+    return multi_core(n, plans, K, points, weights, S, dS, d2S, sign, flags, nullptr);
+}
+
+static sdf_status multi_core(int n, const sdf_plan *plans, int64_t K, const double *points, const double *weights,
+                             void *const *S, void *const *dS, void *const *d2S, int8_t *const *sign,
+                             uint8_t *const *flags, const HostCopy *hc) {
     if (n < 1 || !plans || !plans[0] || !points) return SDF_ERR_INVALID_ARG;
     sdf_plan p0 = plans[0];
     auto at = [](auto *const *arr, int i) { return arr ? arr[i] : nullptr; };
@@ -698,9 +722,19 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
     if (p0->D == 1) {
         // one CTA per line: nothing worth sharing
         for (int i = 0; i < n; ++i) {
-            sdf_status s = sdf_execute(plans[i], K, points, weights, at(S, i), at(dS, i), at(d2S, i), at(sign, i),
+            sdf_plan p = plans[i];
+            sdf_status s = sdf_execute(p, K, points, weights, at(S, i), at(dS, i), at(d2S, i), at(sign, i),
                                        at(flags, i));
             if (s != SDF_OK) return s;
+            if (!hc) continue;
+            const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
+            const int64_t nn = p->nnodes;
+            const HostCopy &h = hc[i];
+            if (h.S) CK(cudaMemcpyAsync(h.S, at(S, i), esz * nn, cudaMemcpyDeviceToHost, p->stream));
+            if (h.dS) CK(cudaMemcpyAsync(h.dS, at(dS, i), esz * nn, cudaMemcpyDeviceToHost, p->stream));
+            if (h.d2S) CK(cudaMemcpyAsync(h.d2S, at(d2S, i), esz * nn, cudaMemcpyDeviceToHost, p->stream));
+            if (h.sign) CK(cudaMemcpyAsync(h.sign, at(sign, i), nn, cudaMemcpyDeviceToHost, p->stream));
+            if (h.flags) CK(cudaMemcpyAsync(h.flags, at(flags, i), nn, cudaMemcpyDeviceToHost, p->stream));
         }
         return SDF_OK;
     }
@@ -801,8 +835,36 @@ sdf_status sdf_execute_multi(int n, const sdf_plan *plans, int64_t K, const doub
         MCK(launch_inverse_epilogue(p, ww, at(S, i), at(dS, i), at(d2S, i), sg, fl, sin));
         if (share_sign && i == 0) MCK(cudaEventRecord(ev[2 * n + 1], p->stream));
         const int8_t *sfix = ww ? (sg ? sg : sin) : nullptr;
-        if (p->prec == SDF_FP32) MCK(launch_fixup(p, ww, at(S, i), at(dS, i), at(d2S, i), sfix, fl));
+        void *fS = at(S, i), *fdS = at(dS, i), *fd2 = at(d2S, i);
+        const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
+        const int64_t nn = p->nnodes;
+        const int nh = p->D * (p->D + 1) / 2;
+        // outputs bound for the host: S, dS, d2S (before the fix-up when
+        // early: it then writes its nodes into the host buffers directly),
+        // or everything after the fix-up
+        auto copy_fields = [&]() -> cudaError_t {
+            const HostCopy &h = hc[i];
+            cudaError_t e = cudaSuccess;
+            if (h.S && e == cudaSuccess) e = cudaMemcpyAsync(h.S, at(S, i), esz * nn, cudaMemcpyDeviceToHost, p->stream);
+            if (h.dS && e == cudaSuccess)
+                e = cudaMemcpyAsync(h.dS, at(dS, i), esz * nn * p->D, cudaMemcpyDeviceToHost, p->stream);
+            if (h.d2S && e == cudaSuccess)
+                e = cudaMemcpyAsync(h.d2S, at(d2S, i), esz * nn * nh, cudaMemcpyDeviceToHost, p->stream);
+            return e;
+        };
+        if (hc && hc[i].early) {
+            MCK(copy_fields());
+            fS = hc[i].mS;
+            fdS = hc[i].mdS;
+            fd2 = hc[i].md2;
+        }
+        if (p->prec == SDF_FP32) MCK(launch_fixup(p, ww, fS, fdS, fd2, sfix, fl));
         if (at(flags, i)) MCK(launch_source_flags(p, at(flags, i)));
+        if (hc) {
+            if (!hc[i].early) MCK(copy_fields());
+            if (hc[i].sign) MCK(cudaMemcpyAsync(hc[i].sign, at(sign, i), nn, cudaMemcpyDeviceToHost, p->stream));
+            if (hc[i].flags) MCK(cudaMemcpyAsync(hc[i].flags, at(flags, i), nn, cudaMemcpyDeviceToHost, p->stream));
+        }
         MCK(cudaEventRecord(ev[n + i], p->stream));
     }
     // join: p0's next x-pass must not overwrite what the others still read
@@ -870,6 +932,7 @@ sdf_status sdf_execute_host(sdf_plan p, int64_t K, const double *points, const d
 sdf_status sdf_execute_multi_host(int n, const sdf_plan *plans, int64_t K, const double *points,
                                   const double *weights, void *const *S, void *const *dS, void *const *d2S,
                                   int8_t *const *sign, uint8_t *const *flags) {
+    ScopedRange range_("sdf_execute_multi_host");
     if (n < 1 || !plans || !points || K < 1) return SDF_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i)
         if (!plans[i]) return SDF_ERR_INVALID_ARG;
@@ -877,23 +940,25 @@ sdf_status sdf_execute_multi_host(int n, const sdf_plan *plans, int64_t K, const
     sdf_plan p0 = plans[0];
     const int D = p0->D;
     const int nh = D * (D + 1) / 2;
-    // device views of every plan's outputs: pinned host memory the kernels
-    // write directly, else the plan's staging buffer (copied back below)
-    std::vector<void *> dev_S(n), dev_dS(n), dev_d2(n), mS(n), mdS(n), md2(n);
+    // every output is computed into the plan's staging buffer and copied
+    // by the copy engine (the link carries ~190 GB/s that way, against
+    // ~110 GB/s for kernels storing to host memory).  plans[0]'s S, dS and
+    // d2S go as soon as its epilogue has written them, beside the other
+    // plans' work, and its fix-up then stores its nodes straight into the
+    // host buffers; that needs them pinned (device-mapped)
+    std::vector<void *> dev_S(n), dev_dS(n), dev_d2(n);
     std::vector<int8_t *> dev_sg(n);
     std::vector<uint8_t *> dev_fl(n);
+    std::vector<HostCopy> hc(n);
     double *dpts = nullptr, *dw = nullptr;
     for (int i = 0; i < n; ++i) {
         sdf_plan p = plans[i];
         const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
         const int64_t nn = p->nnodes;
-        mS[i] = mapped_host(at(S, i));
-        mdS[i] = mapped_host(at(dS, i));
-        md2[i] = mapped_host(at(d2S, i));
+        const int nd = (p->D == 1) ? 1 : p->D, nhh = (p->D == 1) ? 1 : nh;
         const size_t need = (i == 0) ? sizeof(double) * K * D * (weights ? 2 : 1) : 0;
-        const size_t oS = need, odS = oS + ((at(S, i) && !mS[i]) ? esz * nn : 0),
-                     od2 = odS + ((at(dS, i) && !mdS[i]) ? esz * nn * D : 0),
-                     osg = od2 + ((at(d2S, i) && !md2[i]) ? esz * nn * nh : 0), ofl = osg + (at(sign, i) ? nn : 0),
+        const size_t oS = need, odS = oS + (at(S, i) ? esz * nn : 0), od2 = odS + (at(dS, i) ? esz * nn * nd : 0),
+                     osg = od2 + (at(d2S, i) ? esz * nn * nhh : 0), ofl = osg + (at(sign, i) ? nn : 0),
                      tot = ofl + (at(flags, i) ? nn : 0);
         if (tot > p->staging_bytes) {
             cudaStreamSynchronize(p->stream);
@@ -908,28 +973,30 @@ sdf_status sdf_execute_multi_host(int n, const sdf_plan *plans, int64_t K, const
             dpts = reinterpret_cast<double *>(base);
             dw = weights ? dpts + K * D : nullptr;
         }
-        dev_S[i] = at(S, i) ? (mS[i] ? mS[i] : base + oS) : nullptr;
-        dev_dS[i] = at(dS, i) ? (mdS[i] ? mdS[i] : base + odS) : nullptr;
-        dev_d2[i] = at(d2S, i) ? (md2[i] ? md2[i] : base + od2) : nullptr;
+        dev_S[i] = at(S, i) ? base + oS : nullptr;
+        dev_dS[i] = at(dS, i) ? base + odS : nullptr;
+        dev_d2[i] = at(d2S, i) ? base + od2 : nullptr;
         dev_sg[i] = at(sign, i) ? reinterpret_cast<int8_t *>(base + osg) : nullptr;
         dev_fl[i] = at(flags, i) ? reinterpret_cast<uint8_t *>(base + ofl) : nullptr;
+        HostCopy &h = hc[i];
+        h.S = at(S, i);
+        h.dS = at(dS, i);
+        h.d2S = at(d2S, i);
+        h.sign = at(sign, i);
+        h.flags = at(flags, i);
+        h.mS = mapped_host(h.S);
+        h.mdS = mapped_host(h.dS);
+        h.md2 = mapped_host(h.d2S);
+        h.early = i == 0 && n > 1 && p->D >= 2 && p->prec == SDF_FP32 && (!h.S || h.mS) && (!h.dS || h.mdS) &&
+                  (!h.d2S || h.md2);
     }
     CK(cudaMemcpyAsync(dpts, points, sizeof(double) * K * D, cudaMemcpyHostToDevice, p0->stream));
     if (weights) CK(cudaMemcpyAsync(dw, weights, sizeof(double) * K * D, cudaMemcpyHostToDevice, p0->stream));
-    sdf_status s = sdf_execute_multi(n, plans, K, dpts, dw, dev_S.data(), dev_dS.data(), dev_d2.data(),
-                                     dev_sg.data(), dev_fl.data());
-    if (s != SDF_OK) return s;
-    for (int i = 0; i < n; ++i) {
-        sdf_plan p = plans[i];
-        const size_t esz = (p->prec == SDF_FP64) ? sizeof(double) : sizeof(float);
-        const int64_t nn = p->nnodes;
-        if (at(S, i) && !mS[i]) CK(cudaMemcpyAsync(at(S, i), dev_S[i], esz * nn, cudaMemcpyDeviceToHost, p->stream));
-        if (at(dS, i) && !mdS[i])
-            CK(cudaMemcpyAsync(at(dS, i), dev_dS[i], esz * nn * D, cudaMemcpyDeviceToHost, p->stream));
-        if (at(d2S, i) && !md2[i])
-            CK(cudaMemcpyAsync(at(d2S, i), dev_d2[i], esz * nn * nh, cudaMemcpyDeviceToHost, p->stream));
-        if (at(sign, i)) CK(cudaMemcpyAsync(at(sign, i), dev_sg[i], nn, cudaMemcpyDeviceToHost, p->stream));
-        if (at(flags, i)) CK(cudaMemcpyAsync(at(flags, i), dev_fl[i], nn, cudaMemcpyDeviceToHost, p->stream));
+    sdf_status s = multi_core(n, plans, K, dpts, dw, dev_S.data(), dev_dS.data(), dev_d2.data(), dev_sg.data(),
+                              dev_fl.data(), hc.data());
+    if (s != SDF_OK) {
+        for (int i = 0; i < n; ++i) cudaStreamSynchronize(plans[i]->stream);
+        return s;
     }
     sdf_status first = SDF_OK;
     for (int i = 0; i < n; ++i) {

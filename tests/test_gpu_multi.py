@@ -79,31 +79,48 @@ def test_mismatched_plans_rejected():
     assert torch.isfinite(out["S"]).all()
 
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_multi_host_matches_device(pinned):
-    """sdf_execute_multi_host: host points and outputs (pinned: written by the
-    kernels directly; pageable: staged), equal to the device results."""
+@pytest.mark.parametrize("pinned,outputs", [
+    ("all", ("S", "dS", "d2S", "sign")),
+    ("none", ("S", "dS", "d2S", "sign")),
+    ("all", ("S", "sign")),
+    ("all", ("S", "dS", "sign")),
+    # the first plan's S pageable: its outputs are copied after its fix-up
+    ("not_S0", ("S", "dS", "d2S", "sign")),
+])
+def test_multi_host_matches_device(pinned, outputs):
+    """sdf_execute_multi_host: host points and outputs equal to the device
+    results, twice in a row.  With the first plan's S, dS and d2S pinned, they
+    are copied right after its epilogue and its fix-up writes the nodes it
+    recomputes into them directly; otherwise each plan's outputs are copied
+    after its fix-up."""
     s = wl.stars(N=256, K=3000, n_shapes=2, tau=0.004, seed=37)
     taus = [0.004, 0.002]
-    outputs = ("S", "dS", "d2S", "sign")
     plans = [pkg.Plan(2, s.dims, s.h, t, precision="fp32", outputs=outputs) for t in taus]
     dev = pkg.execute_multi(plans, torch.from_numpy(s.points).cuda(), torch.from_numpy(s.weights).cuda())
+    assert plans[0].stats().n_fixup_nodes > 0
     shp = (s.dims[1], s.dims[0])
 
-    def host(shape, dtype):
+    def host(shape, dtype, i, k):
         t = torch.empty(shape, dtype=dtype)
-        return t.pin_memory() if pinned else t
+        if pinned == "none" or (pinned == "not_S0" and i == 0 and k == "S"):
+            return t
+        return t.pin_memory()
 
-    outs = [{"S": host(shp, torch.float32), "dS": host((2,) + shp, torch.float32),
-             "d2S": host((3,) + shp, torch.float32), "sign": host(shp, torch.int8),
-             "flags": host(shp, torch.uint8)} for _ in taus]
-    col = lambda k: [o[k] for o in outs]
-    pkg.sdf_execute_multi_host([p.handle for p in plans], s.K, torch.from_numpy(s.points),
-                               torch.from_numpy(s.weights), col("S"), col("dS"), col("d2S"), col("sign"),
-                               col("flags"))
-    for o, d in zip(outs, dev):
-        for k in o:
-            assert torch.equal(o[k], d[k].cpu()), k
+    shapes = {"S": (shp, torch.float32), "dS": ((2,) + shp, torch.float32), "d2S": ((3,) + shp, torch.float32),
+              "sign": (shp, torch.int8), "flags": (shp, torch.uint8)}
+    want = [k for k in shapes if k in outputs or k == "flags"]
+    outs = [{k: host(*shapes[k], i, k) for k in want} for i in range(len(taus))]
+    col = lambda k: [o[k] for o in outs] if k in want else None
+    for rep in range(2):
+        for o in outs:
+            for v in o.values():
+                v.fill_(7)
+        pkg.sdf_execute_multi_host([p.handle for p in plans], s.K, torch.from_numpy(s.points),
+                                   torch.from_numpy(s.weights), col("S"), col("dS"), col("d2S"), col("sign"),
+                                   col("flags"))
+        for o, d in zip(outs, dev):
+            for k in o:
+                assert torch.equal(o[k], d[k].cpu()), (rep, k)
 
 
 def test_multi_after_pending_work_on_other_streams():
