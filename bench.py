@@ -138,7 +138,8 @@ def cpu_baseline(shapes, n_nodes=12288, seed=0, keep=None):
         sel = rng.choice(s.n_nodes, n_nodes // len(shapes), replace=False)
         X = oracle.grid_nodes(s.dims, s.h, sel)
         t0 = time.perf_counter()
-        ref = oracle.evaluate(Y, X, s.tau, weights=W, want=("S", "dS", "d2S", "mu"))
+        ref = oracle.evaluate(Y, X, s.tau, weights=W, want=("S", "dS", "d2S", "mu", "R"))
+        ref["wmax"] = float(np.linalg.norm(W, axis=1).max())
         total_t += time.perf_counter() - t0
         total_n += len(sel)
         if keep is not None:
@@ -150,6 +151,32 @@ def cpu_baseline(shapes, n_nodes=12288, seed=0, keep=None):
             "sample": "%d random nodes per tau of the 2048^2 grid (direct FP64 sum over all K=40000 points), "
                       "S, grad S, Hessian, mu; %.1f s" % (total_n // len(shapes), total_t),
             "extrapolated_full_step_s": sum(s.n_nodes for s in shapes) / rate}
+
+
+def oracle_accuracy(pkg, shapes, outs, samples):
+    """The bench's own outputs (the last timed step) against the oracle
+    values of the cpu_baseline leg's sampled nodes: over the nodes the
+    library does not cap, max |S - S_oracle| / tau, |grad S - oracle| and
+    |Hessian - oracle| * tau; and sign mismatches away from the points
+    (farther than 2 max|weight| + h sqrt(2) from every point) where the
+    oracle's |mu| is not within 0.05 of 1/2."""
+    acc = []
+    for s, o, (sel, ref) in zip(shapes, outs, samples):
+        fl = o["flags"].cpu().numpy().ravel()[sel]
+        ok = (fl & pkg.SDF_FLAG_CAPPED) == 0
+        sg = o["sign"].cpu().numpy().ravel()[sel]
+        S = o["S"].double().cpu().numpy().ravel()[sel] * sg
+        G = o["dS"].double().cpu().numpy().reshape(2, -1)[:, sel].T
+        H = o["d2S"].double().cpu().numpy().reshape(3, -1)[:, sel].T
+        band = 2 * ref["wmax"] + s.h * np.sqrt(2.0)
+        off = (ref["R"] > band) & (np.abs(np.abs(ref["mu"]) - 0.5) >= 0.05)
+        osign = np.where(np.abs(ref["mu"]) >= 0.5, 1, -1)
+        acc.append({"tau": s.tau, "sampled_nodes": int(len(sel)), "uncapped": int(ok.sum()),
+                    "max_abs_S_minus_oracle_over_tau": float(np.abs(S - ref["S"])[ok].max() / s.tau),
+                    "max_abs_dS_minus_oracle": float(np.abs(G - ref["dS"])[ok].max()),
+                    "max_abs_d2S_minus_oracle_times_tau": float(np.abs(H - ref["d2S"])[ok].max() * s.tau),
+                    "sign_checked": int(off.sum()), "sign_mismatch": int((sg[off] != osign[off]).sum())})
+    return acc
 
 
 def run_reference(args):
@@ -713,6 +740,7 @@ def main():
     samples = []
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(shapes, keep=samples)
+        cpu["accuracy_of_this_run"] = oracle_accuracy(pkg, shapes, outs, samples)
 
     # the other configurations under the same clock (one GPU, rank 0 alone)
     extra = {}
