@@ -66,7 +66,9 @@ typedef enum {
     SDF_ERR_OOM = 4,               /* device allocation failed                  */
     SDF_ERR_CUDA = 5,              /* a CUDA runtime call failed                */
     SDF_ERR_TIMEOUT = 6,           /* a bounded device-side wait expired        */
-    SDF_ERR_CAPACITY = 7           /* input larger than a fixed-size buffer     */
+    SDF_ERR_CAPACITY = 7,          /* input larger than a fixed-size buffer     */
+    SDF_ERR_INTERNAL = 8           /* a device-side consistency check failed    */
+                                   /* (sdf_set_debug_checks)                    */
 } sdf_status;
 
 typedef enum { SDF_FP64 = 0, SDF_FP32 = 1 } sdf_precision;
@@ -594,15 +596,45 @@ sdf_status sdf_execute_noalloc(int D, const int64_t *dims, double h, double tau,
  *                            device were out of memory: the call reports
  *                            SDF_ERR_OOM and releases what it had allocated.
  *                            0 disables.
- *   SDF_HOOK_TMA_WAIT_POLLS  the epilogue's TMA waits give up after `value`
- *                            non-blocking polls (0: the built-in bound), so
- *                            an execute meets the expiry path on purpose: the
- *                            copy in flight still lands (the kernel waits for
- *                            it, bounded) and sdf_sync reports
- *                            SDF_ERR_TIMEOUT; the plan stays usable.
+ *   SDF_HOOK_TMA_WAIT_POLLS  value > 0: the epilogue's TMA waits poll, `value`
+ *                            times, a barrier that nothing completes, so every
+ *                            execute through the TMA epilogue meets the expiry
+ *                            path on its first group: the copy in flight still
+ *                            lands (the kernel waits for it, bounded) and
+ *                            sdf_sync reports SDF_ERR_TIMEOUT; the plan stays
+ *                            usable.  0: the normal waits.
  */
-enum { SDF_HOOK_FAIL_ALLOC = 1, SDF_HOOK_TMA_WAIT_POLLS = 2 };
+enum { SDF_HOOK_FAIL_ALLOC = 1, SDF_HOOK_TMA_WAIT_POLLS = 2, SDF_HOOK_CORRUPT_BINS = 3 };
 sdf_status sdf_debug_hook(int hook, int64_t value);
+/*   SDF_HOOK_CORRUPT_BINS    value != 0: after binning, every execute adds
+ *                            one to the unique-node count of the first bin
+ *                            that lies wholly inside the grid and holds no
+ *                            repeated node, so that its node list takes in
+ *                            the next occupied bin's first node.  Every
+ *                            kernel still reads and writes inside its
+ *                            buffers (the borrowed node is a valid node of
+ *                            the bin's box); the results are wrong, and with
+ *                            the debug checks on the execute reports
+ *                            SDF_ERR_INTERNAL.  0 disables. */
+
+/*
+ * sdf_set_debug_checks -- device-side consistency checks (process-wide; the
+ * paper has no counterpart).  Off unless the environment variable
+ * SDF_DEBUG_CHECKS is set to a non-zero value when the library is first
+ * used, or this call turns them on (on != 0).  With them on, every execute
+ * also checks on the device, after binning, the structures the later
+ * kernels address memory through: bin offsets ascending and within the
+ * binned points, each bin's unique-node count within its points, node codes
+ * inside the bin and the grid, multiplicities positive; for float plans,
+ * after the Chebyshev map, the per-row lists of occupied bins (ascending,
+ * within the row); and at the end, that S, dS and d2S are finite.  A failed
+ * check records SDF_ERR_INTERNAL (reported by sdf_sync, unless an earlier
+ * error was recorded) and sdf_last_error() names the check and the index
+ * where it failed.  The checks read only: results are bitwise those of an
+ * execute without them.  Cost: a few extra launches per execute.
+ */
+sdf_status sdf_set_debug_checks(int on);
+int sdf_get_debug_checks(void);
 
 /* Free the plan and everything it owns (synchronises its stream). */
 void sdf_plan_destroy(sdf_plan plan);

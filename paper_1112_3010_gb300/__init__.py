@@ -26,7 +26,7 @@ SDF_FLAG_CAPPED, SDF_FLAG_FIXUP, SDF_FLAG_SOURCE = 1, 2, 4
 SDF_KERNEL_EXP, SDF_KERNEL_GREEN = 0, 1
 STATUS = {0: "SDF_OK", 1: "SDF_ERR_INVALID_ARG", 2: "SDF_ERR_UNSUPPORTED",
           3: "SDF_ERR_POINT_OUT_OF_GRID", 4: "SDF_ERR_OOM", 5: "SDF_ERR_CUDA",
-          6: "SDF_ERR_TIMEOUT", 7: "SDF_ERR_CAPACITY"}
+          6: "SDF_ERR_TIMEOUT", 7: "SDF_ERR_CAPACITY", 8: "SDF_ERR_INTERNAL"}
 
 EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward", "sdf_sync",
             "sdf_plan_get_info", "sdf_get_stats", "sdf_plan_destroy", "sdf_status_string",
@@ -36,8 +36,9 @@ EXPORTED = ["sdf_plan_create", "sdf_execute", "sdf_execute_host", "sdf_backward"
             "sdf_plan_set_tuning", "sdf_plan_autotune", "sdf_curvature", "sdf_plan_set_full_range",
             "sdf_mesh_sources", "sdf_plan_set_kernel", "sdf_green_profile", "sdf_execute_multi",
             "sdf_execute_multi_host", "sdf_plan_set_padding", "sdf_batch_autotune",
-            "sdf_plan_set_epilogue_loads", "sdf_debug_hook"]
-SDF_HOOK_FAIL_ALLOC, SDF_HOOK_TMA_WAIT_POLLS = 1, 2
+            "sdf_plan_set_epilogue_loads", "sdf_debug_hook", "sdf_set_debug_checks",
+            "sdf_get_debug_checks"]
+SDF_HOOK_FAIL_ALLOC, SDF_HOOK_TMA_WAIT_POLLS, SDF_HOOK_CORRUPT_BINS = 1, 2, 3
 
 
 class SDFError(RuntimeError):
@@ -46,7 +47,7 @@ class SDFError(RuntimeError):
         msg = "%s: %s" % (where, STATUS.get(code, str(code)))
         try:
             extra = _lib().sdf_last_error().decode()
-            if extra and code in (4, 5):
+            if extra and code in (4, 5, 8):
                 msg += " (%s)" % extra
         except Exception:
             pass
@@ -135,6 +136,10 @@ def load_library(path: str | None = None):
         L.sdf_plan_autotune.restype = ctypes.c_int
         L.sdf_debug_hook.argtypes = [ctypes.c_int, i64]
         L.sdf_debug_hook.restype = ctypes.c_int
+        L.sdf_set_debug_checks.argtypes = [ctypes.c_int]
+        L.sdf_set_debug_checks.restype = ctypes.c_int
+        L.sdf_get_debug_checks.argtypes = []
+        L.sdf_get_debug_checks.restype = ctypes.c_int
         L.sdf_plan_set_epilogue_loads.argtypes = [vp, ctypes.c_int]
         L.sdf_plan_set_epilogue_loads.restype = ctypes.c_int
         L.sdf_plan_set_padding.argtypes = [vp, ctypes.POINTER(i64)]
@@ -333,6 +338,16 @@ def sdf_batch_execute(handle, K, points, weights, S, dS, d2S, sign, flags):
 def sdf_debug_hook(hook, value):
     """Test hooks of the failure paths (SDF_HOOK_*)."""
     _ck(_lib().sdf_debug_hook(int(hook), int(value)), "sdf_debug_hook")
+
+
+def sdf_set_debug_checks(on):
+    """Device-side consistency checks for every later execute (process-wide):
+    a failed check raises SDFError with code 8 (SDF_ERR_INTERNAL) at sync."""
+    _ck(_lib().sdf_set_debug_checks(1 if on else 0), "sdf_set_debug_checks")
+
+
+def sdf_get_debug_checks():
+    return bool(_lib().sdf_get_debug_checks())
 
 
 def sdf_plan_set_epilogue_loads(handle, mode):

@@ -13,7 +13,7 @@ OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsdf_gb300.so")
 SOURCES = ["passes_fused_f2.cu", "passes_fused_f3.cu", "passes_inv.cu", "passes_fwd.cu", "passes_fused_d.cu",
            "passes_fused.cu", "api.cu", "points.cu", "spectra.cu", "fixup.cu", "adjoint.cu", "noalloc.cu", "batch.cu",
-           "curvature.cu", "mesh.cu", "line1d.cu"]
+           "curvature.cu", "mesh.cu", "line1d.cu", "debugcheck.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -517,6 +517,7 @@ const char *sdf_status_string(sdf_status s) {
         case SDF_ERR_CUDA: return "CUDA runtime error";
         case SDF_ERR_TIMEOUT: return "a bounded device wait expired";
         case SDF_ERR_CAPACITY: return "input exceeds a fixed-size buffer";
+        case SDF_ERR_INTERNAL: return "a device-side consistency check failed";
         default: return "unknown status";
     }
 }
@@ -656,6 +657,7 @@ sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double
     const bool ww = weights != nullptr;
     if (p->D == 1) {
         CK(launch_line1d(p, K, points, S, dS, d2S, flags));
+        CK(debug_scan_outputs(p, S, dS, d2S));
         return SDF_OK;
     }
     CK(launch_points(p, K, points, weights));
@@ -671,6 +673,7 @@ sdf_status sdf_execute(sdf_plan p, int64_t K, const double *points, const double
     CK(launch_inverse_epilogue(p, ww, S, dS, d2S, sg, fl));
     if (p->prec == SDF_FP32) CK(launch_fixup(p, ww, S, dS, d2S, ww ? sg : nullptr, fl));
     if (flags) CK(launch_source_flags(p, flags));
+    CK(debug_scan_outputs(p, S, dS, d2S));
     return SDF_OK;
 }
 
@@ -860,6 +863,7 @@ static sdf_status multi_core(int n, const sdf_plan *plans, int64_t K, const doub
         }
         if (p->prec == SDF_FP32) MCK(launch_fixup(p, ww, fS, fdS, fd2, sfix, fl));
         if (at(flags, i)) MCK(launch_source_flags(p, at(flags, i)));
+        MCK(debug_scan_outputs(p, at(S, i), at(dS, i), at(d2S, i)));
         if (hc) {
             if (!hc[i].early) MCK(copy_fields());
             if (hc[i].sign) MCK(cudaMemcpyAsync(hc[i].sign, at(sign, i), nn, cudaMemcpyDeviceToHost, p->stream));
@@ -1011,6 +1015,12 @@ sdf_status sdf_sync(sdf_plan p) {
     CK(cudaStreamSynchronize(p->stream));
     CK(cudaMemcpy(p->hsc, p->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
     const int st = p->hsc->status;
+    if (st == SDF_ERR_INTERNAL) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "sdf_sync: device consistency check %d failed at index %lld", p->hsc->dbg_check,
+                 (long long)p->hsc->dbg_where);
+        set_last_error(msg);
+    }
     if (st != 0) CK(cudaMemset(p->dsc, 0, sizeof(int)));
     return (sdf_status)st;
 }
@@ -1148,9 +1158,17 @@ sdf_status sdf_debug_hook(int hook, int64_t value) {
     switch (hook) {
         case SDF_HOOK_FAIL_ALLOC: g_fail_alloc.store(value); return SDF_OK;
         case SDF_HOOK_TMA_WAIT_POLLS: g_tma_polls.store(value); return SDF_OK;
+        case SDF_HOOK_CORRUPT_BINS: set_corrupt_bins(value); return SDF_OK;
         default: return SDF_ERR_INVALID_ARG;
     }
 }
+
+sdf_status sdf_set_debug_checks(int on) {
+    set_debug_checks(on != 0);
+    return SDF_OK;
+}
+
+int sdf_get_debug_checks(void) { return debug_checks() ? 1 : 0; }
 
 sdf_status sdf_plan_set_epilogue_loads(sdf_plan p, int mode) {
     if (!p || (mode != 0 && mode != 1)) return SDF_ERR_INVALID_ARG;

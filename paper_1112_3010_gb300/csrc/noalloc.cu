@@ -237,6 +237,7 @@ extern "C" sdf_status sdf_execute_noalloc(int D, const int64_t *dims, double h, 
     NCK(launch_inverse_epilogue(p, ww, S, dS, d2S, sg, fl));
     if (p->prec == SDF_FP32) NCK(launch_fixup(p, ww, S, dS, d2S, ww ? sg : nullptr, fl));
     if (flags) NCK(launch_source_flags(p, flags));
+    NCK(debug_scan_outputs(p, S, dS, d2S));
     DevScalars hs;
     NCK(cudaMemcpyAsync(&hs, p->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
     NCK(cudaStreamSynchronize(p->stream));

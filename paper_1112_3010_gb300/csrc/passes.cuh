@@ -560,7 +560,7 @@ struct EpiParams {
     double hs_inv;  // 1 / scale of the stored Hessian kernels
     float tau_f, itau_f, hs_inv_f;  // tau, 1/tau, hs_inv in float (float kernels stay off the FP64 pipe)
     unsigned stage_off;  // TMA variant: staging buffer at or after this byte offset (1 KB of slack)
-    unsigned wait_polls; // TMA variant: 0, or the non-blocking polls after which a wait expires (test hook)
+    unsigned wait_polls; // TMA variant: 0, or the test hook's polls of a barrier that never completes
 };
 
 // ---------------------------------------------------------------- TMA staging (epilogue)
@@ -668,11 +668,14 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     // persistent (CTAs stride over the blocks of R lines), and the copy of the
     // next block's first group is issued while the current block's last
     // group is transformed.
-    __shared__ __align__(8) unsigned long long s_bar;
+    // s_never: a barrier nothing arrives on, which the test hook's waits poll
+    // (wait_polls > 0) so that they expire on their first group, whatever the
+    // copies' timing
+    __shared__ __align__(8) unsigned long long s_bar, s_never;
     // the buffer starts at the first 1024-byte boundary at or after stage_off
     const unsigned sbase = smem_u32(smraw);
     V *stage = reinterpret_cast<V *>(smraw + (((sbase + P.stage_off + 1023u) & ~1023u) - sbase));
-    const unsigned bar = smem_u32(&s_bar);
+    const unsigned bar = smem_u32(&s_bar), never = smem_u32(&s_never);
     const unsigned stage_bytes = (unsigned)(R * L * sizeof(V));
     const int64_t nblk = (n_lines + R - 1) / R;
     auto issue = [&](int64_t blk, int g) {  // one thread: copy group g of block blk
@@ -686,6 +689,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     if constexpr (TMA) {
         if (threadIdx.x == 0) {
             mbar_init(bar, 1);
+            if (P.wait_polls) mbar_init(never, 1);
             if (blockIdx.x < nblk) issue(blockIdx.x, P.order[0]);
         }
         __syncthreads();
@@ -723,7 +727,7 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
         const int g = P.order[gi];
         V v[16];
         if constexpr (TMA) {
-            const bool ok = P.wait_polls ? mbar_test(bar, nwait & 1u, P.wait_polls)
+            const bool ok = P.wait_polls ? mbar_test(never, 0u, P.wait_polls)
                                          : mbar_wait(bar, nwait & 1u, kTmaWaitLimit);
             ++nwait;
             if (__syncthreads_or(!ok)) {  // every thread takes the same way out
@@ -814,10 +818,11 @@ __global__ void __launch_bounds__(MT) k_epilogue(const cx<T> *__restrict__ in, i
     }  // blocks of lines
     if constexpr (TMA) {
         if (expired) {
-            // record the expiry; let the copy in flight land (bounded) before the CTA leaves
+            // record the expiry; let the copy in flight land (bounded) before
+            // the CTA leaves: one copy at a time, the one the failed wait
+            // (number nwait - 1) was for
             if (threadIdx.x == 0) atomicCAS(&P.dsc_w->status, 0, (int)SDF_ERR_TIMEOUT);
-            mbar_wait(bar, 0u, kTmaWaitLimit);
-            mbar_wait(bar, 1u, kTmaWaitLimit);
+            mbar_wait(bar, (nwait - 1u) & 1u, kTmaWaitLimit);
             return;
         }
     }

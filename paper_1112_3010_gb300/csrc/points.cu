@@ -419,7 +419,8 @@ cudaError_t launch_points(sdf_plan_impl *p, int64_t K, const double *points, con
         k_dedupe<512><<<(unsigned)p->nbins, 128, 0, st>>>(p->D, K, weights, p->bin_start, p->pt_entry,
                                                          p->bin_nuniq, p->ucell, p->ucount, p->uw, p->dsc);
     prof_end(p, st);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return debug_after_binning(p);
 }
 
 // Summed-area table of the points per bin, written over bin_count (free once
@@ -533,7 +534,9 @@ cudaError_t launch_cheb(sdf_plan_impl *p, cudaStream_t on) {
         k_occ_rows<true><<<gw, 256, 0, st>>>(p->bin_nuniq, (int)nb0, nrows, p->occ_start, p->occ_x);
     }
     prof_end(p, st);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return debug_after_cheb(p, st);
 }
 
 cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags) {

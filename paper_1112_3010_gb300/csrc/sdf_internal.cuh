@@ -67,6 +67,9 @@ struct DevScalars {
     // nearest point in nodes; positive floats order as their bits)
     unsigned long long fix_nmax, fix_rounds;
     unsigned fix_rinv_bits, pad1;
+    // debug checks (sdf_set_debug_checks): the first failed check and where
+    int dbg_check, pad2;
+    long long dbg_where;
 };
 
 // Kernel-level event timing (sdf_profile_enable) and the launch counter.
@@ -184,6 +187,14 @@ cudaError_t launch_inverse_epilogue(sdf_plan_impl *p, bool with_weights, void *S
 cudaError_t launch_fixup(sdf_plan_impl *p, bool with_sign, void *S, void *dS, void *d2S, const int8_t *sign,
                          uint8_t *flags);
 cudaError_t launch_source_flags(sdf_plan_impl *p, uint8_t *flags);
+// Debug checks (debugcheck.cu): the switch, the bin-corruption test hook, and
+// the check launches after binning, after the Chebyshev map and on outputs.
+bool debug_checks();
+void set_debug_checks(bool on);
+void set_corrupt_bins(long long v);
+cudaError_t debug_after_binning(sdf_plan_impl *p);
+cudaError_t debug_after_cheb(sdf_plan_impl *p, cudaStream_t st);
+cudaError_t debug_scan_outputs(sdf_plan_impl *p, const void *S, const void *dS, const void *d2S);
 cudaError_t build_spectra(sdf_plan_impl *p);
 cudaError_t launch_line1d(sdf_plan_impl *p, int64_t K, const double *points, void *S, void *dS, void *d2S,
                           uint8_t *flags);

@@ -4,10 +4,10 @@
 * a device allocation that fails (as an exhausted device would): plan creation
   and the first execute report SDF_ERR_OOM, release what they allocated, and
   the library works again afterwards;
-* the epilogue's TMA waits expire after one non-blocking poll while their
-  copies are in flight: each CTA lets its copy land (a bounded wait), the
-  execute reports SDF_ERR_TIMEOUT through sdf_sync, and the same plan then
-  produces the normal result."""
+* the epilogue's TMA waits poll a barrier that nothing completes and so
+  expire on their first group while its copy is in flight: each CTA lets its
+  copy land (a bounded wait), the execute reports SDF_ERR_TIMEOUT through
+  sdf_sync, and the same plan then produces the normal result."""
 import pytest
 import torch
 
