@@ -123,6 +123,46 @@ def test_multi_host_matches_device(pinned, outputs):
                 assert torch.equal(o[k], d[k].cpu()), (rep, k)
 
 
+@pytest.mark.parametrize("case", ["2d_single", "3d_pair", "1d_pair", "2d_fp64_pair"])
+def test_multi_host_other_shapes(case):
+    """sdf_execute_multi_host with one plan (outputs copied after its fix-up),
+    3D and FP64 plans, and 1D lines (each plan's outputs copied after its
+    execute): the host outputs equal the device ones."""
+    rng = np.random.default_rng(39)
+    if case == "1d_pair":
+        s = wl.Shape(1, (500,), 1 / 500, 2 / 500, rng.uniform(0.3, 0.7, (80, 1)), None)
+        taus, outputs, prec = [2 / 500, 1 / 500], ("S", "dS", "d2S"), "fp32"
+    elif case == "3d_pair":
+        s = wl.sphere(N=40, K=3000, radius=0.3, tau=0.03, seed=33)
+        taus, outputs, prec = [0.03, 0.02], ("S", "dS", "d2S", "sign"), "fp32"
+    elif case == "2d_fp64_pair":
+        s = wl.stars(N=200, K=2000, n_shapes=2, tau=0.006, seed=32)
+        taus, outputs, prec = [0.006, 0.004], ("S", "dS", "sign"), "fp64"
+    else:
+        s = wl.stars(N=256, K=3000, n_shapes=2, tau=0.004, seed=37)
+        taus, outputs, prec = [0.004], ("S", "dS", "d2S", "sign"), "fp32"
+    plans = [pkg.Plan(s.D, s.dims, s.h, t, precision=prec, outputs=outputs) for t in taus]
+    w = torch.from_numpy(s.weights).cuda() if "sign" in outputs else None
+    dev = pkg.execute_multi(plans, torch.from_numpy(s.points).cuda(), w)
+    torch.cuda.synchronize()
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    nd, nh = (1, 1) if s.D == 1 else (s.D, s.D * (s.D + 1) // 2)
+    shp = tuple(reversed(s.dims))
+    shapes = {"S": (shp, dt), "dS": ((nd,) + shp if s.D > 1 else shp, dt),
+              "d2S": ((nh,) + shp if s.D > 1 else shp, dt), "sign": (shp, torch.int8), "flags": (shp, torch.uint8)}
+    want = [k for k in shapes if k in outputs or k == "flags"]
+    outs = [{k: torch.empty(*shapes[k][:1], dtype=shapes[k][1]).pin_memory() for k in want} for _ in taus]
+    col = lambda k: [o[k] for o in outs] if k in want else None
+    pkg.sdf_execute_multi_host([p.handle for p in plans], s.K, torch.from_numpy(s.points),
+                               torch.from_numpy(s.weights) if w is not None else None, col("S"), col("dS"),
+                               col("d2S"), col("sign"), col("flags"))
+    for o, d in zip(outs, dev):
+        for k in o:
+            assert torch.equal(o[k], d[k].cpu().reshape(o[k].shape)), k
+    for p in plans:
+        p.close()
+
+
 def test_multi_after_pending_work_on_other_streams():
     """Plans on their own streams, with an execute still queued on the second
     plan's stream when the multi-execute starts: the first plan's stream
