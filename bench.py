@@ -409,7 +409,7 @@ def bench_c4(torch, pkg, flush, steps):
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
         b = pkg.Batch(2, [x.dims for x in shapes], [x.h for x in shapes], [x.tau for x in shapes],
-                      precision="fp32", outputs=("S", "sign"), n_streams=8, stream=st)
+                      precision="fp32", outputs=("S", "sign"), n_streams=16, stream=st)
         pts = [torch.from_numpy(x.points).cuda() for x in shapes]
         wts = [torch.from_numpy(x.weights).cuda() for x in shapes]
         outs = b.alloc_outputs()
