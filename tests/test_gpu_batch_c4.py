@@ -32,7 +32,7 @@ def test_batch_96_shapes_full_size_against_oracle():
     sides = sorted(set(s.dims[0] for s in shapes))
     assert sides == [256, 384, 512, 768, 1024]
     b = pkg.Batch(2, [s.dims for s in shapes], [s.h for s in shapes], [s.tau for s in shapes],
-                  precision="fp32", outputs=("S", "sign"), n_streams=8)
+                  precision="fp32", outputs=("S", "sign"), n_streams=16)
     pts = [torch.from_numpy(s.points).cuda() for s in shapes]
     wts = [torch.from_numpy(s.weights).cuda() for s in shapes]
     outs = b.alloc_outputs()
