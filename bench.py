@@ -370,6 +370,9 @@ def bench_c3(torch, pkg, flush, steps):
         with torch.cuda.stream(st):
             p = pkg.Plan(3, s.dims, s.h, s.tau, precision=prec, outputs=("S", "dS", "sign"), stream=st)
             o = p.alloc_outputs(["S", "dS", "sign", "flags"])
+        # the tile schedule chosen by the autotuner for both paths (plan-time
+        # work, untimed)
+        tuning = pkg.sdf_plan_autotune(p.handle, s.K, pts, w, 2)
         run = lambda: pkg.sdf_execute(p.handle, s.K, pts, w, o["S"], o["dS"], None, o["sign"], o["flags"])
         with torch.cuda.stream(st):
             run()
@@ -382,6 +385,7 @@ def bench_c3(torch, pkg, flush, steps):
         p.profile(False)
         stt = p.stats()
         res[prec] = {"ms_per_execute": ms, "grid_pts_per_s": s.n_nodes / (ms * 1e-3),
+                     "tile_schedule": {"lines_T": tuning[0], "lines_F": tuning[1], "fused_variant": tuning[2]},
                      "dominant_kernel": _dominant(list(prof.items())),
                      "err_bound_S_over_tau": stt.err_bound_S / s.tau, "err_bound_dS": stt.err_bound_dS,
                      "trusted_frac": stt.trusted_frac}

@@ -40,3 +40,25 @@ def test_torus_sphere_256(prec):
     rep = check(s, res, ref, sel=sel, check_hess=False, label="c3-" + prec)
     print("c3", prec, rep)
     assert rep["trusted"] > 300
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_torus_sphere_256_autotuned(prec, tmp_path, monkeypatch):
+    """The 3D workload with the tile schedule the autotuner picks (as the
+    bench runs it), sampled nodes against the oracle."""
+    monkeypatch.setenv("SDF_AUTOTUNE_CACHE", str(tmp_path / "autotune.tsv"))
+    s = wl.config_c3()
+    plan = pkg.Plan(3, s.dims, s.h, s.tau, precision=prec, outputs=("S", "dS", "sign"))
+    pts = torch.from_numpy(s.points).cuda()
+    w = torch.from_numpy(s.weights).cuda()
+    tune = pkg.sdf_plan_autotune(plan.handle, s.K, pts, w, 2)
+    out = plan.execute(pts, w)
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["stats"] = plan.stats()
+    sel = _sample(s, n_uniform=600, n_near=1400, seed=11)
+    ref = oracle_ref(s, sel=sel, want=("S", "dS", "mu", "R"))
+    rep = check(s, res, ref, sel=sel, check_hess=False, label="c3-tuned-" + prec)
+    print("c3 tuned", prec, tune, rep)
+    assert rep["trusted"] > 300
+    plan.close()
+
