@@ -466,6 +466,8 @@ def bench_c5(torch, pkg, flush, steps):
         wt = torch.from_numpy(wv).float().cuda().reshape(o["S"].shape)
         dY = torch.empty_like(pts)
         dtau = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # the autotuner's tile schedule (plan-time work, untimed)
+    tuning = pkg.sdf_plan_autotune(p.handle, pts.shape[0], pts, None, 2)
     fwd = lambda: pkg.sdf_execute(p.handle, pts.shape[0], pts, None, o["S"], o["dS"], None, None, o["flags"])
     bwd = lambda: pkg.sdf_backward(p.handle, pts.shape[0], pts, wt, o["S"], o["flags"], dY, dtau)
     with torch.cuda.stream(st):
@@ -478,6 +480,7 @@ def bench_c5(torch, pkg, flush, steps):
     p.close()
     return {"workload": "3D adjoint: 128^3 grid padded to 256^3, K=20000 jittered sphere points (snapped), "
                         "tau=0.01, FP32; dL/dY and dL/dtau of L = sum w S",
+            "tile_schedule": {"lines_T": tuning[0], "lines_F": tuning[1], "fused_variant": tuning[2]},
             "forward_ms": ms_f, "backward_ms": ms_b, "grid_pts_per_s_forward_plus_backward":
                 s.n_nodes / ((ms_f + ms_b) * 1e-3)}
 

@@ -38,9 +38,11 @@ def _band_weights(s, center, radius, half_width, seed):
     return w
 
 
-def _run(s, prec, Y, w):
+def _run(s, prec, Y, w, tune=False):
     plan = pkg.Plan(s.D, s.dims, s.h, s.tau, precision=prec, outputs=("S", "dS"))
     pts = torch.from_numpy(Y).cuda()
+    if tune:
+        pkg.sdf_plan_autotune(plan.handle, pts.shape[0], pts, None, 2)
     out = plan.execute(pts, None)
     dt = torch.float64 if prec == "fp64" else torch.float32
     wt = torch.from_numpy(w).to(dt).cuda().reshape(out["S"].shape)
@@ -81,14 +83,17 @@ def test_adjoint_2d_circle(prec):
     assert abs(dtau - rt) <= tol * abs(rt)
 
 
-def test_adjoint_differentiation_workload_full_size():
+@pytest.mark.parametrize("tune", [False, True])
+def test_adjoint_differentiation_workload_full_size(tune, tmp_path, monkeypatch):
     """The 3D differentiation workload: 128^3 grid, K = 20000 jittered sphere
-    points (sigma 0.01), tau = 0.01, float plan; every point's gradient."""
+    points (sigma 0.01), tau = 0.01, float plan; every point's gradient, with
+    the default tile schedule and with the autotuner's (as the bench runs it)."""
+    monkeypatch.setenv("SDF_AUTOTUNE_CACHE", str(tmp_path / "autotune.tsv"))
     s = wl.config_c5()
     Y = _snapped(s)
     s.points = Y
     w = _band_weights(s, (0.5, 0.5, 0.5), 0.3, 0.01, seed=50)
-    dY, dtau, _ = _run(s, "fp32", Y, w)
+    dY, dtau, _ = _run(s, "fp32", Y, w, tune=tune)
     X = oracle.grid_nodes(s.dims, s.h)
     keep = w != 0
     rY, rt = oracle.adjoint(Y, X[keep], w[keep], s.tau)
