@@ -100,3 +100,48 @@ def test_fixup_alu_peak():
     if os.path.exists(peaks):
         ghz = float(json.load(open(peaks)).get("sm_max_mhz", 2070.0)) / 1000.0
     assert bench.fixup_peak_gterms() == pytest.approx(152 * 128 * ghz / bench.FIXUP_FMA_OPS)
+
+
+def test_oracle_accuracy_reports_planted_errors():
+    """The bench's check of its own outputs against the oracle's sampled
+    values: outputs built from the oracle itself, then an S error of 1e-3 tau
+    at one uncapped node, a wild value at a capped node (ignored) and a sign
+    flip at a node off the boundary band."""
+    import numpy as np
+    import torch
+
+    import paper_1112_3010_gb300 as pkg
+    from paper_1112_3010_gb300 import workloads as wl
+
+    s = wl.stars(N=64, K=400, n_shapes=1, tau=0.02, seed=5)
+    samples = []
+    bench.cpu_baseline([s], n_nodes=300, seed=3, keep=samples)
+    sel, ref = samples[0]
+    n = s.n_nodes
+    sgn = np.where(np.abs(ref["mu"]) >= 0.5, 1, -1)
+    S = np.zeros(n)
+    dS = np.zeros((2, n))
+    d2S = np.zeros((3, n))
+    sign = np.ones(n, np.int8)
+    flags = np.zeros(n, np.uint8)
+    S[sel] = ref["S"] * sgn
+    dS[:, sel] = ref["dS"].T
+    d2S[:, sel] = ref["d2S"].T
+    sign[sel] = sgn
+    band = 2 * ref["wmax"] + s.h * np.sqrt(2.0)
+    off = np.nonzero((ref["R"] > band) & (np.abs(np.abs(ref["mu"]) - 0.5) >= 0.05))[0]
+    assert len(off) >= 3
+    a, b, c = off[0], off[1], off[2]
+    S[sel[a]] += 1e-3 * s.tau * sgn[a]          # an S error at an uncapped node
+    flags[sel[b]] = pkg.SDF_FLAG_CAPPED          # a capped node with a wild value: not counted
+    S[sel[b]] = 1e6
+    sign[sel[c]] = -sgn[c]                       # a sign flip off the band
+    S[sel[c]] = ref["S"][c] * -sgn[c]            # (S carries the sign)
+    outs = [{"S": torch.from_numpy(S.astype(np.float32)), "dS": torch.from_numpy(dS.astype(np.float32)),
+             "d2S": torch.from_numpy(d2S.astype(np.float32)), "sign": torch.from_numpy(sign),
+             "flags": torch.from_numpy(flags)}]
+    rep = bench.oracle_accuracy(pkg, [s], outs, samples)[0]
+    assert rep["sampled_nodes"] == len(sel) and rep["uncapped"] == len(sel) - 1
+    assert rep["max_abs_S_minus_oracle_over_tau"] == pytest.approx(1e-3, rel=1e-3)
+    assert rep["sign_mismatch"] == 1 and rep["sign_checked"] == len(off)
+    assert rep["max_abs_dS_minus_oracle"] < 1e-6
